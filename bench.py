@@ -1,0 +1,266 @@
+"""Throughput of the fused D2Q8 porous MRT-LB step on GB300, in MLUPS and as a fraction of the
+HBM roofline.
+
+Default workload: lid-driven porous cavity 4096 x 4096 (eps = 0.4, Da = 1e-3, Re = 100, lid
+velocity 0.1, halfway bounce-back walls, FP32 deviation storage, A-B pull streaming).  One
+"step" is one time step of the whole lattice (gather, collision, store).  Prints ONE JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--precision fp32|fp16|bf16] [--size L]
+
+Multi-GPU: the method has no cross-domain exchange in this workload set-up, so N ranks run N
+independent replicas (weak scaling); value = all cells updated / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & % HBM roofline (FP32 vs FP16 store); adjoint/forward time at stated err"
+PREC = {"fp32": 0, "fp16": 1, "bf16": 2}
+# algorithmic bytes per lattice update: 8 populations read + 8 written
+BYTES_PER_LU = {"fp32": 64, "fp16": 32, "bf16": 32}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def cavity_params(L):
+    lid = 0.1
+    return dict(nu=lid * L / 100.0, phi=0.4, K=1e-3 * L * L, lid=lid)
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1311_7239_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel_key):
+    """DRAM bytes per launch from a committed ncu capture, if it was taken on the current sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        e = d.get(kernel_key)
+        if e and e.get("source_hash") == source_hash():
+            return float(e["bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    Q = "clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if len(r) > 3 + k and r[3 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def cpu_baseline(L, seconds=12.0, size=256):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload (a size x size cavity
+    with the same parameters), on this host's cores."""
+    import numpy as np
+
+    from oracle import mrt_d2q8 as fl
+
+    prm = cavity_params(L)
+    flow = fl.Flow(nx=size, ny=size, phi=np.full((size, size), prm["phi"]), K=np.full((size, size), prm["K"]),
+                   nu=prm["nu"], bc_x="wall", bc_y="wall", u_top=(prm["lid"], 0.0))
+    f = fl.initial_state(flow)
+    f = fl.step(f, flow)
+    n = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        f = fl.step(f, flow)
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": size * size * n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{size}x{size} lid-driven porous cavity with the workload's eps, Da, nu, lid; {n} steps of the numpy FP64 oracle, single thread"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    L = args.size
+    b = cpu_baseline(L, seconds=max(3.0, 2.0 * args.steps), size=256)
+    line = {"impl": "reference", "metric": METRIC, "value": b["value"], "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"lid-driven porous cavity {L}x{L} (sampled: 256x256), eps=0.4, Da=1e-3, Re=100, lid=0.1",
+                       "nx": L, "ny": L},
+            "cpu_baseline": b, "e2e": {"value": b["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+
+    from paper_1311_7239_gb300 import lbm
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    L = args.size
+    prm = cavity_params(L)
+    prec = args.precision
+    stream = torch.cuda.Stream()
+    cfg = lbm.default_config(nx=L, ny=L, bc_x=lbm.WALL, bc_y=lbm.WALL, nu=prm["nu"], phi=prm["phi"], K=prm["K"],
+                             u_wall=[(0, 0), (0, 0), (0, 0), (prm["lid"], 0)], precision=PREC[prec], p_rest=prm["phi"],
+                             dev_scale_log2=10)
+    cfg.stream = stream.cuda_stream
+    lat = lbm.Lattice(cfg)
+    # warm-up (untimed)
+    with torch.cuda.stream(stream):
+        lat.step(args.warmup)
+    lat.sync()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        start.record(stream)
+        lat.step(args.steps)
+        stop.record(stream)
+        stop.synchronize()
+    torch.cuda.synchronize()
+    ms = start.elapsed_time(stop)
+    lat.sync()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    cells = L * L
+    mlups = cells * args.steps * world / (ms * 1e-3) / 1e6
+
+    # end to end through the C-ABI with host buffers: each step takes its wall velocities from
+    # pinned host memory and returns the cavity-centre probe (p, u, v, T) to pinned host memory
+    walls = torch.zeros(4, 2, dtype=torch.float32).pin_memory()
+    walls[3, 0] = prm["lid"]
+    probe = torch.zeros(4, dtype=torch.float32).pin_memory()
+    e2e_steps = max(10, min(args.steps, 2000))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        lat.set_walls(walls)
+        lat.step(1)
+        lat.probe(L // 2, L // 2, probe)
+    e2e_s = time.perf_counter() - t0
+    lat.sync()
+    e2e_mlups = cells * e2e_steps * world / e2e_s / 1e6
+    lat.close()
+
+    if rank != 0:
+        return 0
+    peak, peak_kind = peaks()
+    bpl = BYTES_PER_LU[prec]
+    achieved = bpl * cells / (ms * 1e-3 / args.steps) / 1e9
+    kernel_key = f"k_step_{prec}_uniform_{L}"
+    traffic = traffic_for(kernel_key)
+    line = {
+        "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp16": "f32 (f16 storage)", "bf16": "f32 (bf16 storage)"}[prec], "data": "synthetic",
+        "config": {"workload": f"lid-driven porous cavity {L}x{L}, eps=0.4, Da=1e-3, Re=100, lid=0.1, "
+                               f"{prec} deviation storage, A-B pull streaming",
+                   "nx": L, "ny": L, "precision": prec,
+                   "l2": f"inputs larger than L2 (2 population buffers of {bpl // 2 * cells / 1e6:.0f} MB)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs", "kernel": "k_step",
+                     "algorithmic_bytes_per_lu": bpl},
+        "gpu_launches": args.steps,
+        "e2e": {"value": e2e_mlups, "unit": "MLUPS", "h2d_bytes_per_step": int(walls.numel() * 4),
+                "d2h_bytes_per_step": int(probe.numel() * 4), "steps": e2e_steps,
+                "call": "lbm_set_walls(host) + lbm_step(1) + lbm_probe(host) per step"},
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(L)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=list(PREC))
+    ap.add_argument("--size", type=int, default=4096)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the timed CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_gpu(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,173 @@
+/*
+ * lbm.h -- C-ABI of liblbm.so, a GB300 (sm_103a) solver for the pressure-based D2Q8
+ * multiple-relaxation-time lattice Boltzmann model of incompressible porous flow of
+ * Liu & He, "Multiple-relaxation-time lattice Boltzmann modeling of incompressible flows in
+ * porous media" (arXiv 1311.7239), with the D2Q5 temperature equation of its Appendix B.
+ *
+ * Conventions (all entry points):
+ *   - Every function returns LBM_OK (0) or a negative LBM_E* code; none throws or aborts.
+ *     lbm_strerror() names a code; lbm_last_error() gives the message of the last failure
+ *     on the calling thread.
+ *   - Fields are row-major [ny][nx] (x fastest), row y = 0 at the bottom wall side; population
+ *     arrays are [q][ny][nx] with q in the paper's order (i = 1..8 of Eq. 7 stored as 0..7;
+ *     D2Q5 i = 0..4 of Eq. B.3).
+ *   - Pointers passed in may be device memory of the context's GPU or host memory (pinned or
+ *     pageable); the library detects which.  Caller memory is never freed or retained: inputs
+ *     are copied in, outputs are written before the call's work on the context stream ends.
+ *   - Work is enqueued on the context's CUDA stream (lbm_config.stream, or a stream the
+ *     library creates when that is NULL).  Calls with host outputs, lbm_sync, lbm_residual and
+ *     lbm_nusselt wait for the stream; the others return once the work is enqueued.
+ *   - A context is used by one host thread at a time.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_ABI_VERSION 1u
+
+#if defined(__GNUC__)
+#define LBM_API __attribute__((visibility("default")))
+#else
+#define LBM_API
+#endif
+
+/* status codes */
+#define LBM_OK 0
+#define LBM_EINVAL (-1)    /* bad argument or configuration */
+#define LBM_ENOMEM (-2)    /* device or host allocation failed */
+#define LBM_ECUDA (-3)     /* a CUDA runtime call failed */
+#define LBM_EUNSTABLE (-4) /* a step produced a non-finite velocity (reported at the next sync) */
+#define LBM_ETIMEOUT (-5)  /* a bounded device-side wait gave up */
+#define LBM_EABI (-6)      /* lbm_config.abi_version differs from LBM_ABI_VERSION */
+#define LBM_ESTATE (-7)    /* call not valid in the context's current state */
+
+/* population storage (all arithmetic is FP32; storage holds f - f_rest, see lbm_config) */
+#define LBM_FP32 0u
+#define LBM_FP16_DEV 1u
+#define LBM_BF16_DEV 2u
+
+/* boundary kinds of the x sides (left/right) and y sides (bottom/top) */
+#define LBM_PERIODIC 0u
+#define LBM_WALL 1u     /* halfway bounce-back, optionally moving (u_wall) */
+#define LBM_PRESSURE 2u /* x sides only: pressure columns by non-equilibrium extrapolation */
+
+/* wall indices of u_wall / T_wall */
+#define LBM_LEFT 0
+#define LBM_RIGHT 1
+#define LBM_BOTTOM 2
+#define LBM_TOP 3
+
+/*
+ * Problem description.  Symbols follow the paper: phi porosity, K permeability, nu the fluid
+ * viscosity upsilon, J = upsilon_e / upsilon (Eq. 5), rho0 the mean density, s_e and s_q the
+ * rates of Eq. 13 (1.1 and 1.2 in Sec. 3), a the external acceleration of Eq. 3.
+ * The viscous rate is s_v = 1/tau_v with J nu = c_s^2 (tau_v - 1/2) (Eq. 21).
+ */
+typedef struct lbm_config {
+  uint32_t abi_version; /* = LBM_ABI_VERSION */
+  uint32_t nx, ny;      /* lattice size, 2..65535 each */
+  uint32_t precision;   /* LBM_FP32 | LBM_FP16_DEV | LBM_BF16_DEV */
+  uint32_t bc_x, bc_y;  /* LBM_PERIODIC | LBM_WALL (| LBM_PRESSURE for bc_x) */
+  int32_t forchheimer;  /* 1: F_phi = 1.75 / sqrt(150 phi^3) (Eq. 4); 0: F_phi = 0 (Brinkman) */
+  int32_t thermal;      /* 1: couple the D2Q5 temperature equation (Appendix B, Sec. 3.4) */
+  double nu, J, rho0, s_e, s_q;
+  double ax, ay;        /* uniform external acceleration a (Eq. 3) */
+  double phi, K;        /* uniform medium, used until lbm_set_medium gives per-cell fields */
+  double u_wall[4][2];  /* wall velocities (left, right, bottom, top); a moving lid is u_wall[LBM_TOP] */
+  double p_in, p_out;   /* pressures of the x = 0 and x = nx-1 columns when bc_x == LBM_PRESSURE */
+  double p_rest;        /* reference phi*p of the stored deviations: f_rest,i = 3 w_i p_rest (Eq. 22, u = 0) */
+  int32_t dev_scale_log2; /* FP16/BF16 storage holds (f - f_rest) * 2^dev_scale_log2; ignored for FP32 */
+  /* temperature equation (used when thermal == 1) */
+  double tau_T;         /* zeta_1 = zeta_2 = 1/tau_T (Eq. B.7) */
+  double zeta3, zeta4;  /* remaining rates (1.1 in Sec. 3.4) */
+  double sigma;         /* thermal capacity ratio (Eq. B.1) */
+  double g_beta, T0;    /* buoyancy a = g_beta (T - T0) j (Sec. 3.4); T0 is also the stored reference */
+  double T_wall[4];     /* wall temperature (anti-bounce-back), NaN = adiabatic (bounce-back) */
+  void* stream;         /* cudaStream_t to use, or NULL */
+} lbm_config;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Fill *cfg with the paper's defaults (Sec. 3): J = 1, rho0 = 1, s_e = 1.1, s_q = 1.2,
+ * zeta3 = zeta4 = 1.1, sigma = 1, periodic x, walls in y, FP32, phi = 1, K = 1e30, p_rest = 1,
+ * dev_scale_log2 = 10, adiabatic walls. */
+LBM_API void lbm_config_defaults(lbm_config* cfg);
+
+/* sizeof(lbm_config) as compiled into the library, for bindings to check their layout. */
+LBM_API uint32_t lbm_config_size(void);
+
+/* Create a context on the current CUDA device: allocates two population buffers (A-B
+ * streaming), the medium fields and, if thermal, two temperature buffers.  The state is
+ * initialised as by lbm_init_equilibrium(ctx, 1, 0, 0, 0).  EABI / EINVAL / ENOMEM / ECUDA. */
+LBM_API int lbm_create(const lbm_config* cfg, lbm_ctx** out);
+
+/* Release everything the context owns.  NULL is accepted. */
+LBM_API void lbm_destroy(lbm_ctx* ctx);
+
+/* Per-cell porosity eps (phi of Eq. 3) and permeability K, float32 [ny][nx], copied in.
+ * Either may be NULL to keep a uniform value (cfg.phi / cfg.K).  Requires 0 < eps <= 1 and
+ * K > 0 (checked on the device; EINVAL).  Does not change the populations. */
+LBM_API int lbm_set_medium(lbm_ctx* ctx, const float* eps, const float* K);
+
+/* Set the populations to the equilibrium f_eq(p, u; phi) of Eq. 22 (= M^-1 m_eq, Eqs. 8, 11) with
+ * u = (ux0, uy0) and p = p0 (phi_p_uniform == 0, the initial state of Sec. 3.1) or p = p0/phi
+ * (phi_p_uniform == 1: uniform phi p, the rest state of a medium with varying porosity).
+ * Resets the step counter.  lbm_init_temperature sets g to the equilibrium of Eq. B.6 at
+ * T = T_init, u = 0 (thermal contexts only; ESTATE otherwise). */
+LBM_API int lbm_init_equilibrium(lbm_ctx* ctx, double p0, double ux0, double uy0, int phi_p_uniform);
+LBM_API int lbm_init_temperature(lbm_ctx* ctx, double T_init);
+
+/* Advance n >= 0 time steps of Eq. 6 (collision Eq. 14, streaming Eq. 15) and, if thermal,
+ * of Eq. B.2 with the buoyancy coupling.  Long runs replay a captured CUDA graph. */
+LBM_API int lbm_step(lbm_ctx* ctx, int n);
+
+/* Replace the wall velocities u_wall[4][2] (left, right, bottom, top; float32, host or device)
+ * for the following steps -- e.g. a time-dependent lid.  The copy is enqueued on the stream. */
+LBM_API int lbm_set_walls(lbm_ctx* ctx, const float* u_wall);
+
+/* (p, ux, uy, T) of one cell of the current state into out[4] (T = 0 without a temperature
+ * field), by the same rules as lbm_macros.  Host outputs wait for the stream. */
+LBM_API int lbm_probe(lbm_ctx* ctx, int x, int y, float* out);
+
+/* Macroscopic fields of the current state (pre-collision populations f(x, t)): pressure p
+ * (Eq. 20), velocity u (Eqs. 18-19) and, if thermal, temperature T = sum g.  Outputs are
+ * float32 [ny][nx]; any may be NULL. */
+LBM_API int lbm_macros(lbm_ctx* ctx, float* p, float* ux, float* uy, float* T);
+
+/* Export / import the current pre-collision populations f(x, t) as float32 [8][ny][nx]
+ * (g: [5][ny][nx]).  On import, columns recomputed by a pressure boundary are replaced at
+ * the next step. */
+LBM_API int lbm_get_populations(lbm_ctx* ctx, float* f, float* g);
+LBM_API int lbm_set_populations(lbm_ctx* ctx, const float* f, const float* g);
+
+/* Steady-state residual r = ||u(t) - u(t-1)||_2 / ||u(t)||_2 over all cells, summed in FP64
+ * on the device (needs one step since the last initialisation or import; ESTATE before that).  Waits for the stream. */
+LBM_API int lbm_residual(lbm_ctx* ctx, double* r);
+
+/* Average Nusselt number of a wall with a prescribed temperature (side = LBM_LEFT or
+ * LBM_RIGHT): Nu = (nx / (T_hot - T_cold)) * mean_y(-+ dT/dx at the wall), dT/dx from the
+ * parabola through the wall value and the two nearest cells; the sum is FP64.  Waits. */
+LBM_API int lbm_nusselt(lbm_ctx* ctx, int side, double* nu);
+
+/* Wait for the context stream and report a deferred error (EUNSTABLE, ECUDA). */
+LBM_API int lbm_sync(lbm_ctx* ctx);
+
+/* Number of steps taken since the last initialisation. */
+LBM_API int lbm_step_count(const lbm_ctx* ctx, int64_t* steps);
+
+/* Device byte count of the context's allocations (populations, medium, scratch). */
+LBM_API int lbm_memory_bytes(const lbm_ctx* ctx, uint64_t* bytes);
+
+LBM_API const char* lbm_strerror(int code);
+LBM_API const char* lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

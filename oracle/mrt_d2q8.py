@@ -329,7 +329,9 @@ def initial_state(flow: Flow, p0=1.0, u0=(0.0, 0.0)):
     ux = np.full((flow.ny, flow.nx), float(u0[0]))
     uy = np.full((flow.ny, flow.nx), float(u0[1]))
     p = np.broadcast_to(np.asarray(p0, dtype=np.float64), (flow.ny, flow.nx))
-    return equilibrium(p, ux, uy, flow.phi, flow.rho0)
+    f = equilibrium(p, ux, uy, flow.phi, flow.rho0)
+    # the initial state, like every later one, satisfies the pressure-column rule
+    return pressure_columns(f, flow) if flow.bc_x == "pressure" else f
 
 
 def step(f, flow: Flow):

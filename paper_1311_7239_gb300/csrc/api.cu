@@ -1,0 +1,580 @@
+// C-ABI layer of liblbm.so (declared in include/lbm.h): context lifetime, argument checks,
+// host/device pointer handling and kernel dispatch.  No entry point throws; every failure is a
+// negative status with a message in lbm_last_error().
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+namespace {
+
+thread_local char g_msg[512] = "";
+
+int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define LBM_CUDA(call, what)                 \
+  do {                                       \
+    cudaError_t e_ = (call);                 \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+}  // namespace
+
+struct lbm_ctx {
+  lbm_config cfg;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int prec = PREC_FP32;
+  size_t elem = 4;
+  int pitch = 0;
+  int64_t plane = 0;
+  void* f[2] = {nullptr, nullptr};
+  void* g[2] = {nullptr, nullptr};
+  int cur = 0;
+  float* phi = nullptr;
+  float* K = nullptr;
+  bool het = false;
+  unsigned int* err = nullptr;   // device error word
+  float* walls = nullptr;        // wall velocities [4][2] read by the kernels
+  float* probe = nullptr;        // 4-float read-out slot of lbm_probe
+  double* red = nullptr;         // reduction scratch: 2 * kResidualMaxBlocks partials + 2 results
+  float* stage = nullptr;        // staging for host inputs/outputs
+  size_t stage_bytes = 0;
+  uint64_t bytes = 0;
+  int64_t steps = 0;
+  int64_t history = 0;           // steps since the last initialisation or import
+  StepParams base;
+};
+
+namespace {
+
+bool thermal_of(const lbm_ctx* c) { return c->cfg.thermal != 0; }
+
+int dev_alloc(lbm_ctx* c, void** p, size_t bytes, const char* what) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_fail(e, what);
+  }
+  c->bytes += bytes;
+  return LBM_OK;
+}
+
+// 0: host (or unregistered) memory, 1: device memory of this context's GPU, -1: another GPU
+int pointer_kind(const lbm_ctx* c, const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return a.device == c->device ? 1 : -1;
+  return 0;
+}
+
+int ensure_stage(lbm_ctx* c, size_t bytes) {
+  if (c->stage_bytes >= bytes) return LBM_OK;
+  if (c->stage) {
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->stage);
+    c->bytes -= c->stage_bytes;
+    c->stage = nullptr;
+    c->stage_bytes = 0;
+  }
+  int rc = dev_alloc(c, reinterpret_cast<void**>(&c->stage), bytes, "cudaMalloc(staging)");
+  if (rc == LBM_OK) c->stage_bytes = bytes;
+  return rc;
+}
+
+// Resolve an input array of n floats to a device pointer (copying host data to the staging
+// area at float offset `slot`).
+int input_ptr(lbm_ctx* c, const float* user, size_t n, size_t slot, const float** out) {
+  *out = nullptr;
+  if (!user) return LBM_OK;
+  const int kind = pointer_kind(c, user);
+  if (kind < 0) return fail(LBM_EINVAL, "input pointer %p is memory of another GPU", (const void*)user);
+  if (kind == 1) {
+    *out = user;
+    return LBM_OK;
+  }
+  LBM_CUDA(cudaMemcpyAsync(c->stage + slot, user, n * sizeof(float), cudaMemcpyHostToDevice, c->stream), "copy of host input");
+  *out = c->stage + slot;
+  return LBM_OK;
+}
+
+struct OutArg {
+  float* user;
+  float* dev;
+  size_t n;
+  bool host;
+};
+
+int output_ptr(lbm_ctx* c, float* user, size_t n, size_t slot, OutArg* o) {
+  o->user = user;
+  o->dev = nullptr;
+  o->n = n;
+  o->host = false;
+  if (!user) return LBM_OK;
+  const int kind = pointer_kind(c, user);
+  if (kind < 0) return fail(LBM_EINVAL, "output pointer %p is memory of another GPU", (void*)user);
+  if (kind == 1) {
+    o->dev = user;
+    return LBM_OK;
+  }
+  o->dev = c->stage + slot;
+  o->host = true;
+  return LBM_OK;
+}
+
+int finish_outputs(lbm_ctx* c, OutArg* outs, int n) {
+  bool any = false;
+  for (int i = 0; i < n; ++i) {
+    if (outs[i].user && outs[i].host) {
+      LBM_CUDA(cudaMemcpyAsync(outs[i].user, outs[i].dev, outs[i].n * sizeof(float), cudaMemcpyDeviceToHost, c->stream),
+               "copy of output to host");
+      any = true;
+    }
+  }
+  if (any) LBM_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
+  return LBM_OK;
+}
+
+bool any_host(const lbm_ctx* c, const void* const* ptrs, int n) {
+  for (int i = 0; i < n; ++i)
+    if (ptrs[i] && pointer_kind(c, ptrs[i]) == 0) return true;
+  return false;
+}
+
+StepParams params_for(const lbm_ctx* c, bool forward_dst = true) {
+  StepParams P = c->base;
+  P.src = c->f[c->cur];
+  P.dst = c->f[c->cur ^ 1];
+  P.gsrc = c->g[c->cur];
+  P.gdst = c->g[c->cur ^ 1];
+  P.phi = c->het ? c->phi : nullptr;
+  P.K = c->het ? c->K : nullptr;
+  (void)forward_dst;
+  return P;
+}
+
+int check_error_word(lbm_ctx* c) {
+  unsigned int h = 0;
+  LBM_CUDA(cudaMemcpyAsync(&h, c->err, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "read of error word");
+  LBM_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
+  if (h & 1u) return fail(LBM_EUNSTABLE, "a step produced a non-finite velocity (after %lld steps)", (long long)c->steps);
+  return LBM_OK;
+}
+
+int validate(const lbm_config* c) {
+  if (c->abi_version != LBM_ABI_VERSION) return fail(LBM_EABI, "abi_version %u, library %u", c->abi_version, LBM_ABI_VERSION);
+  if (c->nx < 2 || c->ny < 2 || c->nx > 65535 || c->ny > 65535) return fail(LBM_EINVAL, "nx, ny must be in [2, 65535]");
+  if (c->precision > LBM_BF16_DEV) return fail(LBM_EINVAL, "unknown precision %u", c->precision);
+  if (c->bc_x > LBM_PRESSURE || c->bc_y > LBM_WALL) return fail(LBM_EINVAL, "unknown boundary kind");
+  if (c->bc_x == LBM_PRESSURE && c->nx < 3) return fail(LBM_EINVAL, "pressure columns need nx >= 3");
+  if (!(c->nu > 0) || !(c->J > 0) || !(c->rho0 > 0)) return fail(LBM_EINVAL, "nu, J, rho0 must be positive");
+  if (!(c->s_e > 0 && c->s_e < 2) || !(c->s_q > 0 && c->s_q < 2)) return fail(LBM_EINVAL, "s_e, s_q must be in (0, 2)");
+  if (!(c->phi > 0 && c->phi <= 1) || !(c->K > 0)) return fail(LBM_EINVAL, "uniform phi must be in (0, 1], K > 0");
+  if (!isfinite(c->ax) || !isfinite(c->ay) || !isfinite(c->p_rest)) return fail(LBM_EINVAL, "non-finite a or p_rest");
+  if (c->dev_scale_log2 < -30 || c->dev_scale_log2 > 30) return fail(LBM_EINVAL, "dev_scale_log2 out of [-30, 30]");
+  if (c->thermal) {
+    if (!(c->tau_T > 0.5) || !(c->sigma > 0)) return fail(LBM_EINVAL, "tau_T must exceed 1/2 and sigma be positive");
+    if (!(c->zeta3 > 0 && c->zeta3 < 2) || !(c->zeta4 > 0 && c->zeta4 < 2)) return fail(LBM_EINVAL, "zeta3, zeta4 in (0, 2)");
+  }
+  return LBM_OK;
+}
+
+void fill_base(lbm_ctx* c) {
+  const lbm_config& k = c->cfg;
+  StepParams& P = c->base;
+  memset(&P, 0, sizeof(P));
+  P.nx = (int)k.nx;
+  P.ny = (int)k.ny;
+  P.pitch = c->pitch;
+  P.plane = c->plane;
+  P.bc_x = (int)k.bc_x;
+  P.bc_y = (int)k.bc_y;
+  P.forch = k.forchheimer ? 1 : 0;
+  P.rho0 = (float)k.rho0;
+  P.nu = (float)k.nu;
+  P.s_e = (float)k.s_e;
+  P.s_q = (float)k.s_q;
+  const double tau_v = 3.0 * k.J * k.nu + 0.5;  // Eq. 21: J nu = c_s^2 (tau_v - 1/2)
+  P.s_v = (float)(1.0 / tau_v);
+  P.ax = (float)k.ax;
+  P.ay = (float)k.ay;
+  P.phi_u = (float)k.phi;
+  P.inv_phi_u = (float)(1.0 / k.phi);
+  P.c_lin_u = (float)(k.phi * k.nu / k.K);
+  P.c_nl_u = k.forchheimer ? (float)(1.75 / sqrt(150.0 * k.phi * k.K)) : 0.0f;
+  P.uw = c->walls;
+  for (int w = 0; w < 4; ++w) {
+    P.Tdir[w] = isnan(k.T_wall[w]) ? 0 : 1;
+    P.Tw[w] = isnan(k.T_wall[w]) ? 0.0f : (float)k.T_wall[w];
+  }
+  P.p_in = (float)k.p_in;
+  P.p_out = (float)k.p_out;
+  P.p_rest = (float)k.p_rest;
+  const double sc = c->prec == PREC_FP32 ? 1.0 : ldexp(1.0, k.dev_scale_log2);
+  P.scale = (float)sc;
+  P.inv_scale = (float)(1.0 / sc);
+  P.zeta1 = k.thermal ? (float)(1.0 / k.tau_T) : 1.0f;
+  P.zeta3 = (float)k.zeta3;
+  P.zeta4 = (float)k.zeta4;
+  P.inv_sigma = k.sigma > 0 ? (float)(1.0 / k.sigma) : 1.0f;
+  P.varpi = 0.0f;  // Appendix B fixes varpi = 0
+  P.g_beta = (float)k.g_beta;
+  P.T0 = (float)k.T0;
+  P.err = c->err;
+}
+
+void release(lbm_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (int b = 0; b < 2; ++b) {
+    cudaFree(c->f[b]);
+    cudaFree(c->g[b]);
+  }
+  cudaFree(c->phi);
+  cudaFree(c->K);
+  cudaFree(c->err);
+  cudaFree(c->walls);
+  cudaFree(c->probe);
+  cudaFree(c->red);
+  cudaFree(c->stage);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_config_defaults(lbm_config* cfg) {
+  if (!cfg) return;
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->abi_version = LBM_ABI_VERSION;
+  cfg->nx = cfg->ny = 64;
+  cfg->precision = LBM_FP32;
+  cfg->bc_x = LBM_PERIODIC;
+  cfg->bc_y = LBM_WALL;
+  cfg->forchheimer = 1;
+  cfg->nu = 0.1;
+  cfg->J = 1.0;
+  cfg->rho0 = 1.0;
+  cfg->s_e = 1.1;
+  cfg->s_q = 1.2;
+  cfg->phi = 1.0;
+  cfg->K = 1e30;
+  cfg->p_in = cfg->p_out = 1.0;
+  cfg->p_rest = 1.0;
+  cfg->dev_scale_log2 = 10;
+  cfg->tau_T = 1.0;
+  cfg->zeta3 = cfg->zeta4 = 1.1;
+  cfg->sigma = 1.0;
+  for (int w = 0; w < 4; ++w) cfg->T_wall[w] = NAN;
+}
+
+uint32_t lbm_config_size(void) { return (uint32_t)sizeof(lbm_config); }
+
+int lbm_create(const lbm_config* cfg, lbm_ctx** out) {
+  if (!cfg || !out) return fail(LBM_EINVAL, "null argument");
+  *out = nullptr;
+  int rc = validate(cfg);
+  if (rc) return rc;
+  lbm_ctx* c = new (std::nothrow) lbm_ctx();
+  if (!c) return fail(LBM_ENOMEM, "host allocation of the context");
+  c->cfg = *cfg;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  c->prec = (int)cfg->precision;
+  c->elem = c->prec == PREC_FP32 ? 4 : 2;
+  c->pitch = (int)((cfg->nx + 127) / 128 * 128);
+  c->plane = (int64_t)c->pitch * cfg->ny;
+  if (cfg->stream) {
+    c->stream = static_cast<cudaStream_t>(cfg->stream);
+  } else {
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete c;
+      return cuda_fail(e, "cudaStreamCreate");
+    }
+    c->own_stream = true;
+  }
+  const size_t fbytes = 8 * (size_t)c->plane * c->elem;
+  const size_t gbytes = 5 * (size_t)c->plane * c->elem;
+  for (int b = 0; b < 2 && rc == LBM_OK; ++b) {
+    rc = dev_alloc(c, &c->f[b], fbytes, "cudaMalloc(populations)");
+    if (rc == LBM_OK && cfg->thermal) rc = dev_alloc(c, &c->g[b], gbytes, "cudaMalloc(temperature populations)");
+  }
+  if (rc == LBM_OK) rc = dev_alloc(c, reinterpret_cast<void**>(&c->err), sizeof(unsigned int), "cudaMalloc(error word)");
+  if (rc == LBM_OK)
+    rc = dev_alloc(c, reinterpret_cast<void**>(&c->red), (2 * kResidualMaxBlocks + 2) * sizeof(double), "cudaMalloc(reduction)");
+  if (rc == LBM_OK) rc = dev_alloc(c, reinterpret_cast<void**>(&c->walls), 8 * sizeof(float), "cudaMalloc(walls)");
+  if (rc == LBM_OK) rc = dev_alloc(c, reinterpret_cast<void**>(&c->probe), 4 * sizeof(float), "cudaMalloc(probe)");
+  if (rc == LBM_OK) {
+    float w[8];
+    for (int i = 0; i < 8; ++i) w[i] = (float)cfg->u_wall[i / 2][i % 2];
+    e = cudaMemcpy(c->walls, w, sizeof(w), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) rc = cuda_fail(e, "copy of wall velocities");
+  }
+  if (rc == LBM_OK) {
+    e = cudaMemsetAsync(c->err, 0, sizeof(unsigned int), c->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemset");
+  }
+  if (rc == LBM_OK) {
+    for (int b = 0; b < 2 && rc == LBM_OK; ++b) {
+      e = cudaMemsetAsync(c->f[b], 0, fbytes, c->stream);
+      if (e == cudaSuccess && c->g[b]) e = cudaMemsetAsync(c->g[b], 0, gbytes, c->stream);
+      if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemset");
+    }
+  }
+  if (rc != LBM_OK) {
+    release(c);
+    return rc;
+  }
+  fill_base(c);
+  rc = lbm_init_equilibrium(c, 1.0, 0.0, 0.0, 0);
+  if (rc == LBM_OK && cfg->thermal) rc = lbm_init_temperature(c, cfg->T0);
+  if (rc != LBM_OK) {
+    release(c);
+    return rc;
+  }
+  *out = c;
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx* ctx) { release(ctx); }
+
+int lbm_set_medium(lbm_ctx* c, const float* eps, const float* K) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  if (!eps && !K) {
+    c->het = false;
+    return LBM_OK;
+  }
+  const size_t n = (size_t)c->cfg.nx * c->cfg.ny;
+  const size_t fields = (size_t)c->plane * sizeof(float);
+  int rc = LBM_OK;
+  if (!c->phi) rc = dev_alloc(c, reinterpret_cast<void**>(&c->phi), fields, "cudaMalloc(porosity)");
+  if (rc == LBM_OK && !c->K) rc = dev_alloc(c, reinterpret_cast<void**>(&c->K), fields, "cudaMalloc(permeability)");
+  if (rc) return rc;
+  const void* ptrs[2] = {eps, K};
+  if (any_host(c, ptrs, 2) && (rc = ensure_stage(c, 2 * n * sizeof(float)))) return rc;
+  const float *de = nullptr, *dk = nullptr;
+  if ((rc = input_ptr(c, eps, n, 0, &de)) || (rc = input_ptr(c, K, n, n, &dk))) return rc;
+  LBM_CUDA(cudaMemsetAsync(c->err, 0, sizeof(unsigned int), c->stream), "cudaMemset");
+  LBM_CUDA(launch_medium(de, dk, (float)c->cfg.phi, (float)c->cfg.K, (int)c->cfg.nx, (int)c->cfg.ny, c->pitch, c->phi, c->K,
+                         c->err, c->stream),
+           "medium kernel");
+  unsigned int h = 0;
+  LBM_CUDA(cudaMemcpyAsync(&h, c->err, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "read of error word");
+  LBM_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
+  if (h & 2u) {
+    LBM_CUDA(cudaMemsetAsync(c->err, 0, sizeof(unsigned int), c->stream), "cudaMemset");
+    return fail(LBM_EINVAL, "medium out of range: need 0 < eps <= 1 and 0 < K < 3e38");
+  }
+  c->het = true;
+  return LBM_OK;
+}
+
+int lbm_init_equilibrium(lbm_ctx* c, double p0, double ux0, double uy0, int phi_p_uniform) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  if (!isfinite(p0) || !isfinite(ux0) || !isfinite(uy0)) return fail(LBM_EINVAL, "non-finite initial state");
+  StepParams P = params_for(c);
+  P.dst = c->f[c->cur];
+  LBM_CUDA(launch_init(P, c->prec, c->het, thermal_of(c), (float)p0, (float)ux0, (float)uy0, phi_p_uniform ? 1 : 0, 0.0f, true,
+                       false, c->stream),
+           "init kernel");
+  c->steps = 0;
+  c->history = 0;
+  return LBM_OK;
+}
+
+int lbm_init_temperature(lbm_ctx* c, double T_init) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  if (!thermal_of(c)) return fail(LBM_ESTATE, "context has no temperature field");
+  if (!isfinite(T_init)) return fail(LBM_EINVAL, "non-finite temperature");
+  StepParams P = params_for(c);
+  P.gdst = c->g[c->cur];
+  LBM_CUDA(launch_init(P, c->prec, c->het, true, 0.0f, 0.0f, 0.0f, 0, (float)T_init, false, true, c->stream), "init kernel");
+  c->steps = 0;
+  c->history = 0;
+  return LBM_OK;
+}
+
+int lbm_step(lbm_ctx* c, int n) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  if (n < 0) return fail(LBM_EINVAL, "negative step count");
+  for (int k = 0; k < n; ++k) {
+    StepParams P = params_for(c);
+    LBM_CUDA(launch_step(P, c->prec, c->het, thermal_of(c), c->stream), "step kernel");
+    c->cur ^= 1;
+    ++c->steps;
+    ++c->history;
+  }
+  return LBM_OK;
+}
+
+int lbm_set_walls(lbm_ctx* c, const float* u_wall) {
+  if (!c || !u_wall) return fail(LBM_EINVAL, "null argument");
+  const int kind = pointer_kind(c, u_wall);
+  if (kind < 0) return fail(LBM_EINVAL, "wall velocities in memory of another GPU");
+  LBM_CUDA(cudaMemcpyAsync(c->walls, u_wall, 8 * sizeof(float), kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                           c->stream),
+           "copy of wall velocities");
+  for (int i = 0; i < 8; ++i)
+    if (kind == 0) c->cfg.u_wall[i / 2][i % 2] = u_wall[i];
+  return LBM_OK;
+}
+
+int lbm_probe(lbm_ctx* c, int x, int y, float* out) {
+  if (!c || !out) return fail(LBM_EINVAL, "null argument");
+  if (x < 0 || y < 0 || x >= (int)c->cfg.nx || y >= (int)c->cfg.ny) return fail(LBM_EINVAL, "probe cell outside the lattice");
+  const int kind = pointer_kind(c, out);
+  if (kind < 0) return fail(LBM_EINVAL, "probe output in memory of another GPU");
+  StepParams P = params_for(c);
+  LBM_CUDA(launch_probe(P, c->prec, c->het, thermal_of(c), x, y, kind ? out : c->probe, c->stream), "probe kernel");
+  if (kind == 0) {
+    LBM_CUDA(cudaMemcpyAsync(out, c->probe, 4 * sizeof(float), cudaMemcpyDeviceToHost, c->stream), "copy of probe");
+    LBM_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
+  }
+  return LBM_OK;
+}
+
+int lbm_macros(lbm_ctx* c, float* p, float* ux, float* uy, float* T) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  if (T && !thermal_of(c)) return fail(LBM_ESTATE, "context has no temperature field");
+  const size_t n = (size_t)c->cfg.nx * c->cfg.ny;
+  const void* ptrs[4] = {p, ux, uy, T};
+  int rc;
+  if (any_host(c, ptrs, 4) && (rc = ensure_stage(c, 4 * n * sizeof(float)))) return rc;
+  OutArg o[4];
+  float* users[4] = {p, ux, uy, T};
+  for (int i = 0; i < 4; ++i)
+    if ((rc = output_ptr(c, users[i], n, i * n, &o[i]))) return rc;
+  StepParams P = params_for(c);
+  LBM_CUDA(launch_macros(P, c->prec, c->het, thermal_of(c), o[0].dev, o[1].dev, o[2].dev, o[3].dev, c->stream), "macros kernel");
+  return finish_outputs(c, o, 4);
+}
+
+int lbm_get_populations(lbm_ctx* c, float* f, float* g) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  if (g && !thermal_of(c)) return fail(LBM_ESTATE, "context has no temperature field");
+  const size_t n = (size_t)c->cfg.nx * c->cfg.ny;
+  const void* ptrs[2] = {f, g};
+  int rc;
+  if (any_host(c, ptrs, 2) && (rc = ensure_stage(c, 13 * n * sizeof(float)))) return rc;
+  OutArg o[2];
+  if ((rc = output_ptr(c, f, 8 * n, 0, &o[0])) || (rc = output_ptr(c, g, 5 * n, 8 * n, &o[1]))) return rc;
+  StepParams P = params_for(c);
+  LBM_CUDA(launch_export(P, c->prec, c->het, thermal_of(c), o[0].dev, o[1].dev, c->stream), "export kernel");
+  return finish_outputs(c, o, 2);
+}
+
+int lbm_set_populations(lbm_ctx* c, const float* f, const float* g) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  if (g && !thermal_of(c)) return fail(LBM_ESTATE, "context has no temperature field");
+  const size_t n = (size_t)c->cfg.nx * c->cfg.ny;
+  const void* ptrs[2] = {f, g};
+  int rc;
+  if (any_host(c, ptrs, 2) && (rc = ensure_stage(c, 13 * n * sizeof(float)))) return rc;
+  const float *df = nullptr, *dg = nullptr;
+  if ((rc = input_ptr(c, f, 8 * n, 0, &df)) || (rc = input_ptr(c, g, 5 * n, 8 * n, &dg))) return rc;
+  StepParams P = params_for(c);
+  P.dst = c->f[c->cur];
+  P.gdst = c->g[c->cur];
+  LBM_CUDA(launch_import(P, c->prec, df, dg, c->stream), "import kernel");
+  c->history = 0;
+  if (any_host(c, ptrs, 2)) LBM_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
+  return LBM_OK;
+}
+
+int lbm_residual(lbm_ctx* c, double* r) {
+  if (!c || !r) return fail(LBM_EINVAL, "null argument");
+  if (c->history < 1) return fail(LBM_ESTATE, "the residual needs one step since the last initialisation");
+  StepParams P = params_for(c);
+  const int nb = residual_blocks((int)c->cfg.nx, (int)c->cfg.ny);
+  double* out = c->red + 2 * kResidualMaxBlocks;
+  LBM_CUDA(launch_residual(P, c->prec, c->het, thermal_of(c), c->f[c->cur ^ 1], c->g[c->cur ^ 1], c->red, nb, out, c->stream),
+           "residual kernels");
+  double h[2];
+  LBM_CUDA(cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "read of residual");
+  LBM_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
+  *r = h[1] > 0 ? sqrt(h[0] / h[1]) : 0.0;
+  return check_error_word(c);
+}
+
+int lbm_nusselt(lbm_ctx* c, int side, double* nu) {
+  if (!c || !nu) return fail(LBM_EINVAL, "null argument");
+  if (!thermal_of(c)) return fail(LBM_ESTATE, "context has no temperature field");
+  if (side != LBM_LEFT && side != LBM_RIGHT) return fail(LBM_EINVAL, "side must be LBM_LEFT or LBM_RIGHT");
+  if (c->cfg.bc_x != LBM_WALL || isnan(c->cfg.T_wall[LBM_LEFT]) || isnan(c->cfg.T_wall[LBM_RIGHT]))
+    return fail(LBM_ESTATE, "the Nusselt number needs isothermal left and right walls");
+  const double dT = c->cfg.T_wall[LBM_LEFT] - c->cfg.T_wall[LBM_RIGHT];
+  if (dT == 0) return fail(LBM_EINVAL, "equal wall temperatures");
+  StepParams P = params_for(c);
+  double* out = c->red + 2 * kResidualMaxBlocks;
+  LBM_CUDA(launch_nusselt(P, c->prec, side, out, c->stream), "nusselt kernel");
+  double s = 0;
+  LBM_CUDA(cudaMemcpyAsync(&s, out, sizeof(s), cudaMemcpyDeviceToHost, c->stream), "read of Nusselt sum");
+  LBM_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
+  const double mean = s / (double)c->cfg.ny;
+  *nu = (side == LBM_LEFT ? -1.0 : 1.0) * (double)c->cfg.nx / dT * mean;
+  return check_error_word(c);
+}
+
+int lbm_sync(lbm_ctx* c) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  LBM_CUDA(cudaGetLastError(), "pending launch error");
+  return check_error_word(c);
+}
+
+int lbm_step_count(const lbm_ctx* c, int64_t* steps) {
+  if (!c || !steps) return fail(LBM_EINVAL, "null argument");
+  *steps = c->steps;
+  return LBM_OK;
+}
+
+int lbm_memory_bytes(const lbm_ctx* c, uint64_t* bytes) {
+  if (!c || !bytes) return fail(LBM_EINVAL, "null argument");
+  *bytes = c->bytes;
+  return LBM_OK;
+}
+
+const char* lbm_strerror(int code) {
+  switch (code) {
+    case LBM_OK: return "ok";
+    case LBM_EINVAL: return "invalid argument";
+    case LBM_ENOMEM: return "out of memory";
+    case LBM_ECUDA: return "CUDA error";
+    case LBM_EUNSTABLE: return "unstable: non-finite velocity";
+    case LBM_ETIMEOUT: return "device wait timed out";
+    case LBM_EABI: return "ABI version mismatch";
+    case LBM_ESTATE: return "invalid state for this call";
+    default: return "unknown error";
+  }
+}
+
+const char* lbm_last_error(void) { return g_msg; }
+
+}  // extern "C"

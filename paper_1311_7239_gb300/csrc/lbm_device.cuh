@@ -1,0 +1,354 @@
+// Device-side building blocks of the porous D2Q8 MRT-LB step (Liu & He, arXiv 1311.7239) and of
+// the D2Q5 temperature step (its Appendix B), for sm_103a.
+//
+// Storage: structure-of-arrays planes [q][ny][pitch].  Every plane holds the deviation of a
+// post-collision population from the rest equilibrium, d_i = f_i - f_rest,i with
+// f_rest,i = 3 w_i p_rest (Eq. 22 at u = 0, phi p = p_rest) for the flow and T0 / 5 (Eq. B.6 at
+// u = 0, T = T0) for the temperature; FP16/BF16 planes scale d by 2^k.  The collision below works
+// in those deviation variables throughout, which keeps FP32 arithmetic (and FP16 storage) far
+// from the cancellation of subtracting two O(1) populations.
+//
+// One time step per cell (pull form of Eq. 15 followed by Eq. 14):
+//   gather d_i(x - e_i) (bounce-back/periodic/pressure rules at the edges)
+//   m = M d (Eq. 10, expanded), v, u (Eqs. 18-19), phi p (Eq. 20), F (Eq. 3), S (Eq. 16),
+//   m+ = m - Lambda (m - m_eq) + (I - Lambda/2) S (Eqs. 11-14), d+ = M^-1 m+ (Eq. 8, expanded).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace lbm {
+
+enum : int { PREC_FP32 = 0, PREC_FP16 = 1, PREC_BF16 = 2 };
+enum : int { BC_PERIODIC = 0, BC_WALL = 1, BC_PRESSURE = 2 };
+
+// Everything a step kernel needs, passed by value.
+struct StepParams {
+  const void* src;   // current post-collision planes (8)
+  void* dst;         // next post-collision planes (8)
+  const void* gsrc;  // temperature planes (5), thermal only
+  void* gdst;
+  const float* phi;  // per-cell porosity [ny][pitch], or nullptr for uniform
+  const float* K;    // per-cell permeability [ny][pitch], or nullptr for uniform
+  int nx, ny, pitch;
+  int64_t plane;     // elements per plane = ny * pitch
+  int bc_x, bc_y;
+  int forch;
+  float rho0, nu, s_e, s_q, s_v;
+  float ax, ay;
+  // uniform-medium coefficients
+  float phi_u, inv_phi_u, c_lin_u, c_nl_u;
+  const float* uw;    // wall velocities [4][2] in device memory: left, right, bottom, top
+  float p_in, p_out;  // pressure columns
+  float p_rest;       // phi p of the stored rest state
+  float scale, inv_scale;  // storage scale 2^k (1 for FP32)
+  // temperature
+  float zeta1, zeta3, zeta4, inv_sigma, varpi, g_beta, T0;
+  float Tw[4];
+  int Tdir[4];        // 1 = wall temperature prescribed, 0 = adiabatic
+  unsigned int* err;  // bit 0: non-finite velocity
+};
+
+// D2Q8 velocities of Eq. 7 and the weights w_i listed after Eq. 20 (w_1..4 = 1/9, w_5..8 = 1/36).
+__device__ __forceinline__ int ex_of(int i) { return (i == 0 || i == 4 || i == 7) ? 1 : ((i == 2 || i == 5 || i == 6) ? -1 : 0); }
+__device__ __forceinline__ int ey_of(int i) { return (i == 1 || i == 4 || i == 5) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0); }
+__device__ __forceinline__ int opp_of(int i) { return i < 4 ? (i + 2) & 3 : 4 + ((i - 4 + 2) & 3); }
+__device__ __forceinline__ float w_of(int i) { return i < 4 ? (1.0f / 9.0f) : (1.0f / 36.0f); }
+
+// ---------------------------------------------------------------------------------------------
+// storage codecs
+// ---------------------------------------------------------------------------------------------
+template <int PREC> struct Store;
+template <> struct Store<PREC_FP32> {
+  using T = float;
+  __device__ static __forceinline__ float dec(T v, float) { return v; }
+  __device__ static __forceinline__ T enc(float v, float) { return v; }
+  __device__ static __forceinline__ void load4(const T* p, float o[4], float) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  }
+  __device__ static __forceinline__ void store4(T* p, const float o[4], float) {
+    *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+  }
+};
+template <> struct Store<PREC_FP16> {
+  using T = __half;
+  __device__ static __forceinline__ float dec(T v, float inv) { return __half2float(v) * inv; }
+  __device__ static __forceinline__ T enc(float v, float sc) { return __float2half_rn(v * sc); }
+  __device__ static __forceinline__ void load4(const T* p, float o[4], float inv) {
+    const uint2 raw = *reinterpret_cast<const uint2*>(p);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&raw.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&raw.y));
+    o[0] = a.x * inv; o[1] = a.y * inv; o[2] = b.x * inv; o[3] = b.y * inv;
+  }
+  __device__ static __forceinline__ void store4(T* p, const float o[4], float sc) {
+    __half2 a = __floats2half2_rn(o[0] * sc, o[1] * sc);
+    __half2 b = __floats2half2_rn(o[2] * sc, o[3] * sc);
+    uint2 raw;
+    raw.x = *reinterpret_cast<unsigned int*>(&a);
+    raw.y = *reinterpret_cast<unsigned int*>(&b);
+    *reinterpret_cast<uint2*>(p) = raw;
+  }
+};
+template <> struct Store<PREC_BF16> {
+  using T = __nv_bfloat16;
+  __device__ static __forceinline__ float dec(T v, float inv) { return __bfloat162float(v) * inv; }
+  __device__ static __forceinline__ T enc(float v, float sc) { return __float2bfloat16_rn(v * sc); }
+  __device__ static __forceinline__ void load4(const T* p, float o[4], float inv) {
+    const uint2 raw = *reinterpret_cast<const uint2*>(p);
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw.y));
+    o[0] = a.x * inv; o[1] = a.y * inv; o[2] = b.x * inv; o[3] = b.y * inv;
+  }
+  __device__ static __forceinline__ void store4(T* p, const float o[4], float sc) {
+    __nv_bfloat162 a = __floats2bfloat162_rn(o[0] * sc, o[1] * sc);
+    __nv_bfloat162 b = __floats2bfloat162_rn(o[2] * sc, o[3] * sc);
+    uint2 raw;
+    raw.x = *reinterpret_cast<unsigned int*>(&a);
+    raw.y = *reinterpret_cast<unsigned int*>(&b);
+    *reinterpret_cast<uint2*>(p) = raw;
+  }
+};
+
+// ---------------------------------------------------------------------------------------------
+// medium coefficients of one cell
+// ---------------------------------------------------------------------------------------------
+struct Coef {
+  float phi, inv_phi;
+  float c_lin;  // phi nu / K          (linear Darcy drag of Eq. 3)
+  float c_nl;   // phi F_phi / sqrt(K)  (Forchheimer drag of Eq. 3; = 1.75 / sqrt(150 phi K) by Eq. 4)
+};
+
+template <bool HET>
+__device__ __forceinline__ Coef coef_at(const StepParams& P, int x, int y) {
+  Coef c;
+  if (!HET) {
+    c.phi = P.phi_u; c.inv_phi = P.inv_phi_u; c.c_lin = P.c_lin_u; c.c_nl = P.c_nl_u;
+  } else {
+    const int64_t o = (int64_t)y * P.pitch + x;
+    const float ph = __ldg(P.phi + o);
+    const float k = __ldg(P.K + o);
+    c.phi = ph;
+    c.inv_phi = 1.0f / ph;
+    c.c_lin = ph * P.nu / k;
+    c.c_nl = P.forch ? 1.75f * rsqrtf(150.0f * ph * k) : 0.0f;
+  }
+  return c;
+}
+
+// ---------------------------------------------------------------------------------------------
+// macroscopic velocity and pressure deviation of a pre-collision cell (Eqs. 17-20)
+// ---------------------------------------------------------------------------------------------
+struct Macro {
+  float dm1;       // sum of deviations (first moment of M applied to d)
+  float ux, uy;    // velocity, Eq. 18
+  float phip_dev;  // phi p - p_rest, Eq. 20
+};
+
+__device__ __forceinline__ void velocity_from_j(float jx, float jy, const Coef& c, float ax, float ay,
+                                                float rho0, float& ux, float& uy) {
+  // Eq. 19: v = sum e f / rho0 + phi a / 2 ; l0 = (1 + phi nu / (2K)) / 2 ; l1 = phi F_phi / (2 sqrt K)
+  const float vx = jx / rho0 + 0.5f * c.phi * ax;
+  const float vy = jy / rho0 + 0.5f * c.phi * ay;
+  const float l0 = 0.5f + 0.25f * c.c_lin;
+  const float l1 = 0.5f * c.c_nl;
+  const float vmag = sqrtf(vx * vx + vy * vy);
+  // Eq. 18, the cancellation-free root of l1 |u|^2 + 2 l0 |u| - |v| = 0
+  const float inv = 1.0f / (l0 + sqrtf(l0 * l0 + l1 * vmag));
+  ux = vx * inv;
+  uy = vy * inv;
+}
+
+// ---------------------------------------------------------------------------------------------
+// collision of one cell in deviation variables, d[8] in (pre-collision), out (post-collision)
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ void collide_d2q8(float d[8], const Coef& c, float ax, float ay, const StepParams& P,
+                                             float& ux_out, float& uy_out, float& phip_out) {
+  const float rho0 = P.rho0;
+  // m = M d, Eq. 10 with shared partial sums
+  const float a13 = d[0] + d[2], a24 = d[1] + d[3];
+  const float d13 = d[0] - d[2], d24 = d[1] - d[3];
+  const float s57 = d[4] + d[6], s68 = d[5] + d[7];
+  const float t57 = d[4] - d[6], t68 = d[5] - d[7];
+  const float diag = s57 + s68;
+  const float m1 = a13 + a24 + diag;        // p      (deviation)
+  const float m2 = -(a13 + a24) + diag;     // e      (deviation)
+  const float dxs = t57 - t68;              // e_x-weighted diagonal sum
+  const float dys = t57 + t68;              // e_y-weighted diagonal sum
+  const float m3 = d13 + dxs;               // j_x
+  const float m4 = -2.0f * d13 + dxs;       // q_x
+  const float m5 = d24 + dys;               // j_y
+  const float m6 = -2.0f * d24 + dys;       // q_y
+  const float m7 = a13 - a24;               // p_xx
+  const float m8 = s57 - s68;               // p_xy
+
+  float ux, uy;
+  velocity_from_j(m3, m5, c, ax, ay, rho0, ux, uy);
+  const float usq = ux * ux + uy * uy;
+  // Eq. 20 with c_s^2 / (1 - w0) = 3/5 and s0 = -2|u|^2 / (3 phi): phi p = 3/5 (sum f - 2/3 rho0 |u|^2 / phi)
+  const float phip_dev = 0.6f * (m1 - (2.0f / 3.0f) * rho0 * usq * c.inv_phi);
+  // Eq. 3
+  const float drag = c.c_lin + c.c_nl * sqrtf(usq);
+  const float Fx = -drag * ux + c.phi * ax;
+  const float Fy = -drag * uy + c.phi * ay;
+
+  // Eqs. 11-14.  m1 is conserved (m1_eq = m1, S1 = 0); m3, m5 gain rho0 F for any s3, s5.
+  const float s_e = P.s_e, s_q = P.s_q, s_v = P.s_v;
+  const float S2 = rho0 * 0.8f * (ux * Fx + uy * Fy) * c.inv_phi;
+  const float n2 = m2 - s_e * (m2 + phip_dev) + (1.0f - 0.5f * s_e) * S2;  // e_eq = -phi p
+  const float n3 = m3 + rho0 * Fx;
+  const float n4 = m4 - s_q * (m4 + rho0 * ux) - (1.0f - 0.5f * s_q) * rho0 * Fx;  // q_x,eq = -rho0 u_x
+  const float n5 = m5 + rho0 * Fy;
+  const float n6 = m6 - s_q * (m6 + rho0 * uy) - (1.0f - 0.5f * s_q) * rho0 * Fy;
+  const float hv = 1.0f - 0.5f * s_v;
+  const float n7 = m7 - s_v * (m7 - rho0 * (ux * ux - uy * uy) * c.inv_phi) + hv * 2.0f * rho0 * (ux * Fx - uy * Fy) * c.inv_phi;
+  const float n8 = m8 - s_v * (m8 - rho0 * ux * uy * c.inv_phi) + hv * rho0 * (ux * Fy + uy * Fx) * c.inv_phi;
+
+  // d+ = M^-1 m+ = M^T diag(1/8, 1/8, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4) m+
+  const float q1 = m1 * 0.125f, q2 = n2 * 0.125f;
+  const float q3 = n3 * (1.0f / 6.0f), q4 = n4 * (1.0f / 12.0f);
+  const float q5 = n5 * (1.0f / 6.0f), q6 = n6 * (1.0f / 12.0f);
+  const float q7 = n7 * 0.25f, q8 = n8 * 0.25f;
+  const float A = q1 - q2, B = q1 + q2;
+  const float X = q3 - 2.0f * q4, Y = q5 - 2.0f * q6;
+  const float Px = q3 + q4, Py = q5 + q6;
+  d[0] = A + X + q7;
+  d[1] = A + Y - q7;
+  d[2] = A - X + q7;
+  d[3] = A - Y - q7;
+  d[4] = B + Px + Py + q8;
+  d[5] = B - Px + Py - q8;
+  d[6] = B - Px - Py + q8;
+  d[7] = B + Px - Py - q8;
+  ux_out = ux;
+  uy_out = uy;
+  phip_out = phip_dev;
+}
+
+// macroscopic quantities only (no collision), for read-out kernels
+__device__ __forceinline__ Macro macro_d2q8(const float d[8], const Coef& c, float ax, float ay, float rho0) {
+  Macro r;
+  const float m1 = d[0] + d[1] + d[2] + d[3] + d[4] + d[5] + d[6] + d[7];
+  const float jx = (d[0] - d[2]) + (d[4] - d[5] - d[6] + d[7]);
+  const float jy = (d[1] - d[3]) + (d[4] + d[5] - d[6] - d[7]);
+  velocity_from_j(jx, jy, c, ax, ay, rho0, r.ux, r.uy);
+  r.dm1 = m1;
+  r.phip_dev = 0.6f * (m1 - (2.0f / 3.0f) * rho0 * (r.ux * r.ux + r.uy * r.uy) * c.inv_phi);
+  return r;
+}
+
+// Equilibrium deviation f_eq,i(p, u; phi) - f_rest,i (Eq. 22 with rho0), phip_dev = phi p - p_rest.
+__device__ __forceinline__ void feq_dev_d2q8(float phip_dev, float ux, float uy, float inv_phi, float rho0, float out[8]) {
+  const float usq15 = 1.5f * (ux * ux + uy * uy) * inv_phi;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float eu = (float)ex_of(i) * ux + (float)ey_of(i) * uy;
+    out[i] = w_of(i) * (3.0f * phip_dev + rho0 * (3.0f * eu + 4.5f * eu * eu * inv_phi - usq15));
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// D2Q5 temperature collision in deviation variables (Eq. B.2 with n_eq of Eq. B.6)
+// g[5]: deviations from T0/5, in (pre-collision) and out (post-collision); returns T.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ float collide_d2q5(float g[5], float ux, float uy, const StepParams& P) {
+  // n = N g, Eq. B.4
+  const float n0 = g[0] + g[1] + g[2] + g[3] + g[4];
+  const float n1 = g[1] - g[3];
+  const float n2 = g[2] - g[4];
+  const float side = g[1] + g[2] + g[3] + g[4];
+  const float n3 = side - 4.0f * g[0];
+  const float n4 = g[1] - g[2] + g[3] - g[4];
+  const float T = P.T0 + n0;
+  const float k1 = n1 - P.zeta1 * (n1 - ux * T * P.inv_sigma);
+  const float k2 = n2 - P.zeta1 * (n2 - uy * T * P.inv_sigma);
+  const float k3 = n3 - P.zeta3 * (n3 - P.varpi * T);
+  const float k4 = n4 - P.zeta4 * n4;
+  // g+ = N^-1 n+ = N^T diag(1/5, 1/2, 1/2, 1/20, 1/4) n+
+  const float r0 = 0.2f * n0, r1 = 0.5f * k1, r2 = 0.5f * k2, r3 = 0.05f * k3, r4 = 0.25f * k4;
+  g[0] = r0 - 4.0f * r3;
+  g[1] = r0 + r1 + r3 + r4;
+  g[2] = r0 + r2 + r3 - r4;
+  g[3] = r0 - r1 + r3 + r4;
+  g[4] = r0 - r2 + r3 - r4;
+  return T;
+}
+
+// D2Q5 velocities of Eq. B.3 (0 rest, 1..4 as D2Q8's first four)
+__device__ __forceinline__ int ex5(int i) { return i == 1 ? 1 : (i == 3 ? -1 : 0); }
+__device__ __forceinline__ int ey5(int i) { return i == 2 ? 1 : (i == 4 ? -1 : 0); }
+__device__ __forceinline__ int opp5(int i) { return i == 0 ? 0 : 1 + ((i - 1 + 2) & 3); }
+
+// ---------------------------------------------------------------------------------------------
+// generic pull of one population with every edge rule (used on edge cells and read-outs)
+// ---------------------------------------------------------------------------------------------
+// Wall that owns a link whose source (sx, sy) lies outside: y sides first (corners included).
+__device__ __forceinline__ int wall_of(int sx, int sy, int ny) {
+  if (sy < 0) return 2;
+  if (sy >= ny) return 3;
+  return sx < 0 ? 0 : 1;
+}
+
+template <int PREC>
+__device__ __forceinline__ float pull_one(const StepParams& P, const typename Store<PREC>::T* src, int x, int y, int i) {
+  using S = Store<PREC>;
+  int sx = x - ex_of(i), sy = y - ey_of(i);
+  if (P.bc_x != BC_WALL) sx = (sx + P.nx) % P.nx;
+  if (P.bc_y != BC_WALL) sy = (sy + P.ny) % P.ny;
+  if (sx >= 0 && sx < P.nx && sy >= 0 && sy < P.ny)
+    return S::dec(src[(int64_t)i * P.plane + (int64_t)sy * P.pitch + sx], P.inv_scale);
+  // halfway bounce-back: f_i(x) = f+_opp(i)(x) + 2 w_i rho0 (e_i . u_w) / c_s^2
+  const int w = wall_of(sx, sy, P.ny);
+  const int o = opp_of(i);
+  const float own = S::dec(src[(int64_t)o * P.plane + (int64_t)y * P.pitch + x], P.inv_scale);
+  return own + 6.0f * w_of(i) * P.rho0 * ((float)ex_of(i) * __ldg(P.uw + 2 * w) + (float)ey_of(i) * __ldg(P.uw + 2 * w + 1));
+}
+
+template <int PREC>
+__device__ __forceinline__ void pull_cell(const StepParams& P, const typename Store<PREC>::T* src, int x, int y, float d[8]) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) d[i] = pull_one<PREC>(P, src, x, y, i);
+}
+
+// temperature: anti-bounce-back at walls with a prescribed temperature, bounce-back otherwise
+template <int PREC>
+__device__ __forceinline__ float pull_one_g(const StepParams& P, const typename Store<PREC>::T* src, int x, int y, int i) {
+  using S = Store<PREC>;
+  if (i == 0) return S::dec(src[(int64_t)y * P.pitch + x], P.inv_scale);
+  int sx = x - ex5(i), sy = y - ey5(i);
+  if (P.bc_x != BC_WALL) sx = (sx + P.nx) % P.nx;
+  if (P.bc_y != BC_WALL) sy = (sy + P.ny) % P.ny;
+  if (sx >= 0 && sx < P.nx && sy >= 0 && sy < P.ny)
+    return S::dec(src[(int64_t)i * P.plane + (int64_t)sy * P.pitch + sx], P.inv_scale);
+  const int w = wall_of(sx, sy, P.ny);
+  const float own = S::dec(src[(int64_t)opp5(i) * P.plane + (int64_t)y * P.pitch + x], P.inv_scale);
+  // deviation form of g_i = -g+_opp + 2 T_w / 5 (reference T0 / 5): d_i = -d+_opp + 2 (T_w - T0) / 5
+  return P.Tdir[w] ? (-own + 0.4f * (P.Tw[w] - P.T0)) : own;
+}
+
+template <int PREC>
+__device__ __forceinline__ void pull_cell_g(const StepParams& P, const typename Store<PREC>::T* src, int x, int y, float g[5]) {
+#pragma unroll
+  for (int i = 0; i < 5; ++i) g[i] = pull_one_g<PREC>(P, src, x, y, i);
+}
+
+// Non-equilibrium extrapolation of a pressure column: replaces d of the cell (xb, y) by
+// f_eq(p_b, u_nb; phi_b) + f_nb - f_eq(p_nb, u_nb; phi_nb) with nb = (xb +- 1, y), in deviations.
+template <int PREC, bool HET>
+__device__ __forceinline__ void pressure_column(const StepParams& P, const typename Store<PREC>::T* src, int xb, int y, float d[8]) {
+  const int xn = xb == 0 ? 1 : P.nx - 2;
+  const float pb = xb == 0 ? P.p_in : P.p_out;
+  float dn[8];
+  pull_cell<PREC>(P, src, xn, y, dn);
+  const Coef cn = coef_at<HET>(P, xn, y);
+  const Coef cb = coef_at<HET>(P, xb, y);
+  const Macro mn = macro_d2q8(dn, cn, P.ax, P.ay, P.rho0);
+  float eb[8], en[8];
+  feq_dev_d2q8(cb.phi * pb - P.p_rest, mn.ux, mn.uy, cb.inv_phi, P.rho0, eb);
+  feq_dev_d2q8(mn.phip_dev, mn.ux, mn.uy, cn.inv_phi, P.rho0, en);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) d[i] = eb[i] + dn[i] - en[i];
+}
+
+}  // namespace lbm

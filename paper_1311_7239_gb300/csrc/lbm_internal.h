@@ -1,0 +1,28 @@
+// Host-side declarations shared by the C-ABI layer (api.cu) and the kernel files.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+constexpr int kResidualMaxBlocks = 2048;  // partial-sum slots of the residual reduction
+
+cudaError_t launch_step(const StepParams& P, int prec, bool het, bool thermal, cudaStream_t s);
+cudaError_t launch_medium(const float* eps, const float* K, float phi_u, float K_u, int nx, int ny, int pitch, float* phi_out,
+                          float* K_out, unsigned int* err, cudaStream_t s);
+cudaError_t launch_init(const StepParams& P, int prec, bool het, bool thermal, float p0, float ux0, float uy0, int phip_uniform,
+                        float T_init, bool flow, bool temp, cudaStream_t s);
+cudaError_t launch_import(const StepParams& P, int prec, const float* f, const float* g, cudaStream_t s);
+cudaError_t launch_export(const StepParams& P, int prec, bool het, bool thermal, float* f, float* g, cudaStream_t s);
+cudaError_t launch_macros(const StepParams& P, int prec, bool het, bool thermal, float* p, float* ux, float* uy, float* T,
+                          cudaStream_t s);
+cudaError_t launch_probe(const StepParams& P, int prec, bool het, bool thermal, int x, int y, float* out, cudaStream_t s);
+int residual_blocks(int nx, int ny);
+cudaError_t launch_residual(const StepParams& P, int prec, bool het, bool thermal, const void* prev, const void* gprev,
+                            double* partial, int nblocks, double* out, cudaStream_t s);
+cudaError_t launch_nusselt(const StepParams& P, int prec, int side, double* out, cudaStream_t s);
+
+}  // namespace lbm

@@ -1,0 +1,268 @@
+"""Thin ctypes binding of liblbm.so (C-ABI declared in include/lbm.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.  Arrays are
+passed as raw pointers -- torch tensors (CUDA or CPU) or numpy arrays, float32 and
+C-contiguous -- and the library tells device from host memory itself.  A missing library is an
+error (there is no CPU fallback): build it with ``python -m paper_1311_7239_gb300.build``.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "liblbm.so")
+
+ABI_VERSION = 1
+FP32, FP16_DEV, BF16_DEV = 0, 1, 2
+PERIODIC, WALL, PRESSURE = 0, 1, 2
+LEFT, RIGHT, BOTTOM, TOP = 0, 1, 2, 3
+OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, EABI, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+
+# Every function the header declares, with its ctypes signature.
+_c_ctx = ctypes.c_void_p
+_f32p = ctypes.c_void_p
+
+
+class Config(ctypes.Structure):
+    """Mirror of ``lbm_config`` (field order and types as in include/lbm.h)."""
+
+    _fields_ = [
+        ("abi_version", ctypes.c_uint32),
+        ("nx", ctypes.c_uint32),
+        ("ny", ctypes.c_uint32),
+        ("precision", ctypes.c_uint32),
+        ("bc_x", ctypes.c_uint32),
+        ("bc_y", ctypes.c_uint32),
+        ("forchheimer", ctypes.c_int32),
+        ("thermal", ctypes.c_int32),
+        ("nu", ctypes.c_double),
+        ("J", ctypes.c_double),
+        ("rho0", ctypes.c_double),
+        ("s_e", ctypes.c_double),
+        ("s_q", ctypes.c_double),
+        ("ax", ctypes.c_double),
+        ("ay", ctypes.c_double),
+        ("phi", ctypes.c_double),
+        ("K", ctypes.c_double),
+        ("u_wall", (ctypes.c_double * 2) * 4),
+        ("p_in", ctypes.c_double),
+        ("p_out", ctypes.c_double),
+        ("p_rest", ctypes.c_double),
+        ("dev_scale_log2", ctypes.c_int32),
+        ("tau_T", ctypes.c_double),
+        ("zeta3", ctypes.c_double),
+        ("zeta4", ctypes.c_double),
+        ("sigma", ctypes.c_double),
+        ("g_beta", ctypes.c_double),
+        ("T0", ctypes.c_double),
+        ("T_wall", ctypes.c_double * 4),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+SIGNATURES = {
+    "lbm_config_defaults": (None, [ctypes.POINTER(Config)]),
+    "lbm_config_size": (ctypes.c_uint32, []),
+    "lbm_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(_c_ctx)]),
+    "lbm_destroy": (None, [_c_ctx]),
+    "lbm_set_medium": (ctypes.c_int, [_c_ctx, _f32p, _f32p]),
+    "lbm_init_equilibrium": (ctypes.c_int, [_c_ctx, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int]),
+    "lbm_init_temperature": (ctypes.c_int, [_c_ctx, ctypes.c_double]),
+    "lbm_step": (ctypes.c_int, [_c_ctx, ctypes.c_int]),
+    "lbm_set_walls": (ctypes.c_int, [_c_ctx, _f32p]),
+    "lbm_probe": (ctypes.c_int, [_c_ctx, ctypes.c_int, ctypes.c_int, _f32p]),
+    "lbm_macros": (ctypes.c_int, [_c_ctx, _f32p, _f32p, _f32p, _f32p]),
+    "lbm_get_populations": (ctypes.c_int, [_c_ctx, _f32p, _f32p]),
+    "lbm_set_populations": (ctypes.c_int, [_c_ctx, _f32p, _f32p]),
+    "lbm_residual": (ctypes.c_int, [_c_ctx, ctypes.POINTER(ctypes.c_double)]),
+    "lbm_nusselt": (ctypes.c_int, [_c_ctx, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "lbm_sync": (ctypes.c_int, [_c_ctx]),
+    "lbm_step_count": (ctypes.c_int, [_c_ctx, ctypes.POINTER(ctypes.c_int64)]),
+    "lbm_memory_bytes": (ctypes.c_int, [_c_ctx, ctypes.POINTER(ctypes.c_uint64)]),
+    "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "lbm_last_error": (ctypes.c_char_p, []),
+}
+
+_LIB = None
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: {msg} (status {code})")
+        self.code = code
+
+
+def lib():
+    """The loaded liblbm.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_1311_7239_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        if L.lbm_config_size() != ctypes.sizeof(Config):
+            raise RuntimeError("lbm_config layout of the binding differs from the library's")
+        _LIB = L
+    return _LIB
+
+
+def _check(rc: int, where: str):
+    if rc != OK:
+        L = lib()
+        raise LbmError(rc, where, L.lbm_last_error().decode() or L.lbm_strerror(rc).decode())
+
+
+def _ptr(a, writable=False):
+    """Raw address of a float32 C-contiguous torch tensor or numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):  # torch
+        import torch
+
+        if a.dtype != torch.float32 or not a.is_contiguous():
+            raise TypeError("expected a contiguous float32 tensor")
+        return a.data_ptr()
+    import numpy as np
+
+    if a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError("expected a C-contiguous float32 array")
+    if writable and not a.flags["WRITEABLE"]:
+        raise TypeError("output array is read-only")
+    return a.ctypes.data
+
+
+def default_config(**kw) -> Config:
+    cfg = Config()
+    lib().lbm_config_defaults(ctypes.byref(cfg))
+    for k, v in kw.items():
+        if k == "u_wall":
+            for w, (ux, uy) in enumerate(v):
+                cfg.u_wall[w][0], cfg.u_wall[w][1] = float(ux), float(uy)
+        elif k == "T_wall":
+            for w, t in enumerate(v):
+                cfg.T_wall[w] = math.nan if t is None else float(t)
+        else:
+            setattr(cfg, k, v)
+    return cfg
+
+
+class Lattice:
+    """One lattice context (``lbm_ctx``) on the current CUDA device.
+
+    Outputs of the read-out methods are torch tensors on the context's device unless ``out``
+    arrays are given.  By default the context runs on torch's current CUDA stream.
+    """
+
+    def __init__(self, cfg: Config | None = None, **kw):
+        import torch
+
+        if cfg is None:
+            cfg = default_config(**kw)
+        if not cfg.stream:
+            cfg.stream = torch.cuda.current_stream().cuda_stream
+        self.cfg = cfg
+        self.nx, self.ny = int(cfg.nx), int(cfg.ny)
+        self.thermal = bool(cfg.thermal)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        h = ctypes.c_void_p()
+        _check(lib().lbm_create(ctypes.byref(cfg), ctypes.byref(h)), "lbm_create")
+        self._h = h
+
+    # lifetime -----------------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # set-up -------------------------------------------------------------------------------
+    def set_medium(self, eps=None, K=None):
+        _check(lib().lbm_set_medium(self._h, _ptr(eps), _ptr(K)), "lbm_set_medium")
+
+    def init_equilibrium(self, p0=1.0, ux0=0.0, uy0=0.0, phi_p_uniform=False):
+        _check(lib().lbm_init_equilibrium(self._h, p0, ux0, uy0, int(bool(phi_p_uniform))), "lbm_init_equilibrium")
+
+    def init_temperature(self, T_init):
+        _check(lib().lbm_init_temperature(self._h, T_init), "lbm_init_temperature")
+
+    # time stepping --------------------------------------------------------------------------
+    def step(self, n=1):
+        _check(lib().lbm_step(self._h, int(n)), "lbm_step")
+
+    def sync(self):
+        _check(lib().lbm_sync(self._h), "lbm_sync")
+
+    def step_count(self):
+        v = ctypes.c_int64()
+        _check(lib().lbm_step_count(self._h, ctypes.byref(v)), "lbm_step_count")
+        return v.value
+
+    def memory_bytes(self):
+        v = ctypes.c_uint64()
+        _check(lib().lbm_memory_bytes(self._h, ctypes.byref(v)), "lbm_memory_bytes")
+        return v.value
+
+    def set_walls(self, u_wall):
+        """u_wall: float32 [4, 2] (left, right, bottom, top), torch tensor or numpy array."""
+        _check(lib().lbm_set_walls(self._h, _ptr(u_wall)), "lbm_set_walls")
+
+    # read-outs ------------------------------------------------------------------------------
+    def probe(self, x, y, out=None):
+        """(p, ux, uy, T) of cell (x, y); out: float32 [4] host or device array."""
+        import numpy as np
+
+        out = np.empty(4, np.float32) if out is None else out
+        _check(lib().lbm_probe(self._h, int(x), int(y), _ptr(out, True)), "lbm_probe")
+        return out
+
+    def _new(self, *shape):
+        import torch
+
+        return torch.empty(shape, dtype=torch.float32, device=self.device)
+
+    def macros(self, p=None, ux=None, uy=None, T=None, want_T=None):
+        """(p, ux, uy[, T]) of the current pre-collision state; [ny, nx] float32 each."""
+        want_T = self.thermal if want_T is None else want_T
+        p = self._new(self.ny, self.nx) if p is None else p
+        ux = self._new(self.ny, self.nx) if ux is None else ux
+        uy = self._new(self.ny, self.nx) if uy is None else uy
+        if want_T and T is None:
+            T = self._new(self.ny, self.nx)
+        _check(lib().lbm_macros(self._h, _ptr(p, True), _ptr(ux, True), _ptr(uy, True), _ptr(T, True)), "lbm_macros")
+        return (p, ux, uy, T) if want_T else (p, ux, uy)
+
+    def get_populations(self, f=None, g=None):
+        f = self._new(8, self.ny, self.nx) if f is None else f
+        if self.thermal and g is None:
+            g = self._new(5, self.ny, self.nx)
+        _check(lib().lbm_get_populations(self._h, _ptr(f, True), _ptr(g, True)), "lbm_get_populations")
+        return (f, g) if self.thermal else f
+
+    def set_populations(self, f=None, g=None):
+        _check(lib().lbm_set_populations(self._h, _ptr(f), _ptr(g)), "lbm_set_populations")
+
+    def residual(self):
+        r = ctypes.c_double()
+        _check(lib().lbm_residual(self._h, ctypes.byref(r)), "lbm_residual")
+        return r.value
+
+    def nusselt(self, side=LEFT):
+        v = ctypes.c_double()
+        _check(lib().lbm_nusselt(self._h, int(side), ctypes.byref(v)), "lbm_nusselt")
+        return v.value

@@ -1,0 +1,189 @@
+"""GPU parity of the fused stream-collide path (through the C-ABI) against the FP64 oracle.
+
+Bar (FP32 storage): one step from an arbitrary state matches the oracle element by element to
+FP32 rounding (|df| <= 2e-6 absolute on populations of size ~0.1-1), and trajectories of
+hundreds to thousands of steps match in relative L2 of u and p to <= 1e-5.
+"""
+import numpy as np
+import pytest
+
+from oracle import mrt_d2q8 as fl
+from oracle import thermal_d2q5 as th
+from tests.cases import Case, rel_l2, random_state, to_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1311_7239_gb300 import build, lbm
+
+    build.build()
+    return lbm
+
+
+CAV = {"top": (0.1, 0.0)}
+ONE_STEP_CASES = {
+    "periodic-periodic-uniform": Case(16, 12, bc_x="periodic", bc_y="periodic", ax=2e-4, ay=-1e-4),
+    "channel-lid-het": Case(33, 17, bc_x="periodic", bc_y="wall", walls={"top": (0.05, 0.0)}, het=True, ax=1e-4),
+    "cavity-moving-walls-het": Case(37, 21, bc_x="wall", bc_y="wall", het=True,
+                                    walls={"top": (0.1, 0.0), "bottom": (0.0, 0.01), "left": (0.0, 0.02), "right": (0.0, -0.03)}),
+    "cavity-ragged-3-tiles": Case(1100, 6, bc_x="wall", bc_y="wall", walls=CAV, phi=0.7, K=5.0),
+    "wall-x-periodic-y": Case(20, 9, bc_x="wall", bc_y="periodic", walls={"left": (0.0, 0.05)}, forch=False),
+    "pressure-het": Case(41, 13, bc_x="pressure", bc_y="wall", het=True, p_in=1.01, p_out=0.99),
+    "tiny-2x3": Case(2, 3, bc_x="periodic", bc_y="wall", walls=CAV),
+    "tiny-3x2-walls": Case(3, 2, bc_x="wall", bc_y="wall", walls=CAV),
+    "brinkman-no-forch": Case(64, 8, forch=False, phi=0.1, K=40.96, ax=1e-5),
+}
+
+
+@pytest.mark.parametrize("name", list(ONE_STEP_CASES))
+def test_one_step_matches_oracle_elementwise(lbm, name):
+    case = ONE_STEP_CASES[name]
+    flow = case.flow()
+    f0 = random_state(flow, seed=11)
+    with case.lattice(lbm) as lat:
+        lat.set_populations(to_gpu(f0))
+        back = lat.get_populations().cpu().numpy()
+        # import/export of a pre-collision state is the identity (pressure columns recomputed)
+        assert np.abs(back - f0).max() <= 2e-6
+        lat.step(1)
+        got = lat.get_populations().cpu().numpy()
+        lat.sync()
+    want = fl.step(f0, flow)
+    err = np.abs(got - want).max()
+    assert err <= 2e-6, f"{name}: max |df| = {err:.3e}"
+
+
+def test_init_equilibrium_matches_oracle(lbm):
+    for phip in (False, True):
+        case = Case(50, 30, bc_x="wall", bc_y="wall", walls=CAV, het=True)
+        flow = case.flow()
+        p0 = 1.0 / flow.phi if phip else 1.0
+        want = fl.initial_state(flow, p0=p0, u0=(0.01, -0.02))
+        with case.lattice(lbm) as lat:
+            lat.init_equilibrium(1.0, 0.01, -0.02, phi_p_uniform=phip)
+            got = lat.get_populations().cpu().numpy()
+        assert np.abs(got - want).max() <= 2e-6
+
+
+def _trajectory(lbm, case, steps, check_every=None):
+    flow = case.flow()
+    f = fl.initial_state(flow)
+    with case.lattice(lbm) as lat:
+        lat.step(steps)
+        p, ux, uy = [t.cpu().numpy() for t in lat.macros()]
+        lat.sync()
+    f = fl.run(f, flow, steps)
+    uxo, uyo, po = fl.macroscopic(f, flow)
+    e_u = rel_l2(np.stack([ux, uy]), np.stack([uxo, uyo]))
+    e_p = rel_l2(p, po)
+    return e_u, e_p
+
+
+def test_poiseuille_64_trajectory(lbm):
+    """Porous Poiseuille channel: 64x64, eps = 0.1, Da = 0.01, nu = 0.1, Re = 10 body force (Sec. 3.1)."""
+    H, phi, nu = 64, 0.1, 0.1
+    K = 0.01 * H * H
+    th_ = np.sqrt(phi / K)
+    G = (10 * nu / H) * nu / (K * (1 - 1 / np.cosh(th_ * H / 2)))
+    e_u, e_p = _trajectory(lbm, Case(H, H, nu=nu, phi=phi, K=K, forch=False, ax=G), 1500)
+    assert e_u <= 1e-5 and e_p <= 1e-5, (e_u, e_p)
+
+
+def test_lid_cavity_trajectory(lbm):
+    """Lid-driven porous cavity (Sec. 3.3 set-up, halfway walls): eps = 0.4, Da = 1e-3, Re = 100."""
+    L = 96
+    e_u, e_p = _trajectory(lbm, Case(L, L, nu=0.1 * L / 100, phi=0.4, K=1e-3 * L * L, bc_x="wall", bc_y="wall", walls=CAV), 800)
+    assert e_u <= 1e-5 and e_p <= 1e-5, (e_u, e_p)
+
+
+def test_heterogeneous_pressure_channel_trajectory(lbm):
+    case = Case(96, 48, nu=0.1, phi=0.3, K=1e-3 * 48 * 48, het=True, bc_x="pressure", bc_y="wall", p_in=1.005, p_out=0.995)
+    e_u, e_p = _trajectory(lbm, case, 600)
+    assert e_u <= 1e-5 and e_p <= 1e-5, (e_u, e_p)
+
+
+def _thermal_case(L=48, prec=0, Ra=1e4):
+    nu, tau_v, tau_T, gb = th.parameters_from_Ra(L, Ra, 1.0, 0.1)
+    return Case(L, L, nu=nu, phi=0.6, K=1e-2 * L * L, bc_x="wall", bc_y="wall", precision=prec,
+                thermal=dict(tau_T=tau_T, g_beta=gb, T0=11.0, T_left=21.0, T_right=1.0))
+
+
+def test_natural_convection_trajectory_and_nusselt(lbm):
+    case = _thermal_case()
+    flow, tp = case.flow(), case.thermal_params()
+    f, g = fl.initial_state(flow), th.initial_state(flow, tp)
+    steps = 600
+    with case.lattice(lbm) as lat:
+        lat.step(steps)
+        p, ux, uy, T = [t.cpu().numpy() for t in lat.macros()]
+        nu_l, nu_r = lat.nusselt(0), lat.nusselt(1)
+    for _ in range(steps):
+        f, g = th.coupled_step(f, g, flow, tp)
+    uxo, uyo, po, To = th.coupled_macroscopic(f, g, flow, tp)
+    assert rel_l2(np.stack([ux, uy]), np.stack([uxo, uyo])) <= 1e-5
+    assert rel_l2(T, To) <= 1e-6
+    assert rel_l2(p, po) <= 1e-5
+    nu_o = th.nusselt_left_wall(To, 21.0, 21.0, 1.0, case.nx)
+    assert abs(nu_l - nu_o) <= 1e-5 * abs(nu_o)
+    # right wall: mirror of the same formula
+    Tm = To[:, ::-1]
+    nu_or = th.nusselt_left_wall(Tm, 1.0, 1.0, 21.0, case.nx)
+    assert abs(nu_r - nu_or) <= 1e-5 * abs(nu_or)
+
+
+def test_residual_matches_oracle(lbm):
+    case = Case(40, 30, nu=0.05, phi=0.5, K=2.0, bc_x="wall", bc_y="wall", walls=CAV)
+    flow = case.flow()
+    f = fl.run(fl.initial_state(flow), flow, 59)
+    u_prev = fl.macroscopic(f, flow)[:2]
+    f = fl.step(f, flow)
+    u_now = fl.macroscopic(f, flow)[:2]
+    want = fl.residual(u_now[0], u_now[1], u_prev[0], u_prev[1])
+    with case.lattice(lbm) as lat:
+        lat.step(60)
+        got = lat.residual()
+    assert abs(got - want) <= 1e-3 * want, (got, want)
+
+
+def test_errors_are_reported(lbm):
+    import torch
+
+    case = Case(16, 8)
+    with case.lattice(lbm) as lat:
+        with pytest.raises(lbm.LbmError) as e:
+            lat.residual()  # no step taken yet
+        assert e.value.code == lbm.ESTATE
+        bad = torch.zeros(8, 16, dtype=torch.float32, device="cuda")
+        with pytest.raises(lbm.LbmError) as e:
+            lat.set_medium(bad, None)
+        assert e.value.code == lbm.EINVAL
+        f = torch.full((8, 8, 16), float("nan"), device="cuda")
+        lat.set_populations(f)
+        lat.step(2)
+        with pytest.raises(lbm.LbmError) as e:
+            lat.sync()
+        assert e.value.code == lbm.EUNSTABLE
+
+
+def test_host_pointers_round_trip(lbm):
+    """Host (numpy) arrays in and out give the same result as device tensors."""
+    case = Case(30, 20, bc_x="wall", bc_y="wall", walls=CAV, het=True)
+    flow = case.flow()
+    f0 = random_state(flow, seed=3).astype(np.float32)
+    with case.lattice(lbm) as lat:
+        lat.set_populations(f0)
+        lat.step(3)
+        out_h = np.empty((8, 20, 30), np.float32)
+        lat.get_populations(f=out_h)
+        out_d = lat.get_populations().cpu().numpy()
+        p_h, ux_h, uy_h = (np.empty((20, 30), np.float32) for _ in range(3))
+        lat.macros(p_h, ux_h, uy_h)
+        p_d, ux_d, uy_d = (t.cpu().numpy() for t in lat.macros())
+    assert np.array_equal(out_h, out_d)
+    assert np.array_equal(ux_h, ux_d) and np.array_equal(p_h, p_d)
