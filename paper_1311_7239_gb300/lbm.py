@@ -18,6 +18,7 @@ ABI_VERSION = 1
 FP32, FP16_DEV, BF16_DEV = 0, 1, 2
 PERIODIC, WALL, PRESSURE = 0, 1, 2
 LEFT, RIGHT, BOTTOM, TOP = 0, 1, 2, 3
+CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, EABI, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 
 # Every function the header declares, with its ctypes signature.
@@ -164,7 +165,9 @@ class Lattice:
         if cfg is None:
             cfg = default_config(**kw)
         if not cfg.stream:
-            cfg.stream = torch.cuda.current_stream().cuda_stream
+            # torch's default stream is the legacy default stream (handle 0); pass
+            # cudaStreamLegacy (handle 1) so the library orders its work with torch's.
+            cfg.stream = torch.cuda.current_stream().cuda_stream or CUDA_STREAM_LEGACY
         self.cfg = cfg
         self.nx, self.ny = int(cfg.nx), int(cfg.ny)
         self.thermal = bool(cfg.thermal)

@@ -21,6 +21,8 @@ class Case:
     phi: float = 0.4
     K: float = 10.0
     het: bool = False           # per-cell random medium
+    eps_sd: float = 0.1         # porosity spread of the random medium
+    corr: float = 0.0           # correlation length of the random medium (0: ny / 8)
     forch: bool = True
     ax: float = 0.0
     ay: float = 0.0
@@ -37,7 +39,7 @@ class Case:
         if not self.het:
             return np.full((self.ny, self.nx), self.phi), np.full((self.ny, self.nx), self.K)
         eps, K = synth.heterogeneous_medium(self.ny, self.nx, H=self.ny, seed=self.seed, da_mean=self.K / self.ny**2,
-                                            corr_len=max(2.0, self.ny / 8), eps_mean=self.phi, eps_sd=0.1, eps_lo=0.1,
+                                            corr_len=self.corr or max(2.0, self.ny / 8), eps_mean=self.phi, eps_sd=self.eps_sd, eps_lo=0.1,
                                             eps_hi=0.95)
         # the GPU stores float32 fields: give the oracle the same values
         return eps.astype(np.float32).astype(np.float64), K.astype(np.float32).astype(np.float64)

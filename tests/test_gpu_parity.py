@@ -71,10 +71,14 @@ def test_init_equilibrium_matches_oracle(lbm):
         assert np.abs(got - want).max() <= 2e-6
 
 
-def _trajectory(lbm, case, steps, check_every=None):
+def _trajectory(lbm, case, steps, phip_uniform=None):
+    """Run both sides from the equilibrium initial state; phip_uniform = c starts from the rest
+    state phi p = c (p = c / phi), else from p = 1."""
     flow = case.flow()
-    f = fl.initial_state(flow)
+    f = fl.initial_state(flow, p0=1.0 if phip_uniform is None else phip_uniform / flow.phi)
     with case.lattice(lbm) as lat:
+        if phip_uniform is not None:
+            lat.init_equilibrium(phip_uniform, 0.0, 0.0, phi_p_uniform=True)
         lat.step(steps)
         p, ux, uy = [t.cpu().numpy() for t in lat.macros()]
         lat.sync()
@@ -103,8 +107,9 @@ def test_lid_cavity_trajectory(lbm):
 
 
 def test_heterogeneous_pressure_channel_trajectory(lbm):
-    case = Case(96, 48, nu=0.1, phi=0.3, K=1e-3 * 48 * 48, het=True, bc_x="pressure", bc_y="wall", p_in=1.005, p_out=0.995)
-    e_u, e_p = _trajectory(lbm, case, 600)
+    case = Case(96, 48, nu=0.1, phi=0.3, K=1e-3 * 48 * 48, het=True, eps_sd=0.03, corr=12.0, bc_x="pressure", bc_y="wall",
+                p_in=1.002, p_out=0.998)
+    e_u, e_p = _trajectory(lbm, case, 600, phip_uniform=case.p_rest())
     assert e_u <= 1e-5 and e_p <= 1e-5, (e_u, e_p)
 
 
@@ -187,3 +192,33 @@ def test_host_pointers_round_trip(lbm):
         p_d, ux_d, uy_d = (t.cpu().numpy() for t in lat.macros())
     assert np.array_equal(out_h, out_d)
     assert np.array_equal(ux_h, ux_d) and np.array_equal(p_h, p_d)
+
+
+@pytest.mark.parametrize("prec,bound", [(1, 1e-3), (2, 1e-2)])
+def test_reduced_precision_storage_error(lbm, prec, bound):
+    """FP16 / BF16 storage of f - f_rest with FP32 arithmetic: relative L2 error of u and p vs the
+    FP64 oracle on the lid-driven cavity (bound 1e-3 for FP16; BF16's 8-bit mantissa is reported
+    against a looser 1e-2)."""
+    L = 96
+    case = Case(L, L, nu=0.1 * L / 100, phi=0.4, K=1e-3 * L * L, bc_x="wall", bc_y="wall", walls=CAV, precision=prec)
+    e_u, e_p = _trajectory(lbm, case, 800)
+    print(f"precision {prec}: rel-L2 u {e_u:.3e}, p {e_p:.3e}")
+    assert e_u <= bound and e_p <= bound, (e_u, e_p)
+
+
+@pytest.mark.parametrize("prec,bound", [(1, 1e-3), (2, 1e-2)])
+def test_reduced_precision_thermal_error(lbm, prec, bound):
+    case = _thermal_case(prec=prec)
+    flow, tp = case.flow(), case.thermal_params()
+    f, g = fl.initial_state(flow), th.initial_state(flow, tp)
+    steps = 600
+    with case.lattice(lbm) as lat:
+        lat.step(steps)
+        p, ux, uy, T = [t.cpu().numpy() for t in lat.macros()]
+    for _ in range(steps):
+        f, g = th.coupled_step(f, g, flow, tp)
+    uxo, uyo, po, To = th.coupled_macroscopic(f, g, flow, tp)
+    e_u = rel_l2(np.stack([ux, uy]), np.stack([uxo, uyo]))
+    e_T = rel_l2(T - 11.0, To - 11.0)
+    print(f"precision {prec}: rel-L2 u {e_u:.3e}, T-T0 {e_T:.3e}")
+    assert e_u <= bound and e_T <= bound, (e_u, e_T)
