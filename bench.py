@@ -150,6 +150,46 @@ def run_reference(args, rank, world):
     return 0
 
 
+def make_lattice(lbm, L, prec, stream):
+    prm = cavity_params(L)
+    cfg = lbm.default_config(nx=L, ny=L, bc_x=lbm.WALL, bc_y=lbm.WALL, nu=prm["nu"], phi=prm["phi"], K=prm["K"],
+                             u_wall=[(0, 0), (0, 0), (0, 0), (prm["lid"], 0)], precision=PREC[prec], p_rest=prm["phi"],
+                             dev_scale_log2=10)
+    cfg.stream = stream.cuda_stream
+    return lbm.Lattice(cfg)
+
+
+def timed_steps(lbm, L, prec, steps, warmup, local_rank, dist=None):
+    """(ms for `steps` steps, clock summary, lattice) with CUDA events on the lattice's stream."""
+    import torch
+
+    stream = torch.cuda.Stream()
+    lat = make_lattice(lbm, L, prec, stream)
+    lat.step(warmup)
+    lat.sync()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        start.record(stream)
+        lat.step(steps)
+        stop.record(stream)
+        stop.synchronize()
+    torch.cuda.synchronize()
+    lat.sync()
+    return start.elapsed_time(stop), clk.summary(), lat
+
+
+def accuracy_record():
+    """Relative L2 errors vs the FP64 oracle measured by the GPU parity tests (committed record)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "accuracy.json")) as fh:
+            return json.load(fh)
+    except Exception:
+        return None
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
 
@@ -164,28 +204,7 @@ def run_gpu(args, rank, world, local_rank):
     L = args.size
     prm = cavity_params(L)
     prec = args.precision
-    stream = torch.cuda.Stream()
-    cfg = lbm.default_config(nx=L, ny=L, bc_x=lbm.WALL, bc_y=lbm.WALL, nu=prm["nu"], phi=prm["phi"], K=prm["K"],
-                             u_wall=[(0, 0), (0, 0), (0, 0), (prm["lid"], 0)], precision=PREC[prec], p_rest=prm["phi"],
-                             dev_scale_log2=10)
-    cfg.stream = stream.cuda_stream
-    lat = lbm.Lattice(cfg)
-    # warm-up (untimed)
-    with torch.cuda.stream(stream):
-        lat.step(args.warmup)
-    lat.sync()
-    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local_rank) as clk:
-        start.record(stream)
-        lat.step(args.steps)
-        stop.record(stream)
-        stop.synchronize()
-    torch.cuda.synchronize()
-    ms = start.elapsed_time(stop)
-    lat.sync()
+    ms, clocks, lat = timed_steps(lbm, L, prec, args.steps, args.warmup, local_rank, dist)
     if dist:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -211,9 +230,20 @@ def run_gpu(args, rank, world, local_rank):
     e2e_mlups = cells * e2e_steps * world / e2e_s / 1e6
     lat.close()
 
+    peak, peak_kind = peaks()
+    forms = {}
+    if not args.no_forms:
+        for other in PREC:
+            if other == prec:
+                continue
+            ms_o, clk_o, lat_o = timed_steps(lbm, L, other, max(3, args.steps // 2), args.warmup, local_rank, dist)
+            lat_o.close()
+            bw = BYTES_PER_LU[other] * cells / (ms_o * 1e-3 / max(3, args.steps // 2)) / 1e9
+            forms[other] = {"value": cells * max(3, args.steps // 2) / (ms_o * 1e-3) / 1e6, "unit": "MLUPS",
+                            "roofline_frac": bw / peak, "achieved_gbs": bw, "algorithmic_bytes_per_lu": BYTES_PER_LU[other],
+                            "clocks": clk_o}
     if rank != 0:
         return 0
-    peak, peak_kind = peaks()
     bpl = BYTES_PER_LU[prec]
     achieved = bpl * cells / (ms * 1e-3 / args.steps) / 1e9
     kernel_key = f"k_step_{prec}_uniform_{L}"
@@ -234,8 +264,13 @@ def run_gpu(args, rank, world, local_rank):
         "e2e": {"value": e2e_mlups, "unit": "MLUPS", "h2d_bytes_per_step": int(walls.numel() * 4),
                 "d2h_bytes_per_step": int(probe.numel() * 4), "steps": e2e_steps,
                 "call": "lbm_set_walls(host) + lbm_step(1) + lbm_probe(host) per step"},
-        "clocks": clk.summary(),
+        "clocks": clocks,
     }
+    if not args.no_forms:
+        line["forms"] = forms
+    acc = accuracy_record()
+    if acc:
+        line["accuracy"] = acc
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(L)
     print(json.dumps(line), flush=True)
@@ -251,6 +286,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=list(PREC))
     ap.add_argument("--size", type=int, default=4096)
     ap.add_argument("--no-cpu", action="store_true", help="skip the timed CPU oracle baseline")
+    ap.add_argument("--no-forms", action="store_true", help="skip the other storage precisions and accuracy checks")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

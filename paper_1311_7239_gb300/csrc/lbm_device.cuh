@@ -176,10 +176,8 @@ __device__ __forceinline__ void collide_d2q8(float d[8], const Coef& c, float ax
   const float m2 = -(a13 + a24) + diag;     // e      (deviation)
   const float dxs = t57 - t68;              // e_x-weighted diagonal sum
   const float dys = t57 + t68;              // e_y-weighted diagonal sum
-  const float m3 = d13 + dxs;               // j_x
-  const float m4 = -2.0f * d13 + dxs;       // q_x
-  const float m5 = d24 + dys;               // j_y
-  const float m6 = -2.0f * d24 + dys;       // q_y
+  const float m3 = d13 + dxs;               // j_x  (q_x = -2 d13 + dxs enters k4 below)
+  const float m5 = d24 + dys;               // j_y  (q_y = -2 d24 + dys enters k6 below)
   const float m7 = a13 - a24;               // p_xx
   const float m8 = s57 - s68;               // p_xy
 
@@ -193,34 +191,38 @@ __device__ __forceinline__ void collide_d2q8(float d[8], const Coef& c, float ax
   const float Fx = -drag * ux + c.phi * ax;
   const float Fy = -drag * uy + c.phi * ay;
 
-  // Eqs. 11-14.  m1 is conserved (m1_eq = m1, S1 = 0); m3, m5 gain rho0 F for any s3, s5.
+  // Eqs. 11-14 as increments k = m+ - m = -Lambda (m - m_eq) + (I - Lambda/2) S.  m1 is conserved
+  // (m1_eq = m1, S1 = 0); m3, m5 gain rho0 F for any s3, s5.  The q moments relax towards
+  // -rho0 u, and m4 + rho0 u_x = (m4 + m3) + rho0 F_x / 2 by Eq. 17: that form avoids subtracting
+  // two O(u) numbers.  Adding the increments to the pulled populations (instead of rebuilding
+  // them from m+) keeps FP32 rounding at about one unit of d per step.
   const float s_e = P.s_e, s_q = P.s_q, s_v = P.s_v;
+  const float rFx = rho0 * Fx, rFy = rho0 * Fy;
   const float S2 = rho0 * 0.8f * (ux * Fx + uy * Fy) * c.inv_phi;
-  const float n2 = m2 - s_e * (m2 + phip_dev) + (1.0f - 0.5f * s_e) * S2;  // e_eq = -phi p
-  const float n3 = m3 + rho0 * Fx;
-  const float n4 = m4 - s_q * (m4 + rho0 * ux) - (1.0f - 0.5f * s_q) * rho0 * Fx;  // q_x,eq = -rho0 u_x
-  const float n5 = m5 + rho0 * Fy;
-  const float n6 = m6 - s_q * (m6 + rho0 * uy) - (1.0f - 0.5f * s_q) * rho0 * Fy;
+  const float k2 = -s_e * (m2 + phip_dev) + (1.0f - 0.5f * s_e) * S2;  // e_eq = -phi p
+  const float k3 = rFx;
+  const float k4 = -s_q * ((2.0f * dxs - d13) + 0.5f * rFx) - (1.0f - 0.5f * s_q) * rFx;
+  const float k5 = rFy;
+  const float k6 = -s_q * ((2.0f * dys - d24) + 0.5f * rFy) - (1.0f - 0.5f * s_q) * rFy;
   const float hv = 1.0f - 0.5f * s_v;
-  const float n7 = m7 - s_v * (m7 - rho0 * (ux * ux - uy * uy) * c.inv_phi) + hv * 2.0f * rho0 * (ux * Fx - uy * Fy) * c.inv_phi;
-  const float n8 = m8 - s_v * (m8 - rho0 * ux * uy * c.inv_phi) + hv * rho0 * (ux * Fy + uy * Fx) * c.inv_phi;
+  const float k7 = -s_v * (m7 - rho0 * (ux * ux - uy * uy) * c.inv_phi) + hv * 2.0f * rho0 * (ux * Fx - uy * Fy) * c.inv_phi;
+  const float k8 = -s_v * (m8 - rho0 * ux * uy * c.inv_phi) + hv * rho0 * (ux * Fy + uy * Fx) * c.inv_phi;
 
-  // d+ = M^-1 m+ = M^T diag(1/8, 1/8, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4) m+
-  const float q1 = m1 * 0.125f, q2 = n2 * 0.125f;
-  const float q3 = n3 * (1.0f / 6.0f), q4 = n4 * (1.0f / 12.0f);
-  const float q5 = n5 * (1.0f / 6.0f), q6 = n6 * (1.0f / 12.0f);
-  const float q7 = n7 * 0.25f, q8 = n8 * 0.25f;
-  const float A = q1 - q2, B = q1 + q2;
+  // d+ = d + M^-1 k, M^-1 = M^T diag(1/8, 1/8, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4), k1 = 0
+  const float q2 = k2 * 0.125f;
+  const float q3 = k3 * (1.0f / 6.0f), q4 = k4 * (1.0f / 12.0f);
+  const float q5 = k5 * (1.0f / 6.0f), q6 = k6 * (1.0f / 12.0f);
+  const float q7 = k7 * 0.25f, q8 = k8 * 0.25f;
   const float X = q3 - 2.0f * q4, Y = q5 - 2.0f * q6;
   const float Px = q3 + q4, Py = q5 + q6;
-  d[0] = A + X + q7;
-  d[1] = A + Y - q7;
-  d[2] = A - X + q7;
-  d[3] = A - Y - q7;
-  d[4] = B + Px + Py + q8;
-  d[5] = B - Px + Py - q8;
-  d[6] = B - Px - Py + q8;
-  d[7] = B + Px - Py - q8;
+  d[0] += (X + q7) - q2;
+  d[1] += (Y - q7) - q2;
+  d[2] += (q7 - X) - q2;
+  d[3] += (-Y - q7) - q2;
+  d[4] += (Px + Py + q8) + q2;
+  d[5] += (Py - Px - q8) + q2;
+  d[6] += (q8 - Px - Py) + q2;
+  d[7] += (Px - Py - q8) + q2;
   ux_out = ux;
   uy_out = uy;
   phip_out = phip_dev;
@@ -261,17 +263,17 @@ __device__ __forceinline__ float collide_d2q5(float g[5], float ux, float uy, co
   const float n3 = side - 4.0f * g[0];
   const float n4 = g[1] - g[2] + g[3] - g[4];
   const float T = P.T0 + n0;
-  const float k1 = n1 - P.zeta1 * (n1 - ux * T * P.inv_sigma);
-  const float k2 = n2 - P.zeta1 * (n2 - uy * T * P.inv_sigma);
-  const float k3 = n3 - P.zeta3 * (n3 - P.varpi * T);
-  const float k4 = n4 - P.zeta4 * n4;
-  // g+ = N^-1 n+ = N^T diag(1/5, 1/2, 1/2, 1/20, 1/4) n+
-  const float r0 = 0.2f * n0, r1 = 0.5f * k1, r2 = 0.5f * k2, r3 = 0.05f * k3, r4 = 0.25f * k4;
-  g[0] = r0 - 4.0f * r3;
-  g[1] = r0 + r1 + r3 + r4;
-  g[2] = r0 + r2 + r3 - r4;
-  g[3] = r0 - r1 + r3 + r4;
-  g[4] = r0 - r2 + r3 - r4;
+  // increments n+ - n (n0 conserved), then g+ = g + N^-1 (n+ - n) with
+  // N^-1 = N^T diag(1/5, 1/2, 1/2, 1/20, 1/4)
+  const float r1 = -0.5f * P.zeta1 * (n1 - ux * T * P.inv_sigma);
+  const float r2 = -0.5f * P.zeta1 * (n2 - uy * T * P.inv_sigma);
+  const float r3 = -0.05f * P.zeta3 * (n3 - P.varpi * T);
+  const float r4 = -0.25f * P.zeta4 * n4;
+  g[0] += -4.0f * r3;
+  g[1] += (r1 + r3) + r4;
+  g[2] += (r2 + r3) - r4;
+  g[3] += (r3 - r1) + r4;
+  g[4] += (r3 - r2) - r4;
   return T;
 }
 
