@@ -213,6 +213,7 @@ void fill_base(lbm_ctx* c) {
   P.bc_y = (int)k.bc_y;
   P.forch = k.forchheimer ? 1 : 0;
   P.rho0 = (float)k.rho0;
+  P.inv_rho0 = (float)(1.0 / k.rho0);
   P.nu = (float)k.nu;
   P.s_e = (float)k.s_e;
   P.s_q = (float)k.s_q;

@@ -35,7 +35,7 @@ struct StepParams {
   int64_t plane;     // elements per plane = ny * pitch
   int bc_x, bc_y;
   int forch;
-  float rho0, nu, s_e, s_q, s_v;
+  float rho0, inv_rho0, nu, s_e, s_q, s_v;
   float ax, ay;
   // uniform-medium coefficients
   float phi_u, inv_phi_u, c_lin_u, c_nl_u;
@@ -120,6 +120,11 @@ struct Coef {
   float c_nl;   // phi F_phi / sqrt(K)  (Forchheimer drag of Eq. 3; = 1.75 / sqrt(150 phi K) by Eq. 4)
 };
 
+// Reciprocal and square root through the SFU approximations (a few ulp), which the FP32 error
+// budget of the method tolerates; sqrt of 0 is 0.
+__device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ float fast_sqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+
 template <bool HET>
 __device__ __forceinline__ Coef coef_at(const StepParams& P, int x, int y) {
   Coef c;
@@ -130,8 +135,8 @@ __device__ __forceinline__ Coef coef_at(const StepParams& P, int x, int y) {
     const float ph = __ldg(P.phi + o);
     const float k = __ldg(P.K + o);
     c.phi = ph;
-    c.inv_phi = 1.0f / ph;
-    c.c_lin = ph * P.nu / k;
+    c.inv_phi = fast_rcp(ph);
+    c.c_lin = ph * P.nu * fast_rcp(k);
     c.c_nl = P.forch ? 1.75f * rsqrtf(150.0f * ph * k) : 0.0f;
   }
   return c;
@@ -146,18 +151,20 @@ struct Macro {
   float phip_dev;  // phi p - p_rest, Eq. 20
 };
 
+// Eqs. 18-19; also returns |u| = |v| / (l0 + sqrt(l0^2 + l1 |v|)) for the Forchheimer drag.
 __device__ __forceinline__ void velocity_from_j(float jx, float jy, const Coef& c, float ax, float ay,
-                                                float rho0, float& ux, float& uy) {
-  // Eq. 19: v = sum e f / rho0 + phi a / 2 ; l0 = (1 + phi nu / (2K)) / 2 ; l1 = phi F_phi / (2 sqrt K)
-  const float vx = jx / rho0 + 0.5f * c.phi * ax;
-  const float vy = jy / rho0 + 0.5f * c.phi * ay;
+                                                float inv_rho0, float& ux, float& uy, float& umag) {
+  // v = sum e f / rho0 + phi a / 2 ; l0 = (1 + phi nu / (2K)) / 2 ; l1 = phi F_phi / (2 sqrt K)
+  const float vx = jx * inv_rho0 + 0.5f * c.phi * ax;
+  const float vy = jy * inv_rho0 + 0.5f * c.phi * ay;
   const float l0 = 0.5f + 0.25f * c.c_lin;
   const float l1 = 0.5f * c.c_nl;
-  const float vmag = sqrtf(vx * vx + vy * vy);
+  const float vmag = fast_sqrt(vx * vx + vy * vy);
   // Eq. 18, the cancellation-free root of l1 |u|^2 + 2 l0 |u| - |v| = 0
-  const float inv = 1.0f / (l0 + sqrtf(l0 * l0 + l1 * vmag));
+  const float inv = fast_rcp(l0 + fast_sqrt(l0 * l0 + l1 * vmag));
   ux = vx * inv;
   uy = vy * inv;
+  umag = vmag * inv;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -181,13 +188,13 @@ __device__ __forceinline__ void collide_d2q8(float d[8], const Coef& c, float ax
   const float m7 = a13 - a24;               // p_xx
   const float m8 = s57 - s68;               // p_xy
 
-  float ux, uy;
-  velocity_from_j(m3, m5, c, ax, ay, rho0, ux, uy);
+  float ux, uy, umag;
+  velocity_from_j(m3, m5, c, ax, ay, P.inv_rho0, ux, uy, umag);
   const float usq = ux * ux + uy * uy;
   // Eq. 20 with c_s^2 / (1 - w0) = 3/5 and s0 = -2|u|^2 / (3 phi): phi p = 3/5 (sum f - 2/3 rho0 |u|^2 / phi)
   const float phip_dev = 0.6f * (m1 - (2.0f / 3.0f) * rho0 * usq * c.inv_phi);
   // Eq. 3
-  const float drag = c.c_lin + c.c_nl * sqrtf(usq);
+  const float drag = c.c_lin + c.c_nl * umag;
   const float Fx = -drag * ux + c.phi * ax;
   const float Fy = -drag * uy + c.phi * ay;
 
@@ -234,7 +241,8 @@ __device__ __forceinline__ Macro macro_d2q8(const float d[8], const Coef& c, flo
   const float m1 = d[0] + d[1] + d[2] + d[3] + d[4] + d[5] + d[6] + d[7];
   const float jx = (d[0] - d[2]) + (d[4] - d[5] - d[6] + d[7]);
   const float jy = (d[1] - d[3]) + (d[4] + d[5] - d[6] - d[7]);
-  velocity_from_j(jx, jy, c, ax, ay, rho0, r.ux, r.uy);
+  float umag;
+  velocity_from_j(jx, jy, c, ax, ay, fast_rcp(rho0), r.ux, r.uy, umag);
   r.dm1 = m1;
   r.phip_dev = 0.6f * (m1 - (2.0f / 3.0f) * rho0 * (r.ux * r.ux + r.uy * r.uy) * c.inv_phi);
   return r;

@@ -1,12 +1,13 @@
-// Fused stream-collide kernels of the porous D2Q8 MRT-LB method (Liu & He, arXiv 1311.7239,
+// Fused stream-collide kernel of the porous D2Q8 MRT-LB method (Liu & He, arXiv 1311.7239,
 // Eqs. 6-20) with the optional D2Q5 temperature equation (Appendix B) in the same pass.
 //
-// Layout and work split: planes [q][ny][pitch] with pitch a multiple of 128 elements; one CTA of
-// 128 threads covers 512 consecutive cells of one row, each thread four consecutive cells.  The
-// populations with e_x = 0 are read as aligned vectors; the six with e_x = +-1 are read as the
-// same aligned vectors of the source row and shifted by one cell through a warp shuffle (the
-// warp's first or last lane reads its one extra cell).  Cells on a wall row, on the first or
-// last column, or next to a pressure column recompute their gathers with the generic edge rules.
+// Layout and work split: planes [q][ny][pitch] with pitch a multiple of 128 elements; a thread
+// updates a group of four consecutive cells of one row, a CTA of 128 threads covers 512 cells.
+// The populations with e_x = 0 are read as aligned vectors; the six with e_x = +-1 are read as
+// the same aligned vectors of the source row and shifted by one cell through a warp shuffle (the
+// warp's first or last lane reads its one extra cell).  The interior path has no boundary logic:
+// the groups that touch a wall row or the first/last column (the "frame", a few cells per row)
+// are done by the launch's first blocks with the generic boundary rules, and skipped by the rest.
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
 
@@ -36,30 +37,119 @@ __device__ __forceinline__ void gather4(const typename Store<PREC>::T* __restric
   }
 }
 
+// Frame of the lattice: the groups of C cells that contain a wall-row cell or a cell of the first
+// or last column (the last group of a row also holds the row padding).  Their cells are gathered
+// with every boundary rule (pull_one: halfway bounce-back with wall velocity, periodic wrap,
+// pressure columns), collided and stored by dedicated blocks; the main blocks skip them.
+struct Frame {
+  int groups_per_row;  // G = ceil(nx / C)
+  int cols;            // frame groups per non-wall row: 1 if G == 1, else 2
+  int wall_rows;       // 1 if the bottom and top rows are walls
+  int count;           // number of frame groups
+};
+
+__host__ __device__ inline Frame frame_of(int nx, int ny, int bc_y, int C) {
+  Frame f;
+  f.groups_per_row = (nx + C - 1) / C;
+  f.cols = f.groups_per_row == 1 ? 1 : 2;
+  f.wall_rows = bc_y == BC_WALL ? 1 : 0;
+  f.count = (f.wall_rows ? 2 * f.groups_per_row : 0) + f.cols * (ny - (f.wall_rows ? 2 : 0));
+  return f;
+}
+
 template <int PREC, bool HET, bool THERMAL>
-__global__ void __launch_bounds__(kStepThreads) k_step(const StepParams P) {
+__device__ void frame_group(const StepParams& P, const Frame& F, int k) {
   using S = Store<PREC>;
   using T = typename S::T;
+  constexpr int C = kCellsPerThread;
+  if (k >= F.count) return;
+  int x0, y;
+  if (F.wall_rows && k < 2 * F.groups_per_row) {
+    y = k < F.groups_per_row ? 0 : P.ny - 1;
+    x0 = (k % F.groups_per_row) * C;
+  } else {
+    const int k2 = k - (F.wall_rows ? 2 * F.groups_per_row : 0);
+    y = k2 / F.cols + F.wall_rows;
+    x0 = (k2 % F.cols == 0) ? 0 : (F.groups_per_row - 1) * C;
+  }
+  const T* src = static_cast<const T*>(P.src);
+  const T* gsrc = static_cast<const T*>(P.gsrc);
+  float d[8][C], g[5][C];
+#pragma unroll 1
+  for (int c = 0; c < C; ++c) {
+    const int x = x0 + c;
+    float dc[8], gc[5];
+    if (x < P.nx) {
+      if (P.bc_x == BC_PRESSURE && (x == 0 || x == P.nx - 1))
+        pressure_column<PREC, HET>(P, src, x, y, dc);
+      else
+        pull_cell<PREC>(P, src, x, y, dc);
+      float ay = P.ay;
+      if (THERMAL) {
+        pull_cell_g<PREC>(P, gsrc, x, y, gc);
+        ay += P.g_beta * (gc[0] + gc[1] + gc[2] + gc[3] + gc[4]);
+      }
+      const Coef cf = coef_at<HET>(P, x, y);
+      float ux, uy, phip;
+      collide_d2q8(dc, cf, P.ax, ay, P, ux, uy, phip);
+      if (!(fabsf(ux) + fabsf(uy) < 1e30f)) atomicOr(P.err, 1u);
+      if (THERMAL) collide_d2q5(gc, ux, uy, P);
+    } else {  // row padding: zeros (never gathered by a lattice cell)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) dc[i] = 0.0f;
+#pragma unroll
+      for (int i = 0; i < 5; ++i) gc[i] = 0.0f;
+    }
+    // constant-index copies keep d, g in registers of the unrolled store below
+#pragma unroll
+    for (int cc = 0; cc < C; ++cc)
+      if (cc == c) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) d[i][cc] = dc[i];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) g[i][cc] = gc[i];
+      }
+  }
+  const int64_t r0 = (int64_t)y * P.pitch + x0;
+  T* dst = static_cast<T*>(P.dst);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) S::store4(dst + i * P.plane + r0, d[i], P.scale);
+  if (THERMAL) {
+    T* gdst = static_cast<T*>(P.gdst);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) S::store4(gdst + i * P.plane + r0, g[i], P.scale);
+  }
+}
+
+// One time step.  Blocks [0, frame_blocks) do the frame; the rest cover the lattice row by row,
+// gx blocks per row, and store every group that is not a frame group.
+template <int PREC, bool HET, bool THERMAL>
+__global__ void __launch_bounds__(kStepThreads) k_step(const StepParams P, int frame_blocks, int gx) {
+  using S = Store<PREC>;
+  using T = typename S::T;
+  constexpr int C = kCellsPerThread;
+  if ((int)blockIdx.x < frame_blocks) {
+    const Frame F = frame_of(P.nx, P.ny, P.bc_y, C);
+    frame_group<PREC, HET, THERMAL>(P, F, blockIdx.x * kStepThreads + threadIdx.x);
+    return;
+  }
+  const int b = blockIdx.x - frame_blocks;
+  const int y = b / gx;
+  const int x0 = ((b - y * gx) * kStepThreads + threadIdx.x) * C;
   const T* __restrict__ src = static_cast<const T*>(P.src);
   T* __restrict__ dst = static_cast<T*>(P.dst);
   const int lane = threadIdx.x & 31;
-  const int x0 = (blockIdx.x * kStepThreads + threadIdx.x) * kCellsPerThread;
-  const int y = blockIdx.y;
-  const int xl = x0 < P.pitch - 4 ? x0 : P.pitch - 4;  // loads stay inside the row
+  const int xl = x0 < P.pitch - C ? x0 : P.pitch - C;  // loads stay inside the row
+  // source rows of e_y = +1 and -1 (periodic wrap; wall rows belong to the frame)
   int ym = y - 1, yp = y + 1;
-  if (P.bc_y == BC_WALL) {
-    ym = ym < 0 ? 0 : ym;  // wall rows are redone by the edge path
-    yp = yp >= P.ny ? P.ny - 1 : yp;
-  } else {
-    ym = ym < 0 ? P.ny - 1 : ym;
-    yp = yp >= P.ny ? 0 : yp;
-  }
+  ym = ym < 0 ? P.ny - 1 : ym;
+  yp = yp >= P.ny ? 0 : yp;
   const int64_t pl = P.plane;
   const int64_t rm = (int64_t)ym * P.pitch, r0 = (int64_t)y * P.pitch, rp = (int64_t)yp * P.pitch;
   const float inv = P.inv_scale;
 
   // pull streaming, Eq. 15: d_i(x) = d+_i(x - e_i)
-  float d[8][4];
+  float d[8][C];
   gather4<PREC, 1>(src + 0 * pl + r0, xl, P.pitch, lane, inv, d[0]);   // e1 = ( 1, 0)
   gather4<PREC, 0>(src + 1 * pl + rm, xl, P.pitch, lane, inv, d[1]);   // e2 = ( 0, 1)
   gather4<PREC, -1>(src + 2 * pl + r0, xl, P.pitch, lane, inv, d[2]);  // e3 = (-1, 0)
@@ -68,64 +158,43 @@ __global__ void __launch_bounds__(kStepThreads) k_step(const StepParams P) {
   gather4<PREC, -1>(src + 5 * pl + rm, xl, P.pitch, lane, inv, d[5]);  // e6 = (-1, 1)
   gather4<PREC, -1>(src + 6 * pl + rp, xl, P.pitch, lane, inv, d[6]);  // e7 = (-1,-1)
   gather4<PREC, 1>(src + 7 * pl + rp, xl, P.pitch, lane, inv, d[7]);   // e8 = ( 1,-1)
-  float g[5][4];
-  const T* __restrict__ gsrc = static_cast<const T*>(P.gsrc);
+  float g[5][C];
   if (THERMAL) {
+    const T* __restrict__ gsrc = static_cast<const T*>(P.gsrc);
     gather4<PREC, 0>(gsrc + 0 * pl + r0, xl, P.pitch, lane, inv, g[0]);
     gather4<PREC, 1>(gsrc + 1 * pl + r0, xl, P.pitch, lane, inv, g[1]);
     gather4<PREC, 0>(gsrc + 2 * pl + rm, xl, P.pitch, lane, inv, g[2]);
     gather4<PREC, -1>(gsrc + 3 * pl + r0, xl, P.pitch, lane, inv, g[3]);
     gather4<PREC, 0>(gsrc + 4 * pl + rp, xl, P.pitch, lane, inv, g[4]);
   }
-  if (x0 >= P.pitch) return;  // past the padded row: nothing to store (after the shuffles)
-
+  // (after the shuffles) frame groups and groups past the row are not stored here
   const bool wall_row = P.bc_y == BC_WALL && (y == 0 || y == P.ny - 1);
-  bool bad = false;
+  if (wall_row || x0 == 0 || x0 + C >= P.nx) return;
+
+  float check = 0.0f;
 #pragma unroll
-  for (int c = 0; c < kCellsPerThread; ++c) {
-    const int x = x0 + c;
-    float dc[8], gc[5];
+  for (int c = 0; c < C; ++c) {
+    float dc[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) dc[i] = d[i][c];
-    if (THERMAL) {
-#pragma unroll
-      for (int i = 0; i < 5; ++i) gc[i] = g[i][c];
-    }
-    if (x < P.nx) {
-      if (wall_row || x == 0 || x == P.nx - 1) {
-        if (P.bc_x == BC_PRESSURE && (x == 0 || x == P.nx - 1))
-          pressure_column<PREC, HET>(P, src, x, y, dc);
-        else
-          pull_cell<PREC>(P, src, x, y, dc);
-        if (THERMAL) pull_cell_g<PREC>(P, gsrc, x, y, gc);
-      }
-      const Coef cf = coef_at<HET>(P, x, y);
-      float ax = P.ax, ay = P.ay;
-      if (THERMAL) {
-        // buoyancy a = g beta (T - T0) j (Sec. 3.4), T = sum g of the pre-collision state
-        const float dT = gc[0] + gc[1] + gc[2] + gc[3] + gc[4];
-        ay += P.g_beta * dT;
-      }
-      float ux, uy, phip;
-      collide_d2q8(dc, cf, ax, ay, P, ux, uy, phip);
-      bad |= !(fabsf(ux) + fabsf(uy) < 1e30f);
-      if (THERMAL) collide_d2q5(gc, ux, uy, P);
-    } else {
-#pragma unroll
-      for (int i = 0; i < 8; ++i) dc[i] = 0.0f;
-      if (THERMAL) {
-#pragma unroll
-        for (int i = 0; i < 5; ++i) gc[i] = 0.0f;
-      }
-    }
+    const Coef cf = coef_at<HET>(P, x0 + c, y);
+    float ay = P.ay;
+    if (THERMAL) ay += P.g_beta * (g[0][c] + g[1][c] + g[2][c] + g[3][c] + g[4][c]);  // a = g beta (T - T0) j
+    float ux, uy, phip;
+    collide_d2q8(dc, cf, P.ax, ay, P, ux, uy, phip);
+    check += fabsf(ux) + fabsf(uy);
 #pragma unroll
     for (int i = 0; i < 8; ++i) d[i][c] = dc[i];
     if (THERMAL) {
+      float gc[5];
+#pragma unroll
+      for (int i = 0; i < 5; ++i) gc[i] = g[i][c];
+      collide_d2q5(gc, ux, uy, P);
 #pragma unroll
       for (int i = 0; i < 5; ++i) g[i][c] = gc[i];
     }
   }
-  if (bad) atomicOr(P.err, 1u);
+  if (!(check < 1e30f)) atomicOr(P.err, 1u);  // non-finite velocity in these cells
   const float sc = P.scale;
 #pragma unroll
   for (int i = 0; i < 8; ++i) S::store4(dst + i * pl + r0 + x0, d[i], sc);
@@ -139,8 +208,11 @@ __global__ void __launch_bounds__(kStepThreads) k_step(const StepParams P) {
 template <int PREC, bool HET, bool THERMAL>
 static cudaError_t launch_step_t(const StepParams& P, cudaStream_t s) {
   const int per_block = kStepThreads * kCellsPerThread;
-  dim3 grid((P.nx + per_block - 1) / per_block, P.ny);
-  k_step<PREC, HET, THERMAL><<<grid, kStepThreads, 0, s>>>(P);
+  const int gx = (P.nx + per_block - 1) / per_block;
+  const Frame F = frame_of(P.nx, P.ny, P.bc_y, kCellsPerThread);
+  const int fb = (F.count + kStepThreads - 1) / kStepThreads;
+  const long long blocks = (long long)fb + (long long)gx * P.ny;
+  k_step<PREC, HET, THERMAL><<<(unsigned)blocks, kStepThreads, 0, s>>>(P, fb, gx);
   return cudaGetLastError();
 }
 
