@@ -46,9 +46,11 @@ def cavity_params(L):
 
 
 def source_hash():
+    """Hash of the sources that define the fused step kernel (a recorded ncu traffic figure is
+    only reported while these are unchanged)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1311_7239_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in ("lbm_device.cuh", "step.cu"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
