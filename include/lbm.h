@@ -149,6 +149,24 @@ LBM_API int lbm_set_populations(lbm_ctx* ctx, const float* f, const float* g);
  * on the device (needs one step since the last initialisation or import; ESTATE before that).  Waits for the stream. */
 LBM_API int lbm_residual(lbm_ctx* ctx, double* r);
 
+/* Allocation-free residual, for callers that must not allocate device memory (a service that
+ * sizes one memory pool at start-up, a host whose framework owns all device memory through its
+ * own allocator, a real-time loop that cannot afford the device-wide synchronisation of
+ * cudaMalloc/cudaFree).  The paper has no counterpart: this is the residual above, computed from
+ * two velocity fields the caller holds instead of from a context.
+ *   ux, uy, ux_prev, uy_prev: device float32 arrays of n cells (any layout, the same for all four);
+ *   r: device or host double receiving ||u - u_prev||_2 / ||u||_2 (sums in FP64; 0 if u = 0);
+ *   stream: cudaStream_t to run on (NULL = the default stream).
+ * Limits: 1 <= n <= 67108864 (2^26, an 8192 x 8192 lattice); larger n is EINVAL.  The partial
+ * sums use a fixed 64 KB array in device memory that liblbm.so reserves on every GPU that loads
+ * it, until the process exits; no call allocates or frees anything.  The first call on a device
+ * looks up that array's address (once per device, with the device current); make that first
+ * call before any stream capture.  All calls share the one array and each call overwrites it, so
+ * calls whose work overlaps on the GPU (different streams, or different host threads) race and
+ * must be serialised by the caller.  With a host r the call waits for the stream. */
+LBM_API int lbm_residual_noalloc(const float* ux, const float* uy, const float* ux_prev, const float* uy_prev, int64_t n,
+                                 double* r, void* stream);
+
 /* Average Nusselt number of a wall with a prescribed temperature (side = LBM_LEFT or
  * LBM_RIGHT): Nu = (nx / (T_hot - T_cold)) * mean_y(-+ dT/dx at the wall), dT/dx from the
  * parabola through the wall value and the two nearest cells; the sum is FP64.  Waits. */

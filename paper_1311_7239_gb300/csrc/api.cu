@@ -38,6 +38,12 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 }  // namespace
 
+namespace lbm {
+// Records msg as the calling thread's last error and returns code (for entry points defined in
+// other translation units).
+int record_error(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace lbm
+
 struct lbm_ctx {
   lbm_config cfg;
   int device = 0;

@@ -10,6 +10,7 @@ namespace lbm {
 
 constexpr int kResidualMaxBlocks = 2048;  // partial-sum slots of the residual reduction
 
+int record_error(int code, const char* msg);
 cudaError_t launch_step(const StepParams& P, int prec, bool het, bool thermal, cudaStream_t s);
 cudaError_t launch_medium(const float* eps, const float* K, float phi_u, float K_u, int nx, int ny, int pitch, float* phi_out,
                           float* K_out, unsigned int* err, cudaStream_t s);

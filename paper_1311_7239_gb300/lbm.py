@@ -79,6 +79,7 @@ SIGNATURES = {
     "lbm_set_populations": (ctypes.c_int, [_c_ctx, _f32p, _f32p]),
     "lbm_residual": (ctypes.c_int, [_c_ctx, ctypes.POINTER(ctypes.c_double)]),
     "lbm_nusselt": (ctypes.c_int, [_c_ctx, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "lbm_residual_noalloc": (ctypes.c_int, [_f32p, _f32p, _f32p, _f32p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "lbm_sync": (ctypes.c_int, [_c_ctx]),
     "lbm_step_count": (ctypes.c_int, [_c_ctx, ctypes.POINTER(ctypes.c_int64)]),
     "lbm_memory_bytes": (ctypes.c_int, [_c_ctx, ctypes.POINTER(ctypes.c_uint64)]),
