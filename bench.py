@@ -279,6 +279,30 @@ def run_gpu(args, rank, world, local_rank):
     return 0
 
 
+def run_sweep(args, local_rank):
+    """Throughput over lattice sizes (one JSON line per size and storage precision)."""
+    import torch
+
+    from paper_1311_7239_gb300 import lbm
+
+    torch.cuda.set_device(local_rank)
+    peak, peak_kind = peaks()
+    for L in [int(v) for v in args.sweep.split(",")]:
+        for prec in PREC:
+            steps = max(64, int(args.steps * (4096 / L) ** 2))
+            steps = min(steps, 64000) // 32 * 32
+            ms, clk, lat = timed_steps(lbm, L, prec, steps, args.warmup, local_rank)
+            lat.close()
+            cells = L * L
+            bw = BYTES_PER_LU[prec] * cells * steps / (ms * 1e-3) / 1e9
+            l2 = 2 * BYTES_PER_LU[prec] // 2 * cells / 1e6
+            print(json.dumps({"size": L, "precision": prec, "steps": steps, "MLUPS": cells * steps / (ms * 1e-3) / 1e6,
+                              "achieved_gbs": bw, "roofline_frac": bw / peak, "peak_source": peak_kind,
+                              "state_MB": l2, "l2_resident": l2 < 129.0, "clocks": clk}), flush=True)
+            torch.cuda.empty_cache()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -288,7 +312,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=list(PREC))
     ap.add_argument("--size", type=int, default=4096)
     ap.add_argument("--no-cpu", action="store_true", help="skip the timed CPU oracle baseline")
-    ap.add_argument("--no-forms", action="store_true", help="skip the other storage precisions and accuracy checks")
+    ap.add_argument("--no-forms", action="store_true", help="skip the other storage precisions")
+    ap.add_argument("--sweep", default="", help="comma-separated lattice sizes: print one line per size and precision")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -297,6 +322,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.sweep:
+        return run_sweep(args, local_rank)
     return run_gpu(args, rank, world, local_rank)
 
 

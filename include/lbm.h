@@ -123,7 +123,9 @@ LBM_API int lbm_init_equilibrium(lbm_ctx* ctx, double p0, double ux0, double uy0
 LBM_API int lbm_init_temperature(lbm_ctx* ctx, double T_init);
 
 /* Advance n >= 0 time steps of Eq. 6 (collision Eq. 14, streaming Eq. 15) and, if thermal,
- * of Eq. B.2 with the buoyancy coupling.  Long runs replay a captured CUDA graph. */
+ * of Eq. B.2 with the buoyancy coupling.  Runs of 32 steps or more replay a CUDA graph of 32
+ * steps, captured on first use from a private stream (so a context on the legacy default stream
+ * works too); lbm_set_medium discards the captured graphs. */
 LBM_API int lbm_step(lbm_ctx* ctx, int n);
 
 /* Replace the wall velocities u_wall[4][2] (left, right, bottom, top; float32, host or device)

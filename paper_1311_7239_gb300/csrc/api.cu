@@ -69,9 +69,14 @@ struct lbm_ctx {
   int64_t steps = 0;
   int64_t history = 0;           // steps since the last initialisation or import
   StepParams base;
+  // CUDA graphs of kGraphSteps steps starting from buffer 0 or 1 (captured on first use)
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaStream_t capture_stream = nullptr;
 };
 
 namespace {
+
+constexpr int kGraphSteps = 32;  // steps per captured graph (even: a replay ends on the buffer it began on)
 
 bool thermal_of(const lbm_ctx* c) { return c->cfg.thermal != 0; }
 
@@ -252,9 +257,18 @@ void fill_base(lbm_ctx* c) {
   P.err = c->err;
 }
 
+void drop_graphs(lbm_ctx* c) {
+  for (int b = 0; b < 2; ++b) {
+    if (c->graph[b]) cudaGraphExecDestroy(c->graph[b]);
+    c->graph[b] = nullptr;
+  }
+}
+
 void release(lbm_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
+  drop_graphs(c);
+  if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
   for (int b = 0; b < 2; ++b) {
     cudaFree(c->f[b]);
     cudaFree(c->g[b]);
@@ -375,6 +389,7 @@ void lbm_destroy(lbm_ctx* ctx) { release(ctx); }
 
 int lbm_set_medium(lbm_ctx* c, const float* eps, const float* K) {
   if (!c) return fail(LBM_EINVAL, "null context");
+  drop_graphs(c);  // captured steps bake in the medium mode
   if (!eps && !K) {
     c->het = false;
     return LBM_OK;
@@ -429,12 +444,56 @@ int lbm_init_temperature(lbm_ctx* c, double T_init) {
   return LBM_OK;
 }
 
+namespace {
+
+StepParams params_at(const lbm_ctx* c, int cur) {
+  StepParams P = params_for(c);
+  P.src = c->f[cur];
+  P.dst = c->f[cur ^ 1];
+  P.gsrc = c->g[cur];
+  P.gdst = c->g[cur ^ 1];
+  return P;
+}
+
+// Instantiate the graph of kGraphSteps steps that starts from buffer `cur`.
+int capture_graph(lbm_ctx* c, int cur) {
+  if (!c->capture_stream) LBM_CUDA(cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+  LBM_CUDA(cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+  cudaError_t launch_err = cudaSuccess;
+  for (int k = 0; k < kGraphSteps && launch_err == cudaSuccess; ++k)
+    launch_err = launch_step(params_at(c, cur ^ (k & 1)), c->prec, c->het, thermal_of(c), c->capture_stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->capture_stream, &g);
+  if (launch_err != cudaSuccess || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(launch_err != cudaSuccess ? launch_err : e, "capture of the step graph");
+  }
+  e = cudaGraphInstantiate(&c->graph[cur], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    c->graph[cur] = nullptr;
+    return cuda_fail(e, "cudaGraphInstantiate");
+  }
+  return LBM_OK;
+}
+
+}  // namespace
+
 int lbm_step(lbm_ctx* c, int n) {
   if (!c) return fail(LBM_EINVAL, "null context");
   if (n < 0) return fail(LBM_EINVAL, "negative step count");
+  while (n >= kGraphSteps) {  // replay a captured graph of kGraphSteps steps
+    if (!c->graph[c->cur]) {
+      int rc = capture_graph(c, c->cur);
+      if (rc) return rc;
+    }
+    LBM_CUDA(cudaGraphLaunch(c->graph[c->cur], c->stream), "cudaGraphLaunch");
+    c->steps += kGraphSteps;
+    c->history += kGraphSteps;
+    n -= kGraphSteps;
+  }
   for (int k = 0; k < n; ++k) {
-    StepParams P = params_for(c);
-    LBM_CUDA(launch_step(P, c->prec, c->het, thermal_of(c), c->stream), "step kernel");
+    LBM_CUDA(launch_step(params_at(c, c->cur), c->prec, c->het, thermal_of(c), c->stream), "step kernel");
     c->cur ^= 1;
     ++c->steps;
     ++c->history;

@@ -225,3 +225,20 @@ def test_reduced_precision_thermal_error(lbm, prec, bound):
     e_T = rel_l2(T - 11.0, To - 11.0)
     print(f"precision {prec}: rel-L2 u {e_u:.3e}, T-T0 {e_T:.3e}")
     assert e_u <= bound and e_T <= bound, (e_u, e_T)
+
+
+def test_graph_replay_equals_single_launches(lbm):
+    """lbm_step(n) replays a captured graph of 32 steps; the result is bitwise that of n single steps."""
+    case = Case(150, 70, nu=0.05, phi=0.5, K=3.0, bc_x="wall", bc_y="wall", walls=CAV, het=True)
+    with case.lattice(lbm) as a, case.lattice(lbm) as b:
+        a.step(101)   # three graph replays + 5 launches
+        for _ in range(101):
+            b.step(1)
+        fa = a.get_populations().cpu().numpy()
+        fb = b.get_populations().cpu().numpy()
+        a.step(64)   # a graph starting from the other buffer
+        b.step(64)
+        ga = a.get_populations().cpu().numpy()
+        gb = b.get_populations().cpu().numpy()
+        assert a.step_count() == b.step_count() == 165
+    assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
