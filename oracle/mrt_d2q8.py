@@ -305,7 +305,7 @@ def pressure_columns(f, flow: Flow, phi=None, K=None):
     phi = flow.phi if phi is None else phi
     K = flow.K if K is None else K
     ax, ay = _accel(flow, f[0])
-    out = f.copy()
+    out = f.astype(np.result_type(f, phi, K), copy=True)
     for xb, xn, pb in ((0, 1, flow.p_in), (flow.nx - 1, flow.nx - 2, flow.p_out)):
         fn = f[:, :, xn]
         ux, uy = velocity(fn, phi[:, xn], K[:, xn], flow.nu, flow.rho0, flow.forchheimer, ax[:, xn], ay[:, xn])
