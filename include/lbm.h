@@ -113,6 +113,9 @@ LBM_API void lbm_destroy(lbm_ctx* ctx);
  * Either may be NULL to keep a uniform value (cfg.phi / cfg.K).  Requires 0 < eps <= 1 and
  * K > 0 (checked on the device; EINVAL).  Does not change the populations. */
 LBM_API int lbm_set_medium(lbm_ctx* ctx, const float* eps, const float* K);
+/* The same with log K given instead of K (K = exp(logK) per cell; the parameterisation of the
+ * adjoint's gradient). */
+LBM_API int lbm_set_medium_log(lbm_ctx* ctx, const float* eps, const float* logK);
 
 /* Set the populations to the equilibrium f_eq(p, u; phi) of Eq. 22 (= M^-1 m_eq, Eqs. 8, 11) with
  * u = (ux0, uy0) and p = p0 (phi_p_uniform == 0, the initial state of Sec. 3.1) or p = p0/phi
@@ -168,6 +171,23 @@ LBM_API int lbm_residual(lbm_ctx* ctx, double* r);
  * must be serialised by the caller.  With a host r the call waits for the stream. */
 LBM_API int lbm_residual_noalloc(const float* ux, const float* uy, const float* ux_prev, const float* uy_prev, int64_t n,
                                  double* r, void* stream);
+
+/* loss kinds of lbm_adjoint */
+#define LBM_LOSS_OUTLET_FLUX 0     /* L = sum_y u_x(nx-1, y) of the final state */
+#define LBM_LOSS_VELOCITY_MISFIT 1 /* L = 1/2 sum |u - u*|^2 over all cells of the final state */
+
+/* Discrete adjoint of T flow steps (collision Eq. 14, streaming Eq. 15, pressure columns) from the
+ * current initial state (call right after lbm_init_equilibrium; ESTATE otherwise, and for thermal
+ * contexts): runs the T steps -- the context ends at step T, as after lbm_step(ctx, T) -- and
+ * returns the loss and its gradient with respect to the per-cell log K and eps (phi) fields,
+ * including their effect on the initial equilibrium (Eq. 22).  Memory: checkpoints of the
+ * post-collision state every ceil(sqrt(T)) steps plus one segment of ceil(sqrt(T)) states are
+ * allocated for the call and freed before it returns; the forward work is about 2 T steps.
+ *   target_ux, target_uy: float32 [ny][nx] (misfit loss only; host or device).
+ *   grad_logK, grad_eps: double [ny][nx] outputs (host or device; NULL skips); loss: double.
+ * Waits for the stream. */
+LBM_API int lbm_adjoint(lbm_ctx* ctx, int T, int loss_kind, const float* target_ux, const float* target_uy, double* grad_logK,
+                        double* grad_eps, double* loss);
 
 /* Average Nusselt number of a wall with a prescribed temperature (side = LBM_LEFT or
  * LBM_RIGHT): Nu = (nx / (T_hot - T_cold)) * mean_y(-+ dT/dx at the wall), dT/dx from the

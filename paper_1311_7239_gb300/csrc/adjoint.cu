@@ -1,0 +1,416 @@
+// Discrete adjoint of the fused D2Q8 porous MRT-LB step (Liu & He, arXiv 1311.7239, Eqs. 3-20):
+// gradients of a scalar loss of the state after T steps with respect to the per-cell
+// log-permeability l = log K and porosity phi (theta of Eq. 3 and Eq. 4).
+//
+// Forward map in pre-collision variables: z(t+1) = N(P(C(z(t); theta)); theta), z(0) = N(f_eq(theta)),
+// with C the collision (Eq. 14 as d+ = d + M^-1 k, k = m+ - m), P the pull streaming with its wall
+// rules (Eq. 15) and N the pressure columns (non-equilibrium extrapolation).  The adjoint state
+// nu(t) = dL/dz(t) obeys nu(t) = J_C(z(t))^T P^T J_N^T nu(t+1); every piece is differentiated
+// here by hand in reverse mode:
+//   - P^T is the reversed link table (a gather of nu from x + e_i, or from the opposite slot
+//     through a wall); the moving-wall term is a constant and has no derivative.
+//   - J_C^T mu = mu + M^T kbar, kbar = (dk/dm)^T w, w = M^-T mu, through Eq. 11-14 (m_eq, S),
+//     Eq. 3 (F), Eq. 20 (phi p) and the root of Eqs. 18-19 (u, |u|).  At |v| = 0 the derivative
+//     of |v| is taken as 0 (the one-sided limit of the smooth part of Eq. 18).
+//   - J_N^T moves the adjoint of each pressure-column cell onto its neighbour column.
+// theta enters through phi (Eq. 3, 11, 16, 19, 20 and F_phi of Eq. 4) and K (Eq. 3, 19); with
+// c_lin = phi nu / K and c_nl = phi F_phi / sqrt(K) = 1.75 / sqrt(150 phi K):
+//   dc_lin/dl = -c_lin, dc_lin/dphi = c_lin / phi, dc_nl/dl = -c_nl / 2, dc_nl/dphi = -c_nl / (2 phi).
+// Gradients accumulate in FP64; the adjoint state is stored in FP32 planes [8][ny][pitch].
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+
+namespace lbm {
+
+// Reverse of velocity_from_j: adjoints (ubx, uby) of u and umb of |u| -> adjoints of jx, jy and
+// of the coefficients c_lin, c_nl and phi (through phi a / 2).
+struct VelBar {
+  float jx, jy, clin, cnl, phi;
+};
+
+__device__ __forceinline__ VelBar velocity_vjp(float jx, float jy, const Coef& c, float ax, float ay, float inv_rho0, float ubx,
+                                               float uby, float umb) {
+  const float vx = jx * inv_rho0 + 0.5f * c.phi * ax;
+  const float vy = jy * inv_rho0 + 0.5f * c.phi * ay;
+  const float l0 = 0.5f + 0.25f * c.c_lin;
+  const float l1 = 0.5f * c.c_nl;
+  const float vmag = fast_sqrt(vx * vx + vy * vy);
+  const float sR = fast_sqrt(l0 * l0 + l1 * vmag);
+  const float inv = fast_rcp(l0 + sR);
+  float vbx = ubx * inv, vby = uby * inv;
+  float inv_bar = ubx * vx + uby * vy + umb * vmag;
+  float vmag_bar = umb * inv;
+  const float D_bar = -inv * inv * inv_bar;
+  const float R_bar = D_bar * 0.5f * fast_rcp(sR);
+  const float l0_bar = D_bar + 2.0f * l0 * R_bar;
+  const float l1_bar = vmag * R_bar;
+  vmag_bar += l1 * R_bar;
+  if (vmag > 0.0f) {
+    const float iv = fast_rcp(vmag);
+    vbx += vmag_bar * vx * iv;
+    vby += vmag_bar * vy * iv;
+  }
+  VelBar o;
+  o.jx = vbx * inv_rho0;
+  o.jy = vby * inv_rho0;
+  o.phi = 0.5f * (ax * vbx + ay * vby);
+  o.clin = 0.25f * l0_bar;
+  o.cnl = 0.5f * l1_bar;
+  return o;
+}
+
+// theta-gradients from the adjoints of c_lin, c_nl, 1/phi and phi itself.
+__device__ __forceinline__ void theta_bar(const Coef& c, float clin_bar, float cnl_bar, float iphi_bar, float phi_bar, double& g_l,
+                                          double& g_phi) {
+  g_l += (double)(-c.c_lin * clin_bar - 0.5f * c.c_nl * cnl_bar);
+  g_phi += (double)(phi_bar - c.inv_phi * c.inv_phi * iphi_bar + c.c_lin * c.inv_phi * clin_bar -
+                    0.5f * c.c_nl * c.inv_phi * cnl_bar);
+}
+
+// nu = J_C(z)^T mu and the theta-gradient (dC/dtheta)^T mu of one cell.
+__device__ void collide_vjp(const float z[8], const Coef& c, float ax, float ay, const StepParams& P, const float mu[8], float nu[8],
+                            double& g_l, double& g_phi) {
+  const float rho0 = P.rho0;
+  // forward quantities (as collide_d2q8)
+  const float a13 = z[0] + z[2], a24 = z[1] + z[3];
+  const float d13 = z[0] - z[2], d24 = z[1] - z[3];
+  const float s57 = z[4] + z[6], s68 = z[5] + z[7];
+  const float t57 = z[4] - z[6], t68 = z[5] - z[7];
+  const float m1 = a13 + a24 + s57 + s68;
+  const float m3 = d13 + (t57 - t68), m5 = d24 + (t57 + t68);
+  float ux, uy, umag;
+  velocity_from_j(m3, m5, c, ax, ay, P.inv_rho0, ux, uy, umag);
+  const float usq = ux * ux + uy * uy;
+  const float drag = c.c_lin + c.c_nl * umag;
+  const float Fx = -drag * ux + c.phi * ax;
+  const float Fy = -drag * uy + c.phi * ay;
+  const float ip = c.inv_phi;
+  (void)m1;
+  // w = M^-T mu = diag(1/8, 1/8, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4) M mu (w1 is not needed: k1 = 0)
+  const float b13 = mu[0] - mu[2], b24 = mu[1] - mu[3];
+  const float bx = mu[4] - mu[5] - mu[6] + mu[7], by = mu[4] + mu[5] - mu[6] - mu[7];
+  const float w2 = (-(mu[0] + mu[1] + mu[2] + mu[3]) + (mu[4] + mu[5] + mu[6] + mu[7])) * 0.125f;
+  const float w3 = (b13 + bx) * (1.0f / 6.0f), w4 = (-2.0f * b13 + bx) * (1.0f / 12.0f);
+  const float w5 = (b24 + by) * (1.0f / 6.0f), w6 = (-2.0f * b24 + by) * (1.0f / 12.0f);
+  const float w7 = (mu[0] - mu[1] + mu[2] - mu[3]) * 0.25f, w8 = (mu[4] - mu[5] + mu[6] - mu[7]) * 0.25f;
+  const float s_e = P.s_e, s_q = P.s_q, s_v = P.s_v, hv = 1.0f - 0.5f * s_v;
+  float mb1 = 0.f, mb2 = 0.f, mb3 = 0.f, mb4 = 0.f, mb5 = 0.f, mb6 = 0.f, mb7 = 0.f, mb8 = 0.f;
+  float ubx = 0.f, uby = 0.f, Fbx = 0.f, Fby = 0.f, Pb = 0.f, S2b = 0.f, ipb = 0.f, phib = 0.f;
+  // k2 = -s_e (m2 + phi p) + (1 - s_e/2) S2
+  mb2 += -s_e * w2;
+  Pb += -s_e * w2;
+  S2b += (1.0f - 0.5f * s_e) * w2;
+  // k3 = rho0 F_x ; k4 = -s_q (m4 + m3) - rho0 F_x
+  Fbx += rho0 * w3 - rho0 * w4;
+  mb4 += -s_q * w4;
+  mb3 += -s_q * w4;
+  // k5 = rho0 F_y ; k6 = -s_q (m6 + m5) - rho0 F_y
+  Fby += rho0 * w5 - rho0 * w6;
+  mb6 += -s_q * w6;
+  mb5 += -s_q * w6;
+  // k7 = -s_v m7 + s_v rho0 (ux^2 - uy^2)/phi + hv 2 rho0 (ux Fx - uy Fy)/phi
+  mb7 += -s_v * w7;
+  ubx += w7 * 2.0f * rho0 * ip * (s_v * ux + hv * Fx);
+  uby += -w7 * 2.0f * rho0 * ip * (s_v * uy + hv * Fy);
+  Fbx += w7 * 2.0f * hv * rho0 * ux * ip;
+  Fby += -w7 * 2.0f * hv * rho0 * uy * ip;
+  ipb += w7 * rho0 * (s_v * (ux * ux - uy * uy) + 2.0f * hv * (ux * Fx - uy * Fy));
+  // k8 = -s_v m8 + s_v rho0 ux uy/phi + hv rho0 (ux Fy + uy Fx)/phi
+  mb8 += -s_v * w8;
+  ubx += w8 * rho0 * ip * (s_v * uy + hv * Fy);
+  uby += w8 * rho0 * ip * (s_v * ux + hv * Fx);
+  Fby += w8 * hv * rho0 * ux * ip;
+  Fbx += w8 * hv * rho0 * uy * ip;
+  ipb += w8 * rho0 * (s_v * ux * uy + hv * (ux * Fy + uy * Fx));
+  // S2 = 0.8 rho0 (u . F) / phi
+  ubx += S2b * 0.8f * rho0 * Fx * ip;
+  uby += S2b * 0.8f * rho0 * Fy * ip;
+  Fbx += S2b * 0.8f * rho0 * ux * ip;
+  Fby += S2b * 0.8f * rho0 * uy * ip;
+  ipb += S2b * 0.8f * rho0 * (ux * Fx + uy * Fy);
+  // phi p (deviation) = 0.6 m1 - 0.4 rho0 |u|^2 / phi
+  mb1 += 0.6f * Pb;
+  ubx += -0.8f * rho0 * ux * ip * Pb;
+  uby += -0.8f * rho0 * uy * ip * Pb;
+  ipb += -0.4f * rho0 * usq * Pb;
+  // F = -(c_lin + c_nl |u|) u + phi a
+  ubx += -drag * Fbx;
+  uby += -drag * Fby;
+  const float drag_b = -(ux * Fbx + uy * Fby);
+  float clin_b = drag_b;
+  float cnl_b = umag * drag_b;
+  const float umag_b = c.c_nl * drag_b;
+  phib += ax * Fbx + ay * Fby;
+  // u, |u| from j (Eqs. 18-19)
+  const VelBar vb = velocity_vjp(m3, m5, c, ax, ay, P.inv_rho0, ubx, uby, umag_b);
+  mb3 += vb.jx;
+  mb5 += vb.jy;
+  clin_b += vb.clin;
+  cnl_b += vb.cnl;
+  phib += vb.phi;
+  // nu = mu + M^T mbar
+  const float A = mb1 - mb2, B = mb1 + mb2;
+  const float X = mb3 - 2.0f * mb4, Y = mb5 - 2.0f * mb6;
+  const float Px = mb3 + mb4, Py = mb5 + mb6;
+  nu[0] = mu[0] + A + X + mb7;
+  nu[1] = mu[1] + A + Y - mb7;
+  nu[2] = mu[2] + A - X + mb7;
+  nu[3] = mu[3] + A - Y - mb7;
+  nu[4] = mu[4] + B + Px + Py + mb8;
+  nu[5] = mu[5] + B - Px + Py - mb8;
+  nu[6] = mu[6] + B - Px - Py + mb8;
+  nu[7] = mu[7] + B + Px - Py - mb8;
+  theta_bar(c, clin_b, cnl_b, ipb, phib, g_l, g_phi);
+}
+
+// pre-collision state of a cell gathered from a post-collision buffer (pressure columns included)
+template <int PREC, bool HET>
+__device__ __forceinline__ void gather_z(const StepParams& P, const void* buf, int x, int y, float z[8]) {
+  using T = typename Store<PREC>::T;
+  const T* src = static_cast<const T*>(buf);
+  if (P.bc_x == BC_PRESSURE && (x == 0 || x == P.nx - 1))
+    pressure_column<PREC, HET>(P, src, x, y, z);
+  else
+    pull_cell<PREC>(P, src, x, y, z);
+}
+
+// --------------------------------------------------------------------------------------------
+// kernels
+// --------------------------------------------------------------------------------------------
+struct AdjArgs {
+  const float* nu_in;  // nu(t+1) after J_N^T (planes [8][ny][pitch])
+  float* nu_out;       // nu(t)
+  double* g_l;         // dL/dlog K  [ny][nx]
+  double* g_phi;       // dL/dphi    [ny][nx]
+};
+
+// Seed: nu(T) = dL/dz(T) and the explicit theta-gradient of the loss; per-block loss partials.
+// kind 0: L = sum_y u_x(nx-1, y); kind 1: L = 1/2 sum |u - u*|^2.
+template <int PREC, bool HET>
+__global__ void k_adj_seed(const StepParams P, AdjArgs A, int kind, const float* __restrict__ tux, const float* __restrict__ tuy,
+                           double* __restrict__ partial) {
+  double lsum = 0.0;
+  const int64_t n = (int64_t)P.nx * P.ny;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const int y = (int)(k / P.nx), x = (int)(k - (int64_t)y * P.nx);
+    float z[8];
+    gather_z<PREC, HET>(P, P.src, x, y, z);
+    const Coef c = coef_at<HET>(P, x, y);
+    const float jx = (z[0] - z[2]) + (z[4] - z[5] - z[6] + z[7]);
+    const float jy = (z[1] - z[3]) + (z[4] + z[5] - z[6] - z[7]);
+    float ux, uy, umag;
+    velocity_from_j(jx, jy, c, P.ax, P.ay, P.inv_rho0, ux, uy, umag);
+    float ubx = 0.f, uby = 0.f;
+    if (kind == 0) {
+      if (x == P.nx - 1) {
+        lsum += ux;
+        ubx = 1.0f;
+      }
+    } else {
+      const float ex = ux - tux[k], ey = uy - tuy[k];
+      lsum += 0.5 * ((double)ex * ex + (double)ey * ey);
+      ubx = ex;
+      uby = ey;
+    }
+    float nu[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    double gl = 0.0, gp = 0.0;
+    if (ubx != 0.0f || uby != 0.0f) {
+      const VelBar vb = velocity_vjp(jx, jy, c, P.ax, P.ay, P.inv_rho0, ubx, uby, 0.0f);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) nu[i] = (float)ex_of(i) * vb.jx + (float)ey_of(i) * vb.jy;
+      theta_bar(c, vb.clin, vb.cnl, 0.0f, vb.phi, gl, gp);
+    }
+    const int64_t o = (int64_t)y * P.pitch + x;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) A.nu_out[i * P.plane + o] = nu[i];
+    A.g_l[k] += gl;
+    A.g_phi[k] += gp;
+  }
+  // block sum of the loss
+  __shared__ double sh[32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, off);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = lsum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+    partial[blockIdx.x] = s;
+  }
+}
+
+__global__ void k_adj_loss_total(const double* __restrict__ partial, int nblocks, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < nblocks; ++i) s += partial[i];
+    out[0] = s;
+  }
+}
+
+// J_N^T in place on nu: one thread per row handles both pressure columns (they share a neighbour
+// column when nx = 3).  z(nb) is gathered from `buf`, the post-collision buffer whose gather is
+// the state at which N was applied.
+template <int PREC, bool HET>
+__global__ void k_adj_nee(const StepParams P, const void* buf, float* __restrict__ nu, double* __restrict__ g_l,
+                          double* __restrict__ g_phi) {
+  const int y = blockIdx.x * blockDim.x + threadIdx.x;
+  if (y >= P.ny) return;
+  using T = typename Store<PREC>::T;
+  for (int side = 0; side < 2; ++side) {
+    const int xb = side ? P.nx - 1 : 0, xn = side ? P.nx - 2 : 1;
+    const float pb = side ? P.p_out : P.p_in;
+    const int64_t ob = (int64_t)y * P.pitch + xb, on = (int64_t)y * P.pitch + xn;
+    float nb_[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      nb_[i] = nu[i * P.plane + ob];
+      nu[i * P.plane + ob] = 0.0f;
+    }
+    float z[8];
+    pull_cell<PREC>(P, static_cast<const T*>(buf), xn, y, z);
+    const Coef cn = coef_at<HET>(P, xn, y);
+    const Coef cb = coef_at<HET>(P, xb, y);
+    const float jx = (z[0] - z[2]) + (z[4] - z[5] - z[6] + z[7]);
+    const float jy = (z[1] - z[3]) + (z[4] + z[5] - z[6] - z[7]);
+    float ux, uy, umag;
+    velocity_from_j(jx, jy, cn, P.ax, P.ay, P.inv_rho0, ux, uy, umag);
+    const float usq = ux * ux + uy * uy;
+    const float rho0 = P.rho0;
+    // N_b,i = z_nb,i + 3 w_i (phi_b p_b - phi_n p_n) + rho0 w_i (4.5 (e_i.u)^2 - 1.5 |u|^2)(1/phi_b - 1/phi_n)
+    float W = 0.f, WA = 0.f, gux = 0.f, guy = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float wi = w_of(i) * nb_[i];
+      const float ex = (float)ex_of(i), ey = (float)ey_of(i);
+      const float eu = ex * ux + ey * uy;
+      W += wi;
+      WA += wi * (4.5f * eu * eu - 1.5f * usq);
+      gux += wi * (9.0f * eu * ex - 3.0f * ux);
+      guy += wi * (9.0f * eu * ey - 3.0f * uy);
+    }
+    const float diff = cb.inv_phi - cn.inv_phi;
+    float ubx = rho0 * diff * gux, uby = rho0 * diff * guy;
+    const float Pn_b = -3.0f * W;  // adjoint of phi_n p_n
+    float ipn_b = -rho0 * WA;       // adjoint of 1/phi_n
+    const float ipb_b = rho0 * WA;  // adjoint of 1/phi_b
+    // phi_n p_n (deviation) = 0.6 m1 - 0.4 rho0 |u|^2 / phi_n
+    const float mb1 = 0.6f * Pn_b;
+    ubx += -0.8f * rho0 * ux * cn.inv_phi * Pn_b;
+    uby += -0.8f * rho0 * uy * cn.inv_phi * Pn_b;
+    ipn_b += -0.4f * rho0 * usq * Pn_b;
+    const VelBar vb = velocity_vjp(jx, jy, cn, P.ax, P.ay, P.inv_rho0, ubx, uby, 0.0f);
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      nu[i * P.plane + on] += nb_[i] + mb1 + (float)ex_of(i) * vb.jx + (float)ey_of(i) * vb.jy;
+    const int64_t kb = (int64_t)y * P.nx + xb, kn = (int64_t)y * P.nx + xn;
+    // boundary cell: phi_b p_b and 1/phi_b
+    g_phi[kb] += (double)(3.0f * pb * W - cb.inv_phi * cb.inv_phi * ipb_b);
+    double gl = 0.0, gp = 0.0;
+    theta_bar(cn, vb.clin, vb.cnl, ipn_b, vb.phi, gl, gp);
+    g_l[kn] += gl;
+    g_phi[kn] += gp;
+  }
+}
+
+// nu(t) = J_C(z(t))^T P^T nu~(t+1), gradient += (dC/dtheta)^T P^T nu~(t+1); z(t) from buf = b(t).
+template <int PREC, bool HET>
+__global__ void __launch_bounds__(128) k_adj_step(const StepParams P, const void* buf, AdjArgs A) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  if (x >= P.nx) return;
+  // P^T: the slot (i, x) feeds the cell x + e_i, or the cell x itself through a wall
+  float mu[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    int tx = x + ex_of(i), ty = y + ey_of(i);
+    if (P.bc_x != BC_WALL) tx = (tx + P.nx) % P.nx;
+    if (P.bc_y != BC_WALL) ty = (ty + P.ny) % P.ny;
+    if (tx >= 0 && tx < P.nx && ty >= 0 && ty < P.ny)
+      mu[i] = A.nu_in[i * P.plane + (int64_t)ty * P.pitch + tx];
+    else
+      mu[i] = A.nu_in[opp_of(i) * P.plane + (int64_t)y * P.pitch + x];
+  }
+  float z[8];
+  gather_z<PREC, HET>(P, buf, x, y, z);
+  const Coef c = coef_at<HET>(P, x, y);
+  float nu[8];
+  double gl = 0.0, gp = 0.0;
+  collide_vjp(z, c, P.ax, P.ay, P, mu, nu, gl, gp);
+  const int64_t o = (int64_t)y * P.pitch + x;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) A.nu_out[i * P.plane + o] = nu[i];
+  const int64_t k = (int64_t)y * P.nx + x;
+  A.g_l[k] += gl;
+  A.g_phi[k] += gp;
+}
+
+// Initial state: z(0) = f_eq(p0, u0; phi) (Eq. 22): dL/dphi += sum_i nu_i d f_eq,i / d phi.
+template <bool HET>
+__global__ void k_adj_init(const StepParams P, const float* __restrict__ nu, double* __restrict__ g_phi, float p0, float ux0, float uy0,
+                           int phip_uniform) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  if (x >= P.nx) return;
+  const Coef c = coef_at<HET>(P, x, y);
+  const float usq = ux0 * ux0 + uy0 * uy0;
+  const float pterm = phip_uniform ? 0.0f : 3.0f * p0;
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float eu = (float)ex_of(i) * ux0 + (float)ey_of(i) * uy0;
+    const float d = w_of(i) * (pterm - P.rho0 * (4.5f * eu * eu - 1.5f * usq) * c.inv_phi * c.inv_phi);
+    s += d * nu[i * P.plane + (int64_t)y * P.pitch + x];
+  }
+  g_phi[(int64_t)y * P.nx + x] += (double)s;
+}
+
+// --------------------------------------------------------------------------------------------
+// launchers
+// --------------------------------------------------------------------------------------------
+#define LBM_ADJ_DISPATCH(prec, het, CALL)                                        \
+  do {                                                                            \
+    if (prec == PREC_FP32) { if (het) { CALL(PREC_FP32, true); } else { CALL(PREC_FP32, false); } } \
+    else if (prec == PREC_FP16) { if (het) { CALL(PREC_FP16, true); } else { CALL(PREC_FP16, false); } } \
+    else { if (het) { CALL(PREC_BF16, true); } else { CALL(PREC_BF16, false); } } \
+  } while (0)
+
+cudaError_t launch_adj_seed(const StepParams& P, int prec, bool het, float* nu_out, double* g_l, double* g_phi, int kind,
+                            const float* tux, const float* tuy, double* partial, int nblocks, double* loss_out, cudaStream_t s) {
+  AdjArgs A{nullptr, nu_out, g_l, g_phi};
+#define CALL_SEED(PR, H) k_adj_seed<PR, H><<<nblocks, 256, 0, s>>>(P, A, kind, tux, tuy, partial)
+  LBM_ADJ_DISPATCH(prec, het, CALL_SEED);
+#undef CALL_SEED
+  k_adj_loss_total<<<1, 32, 0, s>>>(partial, nblocks, loss_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_nee(const StepParams& P, int prec, bool het, const void* buf, float* nu, double* g_l, double* g_phi,
+                           cudaStream_t s) {
+  const int blocks = (P.ny + 127) / 128;
+#define CALL_NEE(PR, H) k_adj_nee<PR, H><<<blocks, 128, 0, s>>>(P, buf, nu, g_l, g_phi)
+  LBM_ADJ_DISPATCH(prec, het, CALL_NEE);
+#undef CALL_NEE
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_step(const StepParams& P, int prec, bool het, const void* buf, const float* nu_in, float* nu_out, double* g_l,
+                            double* g_phi, cudaStream_t s) {
+  AdjArgs A{nu_in, nu_out, g_l, g_phi};
+  dim3 grid((P.nx + 127) / 128, P.ny);
+#define CALL_ADJ(PR, H) k_adj_step<PR, H><<<grid, 128, 0, s>>>(P, buf, A)
+  LBM_ADJ_DISPATCH(prec, het, CALL_ADJ);
+#undef CALL_ADJ
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_init(const StepParams& P, bool het, const float* nu, double* g_phi, float p0, float ux0, float uy0,
+                            int phip_uniform, cudaStream_t s) {
+  dim3 grid((P.nx + 127) / 128, P.ny);
+  if (het)
+    k_adj_init<true><<<grid, 128, 0, s>>>(P, nu, g_phi, p0, ux0, uy0, phip_uniform);
+  else
+    k_adj_init<false><<<grid, 128, 0, s>>>(P, nu, g_phi, p0, ux0, uy0, phip_uniform);
+  return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "../../include/lbm.h"
 #include "lbm_internal.h"
@@ -69,6 +70,9 @@ struct lbm_ctx {
   int64_t steps = 0;
   int64_t history = 0;           // steps since the last initialisation or import
   StepParams base;
+  // parameters of the last lbm_init_equilibrium (the initial state the adjoint differentiates)
+  double init_p0 = 1.0, init_ux = 0.0, init_uy = 0.0;
+  int init_phip = 0;
   // CUDA graphs of kGraphSteps steps starting from buffer 0 or 1 (captured on first use)
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   cudaStream_t capture_stream = nullptr;
@@ -387,7 +391,7 @@ int lbm_create(const lbm_config* cfg, lbm_ctx** out) {
 
 void lbm_destroy(lbm_ctx* ctx) { release(ctx); }
 
-int lbm_set_medium(lbm_ctx* c, const float* eps, const float* K) {
+static int set_medium(lbm_ctx* c, const float* eps, const float* K, int log_k) {
   if (!c) return fail(LBM_EINVAL, "null context");
   drop_graphs(c);  // captured steps bake in the medium mode
   if (!eps && !K) {
@@ -406,7 +410,7 @@ int lbm_set_medium(lbm_ctx* c, const float* eps, const float* K) {
   if ((rc = input_ptr(c, eps, n, 0, &de)) || (rc = input_ptr(c, K, n, n, &dk))) return rc;
   LBM_CUDA(cudaMemsetAsync(c->err, 0, sizeof(unsigned int), c->stream), "cudaMemset");
   LBM_CUDA(launch_medium(de, dk, (float)c->cfg.phi, (float)c->cfg.K, (int)c->cfg.nx, (int)c->cfg.ny, c->pitch, c->phi, c->K,
-                         c->err, c->stream),
+                         c->err, log_k, c->stream),
            "medium kernel");
   unsigned int h = 0;
   LBM_CUDA(cudaMemcpyAsync(&h, c->err, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "read of error word");
@@ -419,6 +423,10 @@ int lbm_set_medium(lbm_ctx* c, const float* eps, const float* K) {
   return LBM_OK;
 }
 
+int lbm_set_medium(lbm_ctx* c, const float* eps, const float* K) { return set_medium(c, eps, K, 0); }
+
+int lbm_set_medium_log(lbm_ctx* c, const float* eps, const float* logK) { return set_medium(c, eps, logK, 1); }
+
 int lbm_init_equilibrium(lbm_ctx* c, double p0, double ux0, double uy0, int phi_p_uniform) {
   if (!c) return fail(LBM_EINVAL, "null context");
   if (!isfinite(p0) || !isfinite(ux0) || !isfinite(uy0)) return fail(LBM_EINVAL, "non-finite initial state");
@@ -429,6 +437,10 @@ int lbm_init_equilibrium(lbm_ctx* c, double p0, double ux0, double uy0, int phi_
            "init kernel");
   c->steps = 0;
   c->history = 0;
+  c->init_p0 = p0;
+  c->init_ux = ux0;
+  c->init_uy = uy0;
+  c->init_phip = phi_p_uniform ? 1 : 0;
   return LBM_OK;
 }
 
@@ -606,6 +618,113 @@ int lbm_nusselt(lbm_ctx* c, int side, double* nu) {
   LBM_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
   const double mean = s / (double)c->cfg.ny;
   *nu = (side == LBM_LEFT ? -1.0 : 1.0) * (double)c->cfg.nx / dT * mean;
+  return check_error_word(c);
+}
+
+namespace {
+
+// Device buffers of one adjoint run, freed on every exit path.
+struct AdjointBuffers {
+  std::vector<void*> ptrs;
+  ~AdjointBuffers() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  void* get(size_t bytes, cudaError_t* e) {
+    void* p = nullptr;
+    *e = cudaMalloc(&p, bytes);
+    if (*e == cudaSuccess) ptrs.push_back(p);
+    return p;
+  }
+};
+
+int copy_out(lbm_ctx* c, void* user, const void* dev, size_t bytes, bool* waited) {
+  if (!user) return LBM_OK;
+  const int kind = pointer_kind(c, user);
+  if (kind < 0) return fail(LBM_EINVAL, "output in memory of another GPU");
+  LBM_CUDA(cudaMemcpyAsync(user, dev, bytes, kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream), "copy of output");
+  if (!kind) *waited = true;
+  return LBM_OK;
+}
+
+}  // namespace
+
+int lbm_adjoint(lbm_ctx* c, int T, int loss_kind, const float* target_ux, const float* target_uy, double* grad_logK,
+                double* grad_eps, double* loss) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  if (T < 1) return fail(LBM_EINVAL, "T must be at least 1");
+  if (loss_kind != LBM_LOSS_OUTLET_FLUX && loss_kind != LBM_LOSS_VELOCITY_MISFIT) return fail(LBM_EINVAL, "unknown loss kind");
+  if (loss_kind == LBM_LOSS_VELOCITY_MISFIT && (!target_ux || !target_uy)) return fail(LBM_EINVAL, "misfit loss needs a target");
+  if (thermal_of(c)) return fail(LBM_ESTATE, "the adjoint covers the isothermal flow step only");
+  if (c->steps != 0 || c->history != 0)
+    return fail(LBM_ESTATE, "lbm_adjoint differentiates from the initial state: call lbm_init_equilibrium first");
+  const int64_t n = (int64_t)c->cfg.nx * c->cfg.ny;
+  const size_t fbytes = 8 * (size_t)c->plane * c->elem;
+  const size_t nubytes = 8 * (size_t)c->plane * sizeof(float);
+  int ck = 1;
+  while ((int64_t)ck * ck < T) ++ck;  // checkpoint interval ceil(sqrt(T))
+  const int nck = (T + ck - 1) / ck;
+  AdjointBuffers mem;
+  cudaError_t e = cudaSuccess;
+  float* nu[2];
+  for (int b = 0; b < 2; ++b)
+    if (!(nu[b] = static_cast<float*>(mem.get(nubytes, &e)))) return cuda_fail(e, "cudaMalloc(adjoint state)");
+  double* gl = static_cast<double*>(mem.get(n * sizeof(double), &e));
+  double* gp = gl ? static_cast<double*>(mem.get(n * sizeof(double), &e)) : nullptr;
+  if (!gp) return cuda_fail(e, "cudaMalloc(gradients)");
+  std::vector<void*> ckpt(nck), seg(ck);
+  for (int k = 0; k < nck; ++k)
+    if (!(ckpt[k] = mem.get(fbytes, &e))) return cuda_fail(e, "cudaMalloc(checkpoints)");
+  for (int j = 0; j < ck; ++j)
+    if (!(seg[j] = mem.get(fbytes, &e))) return cuda_fail(e, "cudaMalloc(segment states)");
+  const float *tux = nullptr, *tuy = nullptr;
+  if (loss_kind == LBM_LOSS_VELOCITY_MISFIT) {
+    const void* ptrs[2] = {target_ux, target_uy};
+    int rc;
+    if (any_host(c, ptrs, 2) && (rc = ensure_stage(c, 2 * n * sizeof(float)))) return rc;
+    if ((rc = input_ptr(c, target_ux, n, 0, &tux)) || (rc = input_ptr(c, target_uy, n, n, &tuy))) return rc;
+  }
+  LBM_CUDA(cudaMemsetAsync(gl, 0, n * sizeof(double), c->stream), "cudaMemset");
+  LBM_CUDA(cudaMemsetAsync(gp, 0, n * sizeof(double), c->stream), "cudaMemset");
+  const bool pressure = c->cfg.bc_x == LBM_PRESSURE;
+  // forward sweep, keeping the buffer before every ck-th step
+  for (int t = 0; t < T; ++t) {
+    if (t % ck == 0)
+      LBM_CUDA(cudaMemcpyAsync(ckpt[t / ck], c->f[c->cur], fbytes, cudaMemcpyDeviceToDevice, c->stream), "checkpoint copy");
+    LBM_CUDA(launch_step(params_at(c, c->cur), c->prec, c->het, false, c->stream), "step kernel");
+    c->cur ^= 1;
+    ++c->steps;
+    ++c->history;
+  }
+  StepParams P = params_at(c, c->cur);
+  const int nb = residual_blocks((int)c->cfg.nx, (int)c->cfg.ny);
+  double* loss_dev = c->red + 2 * kResidualMaxBlocks;
+  LBM_CUDA(launch_adj_seed(P, c->prec, c->het, nu[0], gl, gp, loss_kind, tux, tuy, c->red, nb, loss_dev, c->stream), "adjoint seed");
+  if (pressure) LBM_CUDA(launch_adj_nee(P, c->prec, c->het, c->f[c->cur], nu[0], gl, gp, c->stream), "adjoint pressure columns");
+  int cur_nu = 0;
+  for (int k = nck - 1; k >= 0; --k) {
+    const int t0 = k * ck, t1 = (t0 + ck < T) ? t0 + ck : T;
+    LBM_CUDA(cudaMemcpyAsync(seg[0], ckpt[k], fbytes, cudaMemcpyDeviceToDevice, c->stream), "checkpoint restore");
+    for (int j = 1; j < t1 - t0; ++j) {
+      StepParams F = P;
+      F.src = seg[j - 1];
+      F.dst = seg[j];
+      LBM_CUDA(launch_step(F, c->prec, c->het, false, c->stream), "recompute step");
+    }
+    for (int t = t1 - 1; t >= t0; --t) {
+      const void* buf = seg[t - t0];
+      LBM_CUDA(launch_adj_step(P, c->prec, c->het, buf, nu[cur_nu], nu[cur_nu ^ 1], gl, gp, c->stream), "adjoint step");
+      cur_nu ^= 1;
+      if (pressure) LBM_CUDA(launch_adj_nee(P, c->prec, c->het, buf, nu[cur_nu], gl, gp, c->stream), "adjoint pressure columns");
+    }
+  }
+  LBM_CUDA(launch_adj_init(P, c->het, nu[cur_nu], gp, (float)c->init_p0, (float)c->init_ux, (float)c->init_uy, c->init_phip, c->stream),
+           "adjoint initial state");
+  bool waited = false;
+  int rc;
+  if ((rc = copy_out(c, grad_logK, gl, n * sizeof(double), &waited)) || (rc = copy_out(c, grad_eps, gp, n * sizeof(double), &waited)) ||
+      (rc = copy_out(c, loss, loss_dev, sizeof(double), &waited)))
+    return rc;
+  LBM_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");  // the temporaries are freed on return
   return check_error_word(c);
 }
 

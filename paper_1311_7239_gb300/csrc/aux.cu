@@ -15,7 +15,7 @@ namespace lbm {
 // medium: dense [ny][nx] user arrays -> pitched fields, with range checks (err bit 1)
 // --------------------------------------------------------------------------------------------
 __global__ void k_medium(const float* __restrict__ eps, const float* __restrict__ K, float phi_u, float K_u, int nx, int ny,
-                         int pitch, float* __restrict__ phi_out, float* __restrict__ K_out, unsigned int* err) {
+                         int pitch, float* __restrict__ phi_out, float* __restrict__ K_out, unsigned int* err, int log_k) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y;
   if (y >= ny) return;
@@ -26,7 +26,7 @@ __global__ void k_medium(const float* __restrict__ eps, const float* __restrict_
   }
   const int64_t i = (int64_t)y * nx + x;
   const float ph = eps ? eps[i] : phi_u;
-  const float k = K ? K[i] : K_u;
+  const float k = K ? (log_k ? expf(K[i]) : K[i]) : K_u;
   if (!(ph > 0.0f && ph <= 1.0f) || !(k > 0.0f && k < 3.0e38f)) atomicOr(err, 2u);
   phi_out[o] = ph;
   K_out[o] = k;
@@ -336,8 +336,8 @@ __global__ void k_nusselt(const StepParams P, int side, double* __restrict__ out
 static dim3 row_grid(int n, int ny, int threads) { return dim3((n + threads - 1) / threads, ny); }
 
 cudaError_t launch_medium(const float* eps, const float* K, float phi_u, float K_u, int nx, int ny, int pitch, float* phi_out,
-                          float* K_out, unsigned int* err, cudaStream_t s) {
-  k_medium<<<row_grid(pitch, ny, 256), 256, 0, s>>>(eps, K, phi_u, K_u, nx, ny, pitch, phi_out, K_out, err);
+                          float* K_out, unsigned int* err, int log_k, cudaStream_t s) {
+  k_medium<<<row_grid(pitch, ny, 256), 256, 0, s>>>(eps, K, phi_u, K_u, nx, ny, pitch, phi_out, K_out, err, log_k);
   return cudaGetLastError();
 }
 

@@ -13,7 +13,7 @@ constexpr int kResidualMaxBlocks = 2048;  // partial-sum slots of the residual r
 int record_error(int code, const char* msg);
 cudaError_t launch_step(const StepParams& P, int prec, bool het, bool thermal, cudaStream_t s);
 cudaError_t launch_medium(const float* eps, const float* K, float phi_u, float K_u, int nx, int ny, int pitch, float* phi_out,
-                          float* K_out, unsigned int* err, cudaStream_t s);
+                          float* K_out, unsigned int* err, int log_k, cudaStream_t s);
 cudaError_t launch_init(const StepParams& P, int prec, bool het, bool thermal, float p0, float ux0, float uy0, int phip_uniform,
                         float T_init, bool flow, bool temp, cudaStream_t s);
 cudaError_t launch_import(const StepParams& P, int prec, const float* f, const float* g, cudaStream_t s);
@@ -25,5 +25,14 @@ int residual_blocks(int nx, int ny);
 cudaError_t launch_residual(const StepParams& P, int prec, bool het, bool thermal, const void* prev, const void* gprev,
                             double* partial, int nblocks, double* out, cudaStream_t s);
 cudaError_t launch_nusselt(const StepParams& P, int prec, int side, double* out, cudaStream_t s);
+
+cudaError_t launch_adj_seed(const StepParams& P, int prec, bool het, float* nu_out, double* g_l, double* g_phi, int kind,
+                            const float* tux, const float* tuy, double* partial, int nblocks, double* loss_out, cudaStream_t s);
+cudaError_t launch_adj_nee(const StepParams& P, int prec, bool het, const void* buf, float* nu, double* g_l, double* g_phi,
+                           cudaStream_t s);
+cudaError_t launch_adj_step(const StepParams& P, int prec, bool het, const void* buf, const float* nu_in, float* nu_out, double* g_l,
+                            double* g_phi, cudaStream_t s);
+cudaError_t launch_adj_init(const StepParams& P, bool het, const float* nu, double* g_phi, float p0, float ux0, float uy0,
+                            int phip_uniform, cudaStream_t s);
 
 }  // namespace lbm

@@ -19,6 +19,7 @@ FP32, FP16_DEV, BF16_DEV = 0, 1, 2
 PERIODIC, WALL, PRESSURE = 0, 1, 2
 LEFT, RIGHT, BOTTOM, TOP = 0, 1, 2, 3
 CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy
+LOSS_OUTLET_FLUX, LOSS_VELOCITY_MISFIT = 0, 1
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, EABI, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 
 # Every function the header declares, with its ctypes signature.
@@ -69,6 +70,7 @@ SIGNATURES = {
     "lbm_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(_c_ctx)]),
     "lbm_destroy": (None, [_c_ctx]),
     "lbm_set_medium": (ctypes.c_int, [_c_ctx, _f32p, _f32p]),
+    "lbm_set_medium_log": (ctypes.c_int, [_c_ctx, _f32p, _f32p]),
     "lbm_init_equilibrium": (ctypes.c_int, [_c_ctx, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int]),
     "lbm_init_temperature": (ctypes.c_int, [_c_ctx, ctypes.c_double]),
     "lbm_step": (ctypes.c_int, [_c_ctx, ctypes.c_int]),
@@ -79,6 +81,8 @@ SIGNATURES = {
     "lbm_set_populations": (ctypes.c_int, [_c_ctx, _f32p, _f32p]),
     "lbm_residual": (ctypes.c_int, [_c_ctx, ctypes.POINTER(ctypes.c_double)]),
     "lbm_nusselt": (ctypes.c_int, [_c_ctx, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "lbm_adjoint": (ctypes.c_int, [_c_ctx, ctypes.c_int, ctypes.c_int, _f32p, _f32p, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p]),
     "lbm_residual_noalloc": (ctypes.c_int, [_f32p, _f32p, _f32p, _f32p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "lbm_sync": (ctypes.c_int, [_c_ctx]),
     "lbm_step_count": (ctypes.c_int, [_c_ctx, ctypes.POINTER(ctypes.c_int64)]),
@@ -199,6 +203,9 @@ class Lattice:
     def set_medium(self, eps=None, K=None):
         _check(lib().lbm_set_medium(self._h, _ptr(eps), _ptr(K)), "lbm_set_medium")
 
+    def set_medium_log(self, eps=None, logK=None):
+        _check(lib().lbm_set_medium_log(self._h, _ptr(eps), _ptr(logK)), "lbm_set_medium_log")
+
     def init_equilibrium(self, p0=1.0, ux0=0.0, uy0=0.0, phi_p_uniform=False):
         _check(lib().lbm_init_equilibrium(self._h, p0, ux0, uy0, int(bool(phi_p_uniform))), "lbm_init_equilibrium")
 
@@ -266,7 +273,60 @@ class Lattice:
         _check(lib().lbm_residual(self._h, ctypes.byref(r)), "lbm_residual")
         return r.value
 
+    def adjoint(self, T, loss="flux", target=None):
+        """(L, dL/dlogK, dL/deps) of T steps from the current initial state (float64 [ny, nx] tensors)."""
+        import torch
+
+        kind = {"flux": LOSS_OUTLET_FLUX, "misfit": LOSS_VELOCITY_MISFIT}[loss]
+        gk = torch.zeros(self.ny, self.nx, dtype=torch.float64, device=self.device)
+        ge = torch.zeros(self.ny, self.nx, dtype=torch.float64, device=self.device)
+        L = torch.zeros(1, dtype=torch.float64, device=self.device)
+        tx, ty = (None, None) if target is None else target
+        _check(lib().lbm_adjoint(self._h, int(T), kind, _ptr(tx), _ptr(ty), gk.data_ptr(), ge.data_ptr(), L.data_ptr()),
+               "lbm_adjoint")
+        return float(L.item()), gk, ge
+
     def nusselt(self, side=LEFT):
         v = ctypes.c_double()
         _check(lib().lbm_nusselt(self._h, int(side), ctypes.byref(v)), "lbm_nusselt")
         return v.value
+
+
+def _autograd_function():
+    import torch
+
+    class PorousFlowLoss(torch.autograd.Function):
+        """loss = L(u(T; log K, eps)) of T steps of the porous flow from the equilibrium initial
+        state, with d loss / d(log K, eps) from the discrete adjoint (lbm_adjoint).
+
+        apply(logK, eps, cfg, T, loss="flux", target=None, p0=1.0, phi_p_uniform=False):
+        logK, eps: float32 CUDA tensors [ny, nx]; cfg: a ``Config`` (copied); target: (ux*, uy*)
+        for the misfit loss.  The forward call already runs the adjoint and keeps the gradient.
+        """
+
+        @staticmethod
+        def forward(ctx, logK, eps, cfg, T, loss="flux", target=None, p0=1.0, phi_p_uniform=False):
+            lat = Lattice(Config.from_buffer_copy(cfg))
+            try:
+                lat.set_medium_log(eps.detach().contiguous(), logK.detach().contiguous())
+                lat.init_equilibrium(p0, 0.0, 0.0, phi_p_uniform)
+                L, gk, ge = lat.adjoint(T, loss, target)
+            finally:
+                lat.close()
+            ctx.save_for_backward(gk, ge)
+            return torch.tensor(L, dtype=torch.float64, device=logK.device)
+
+        @staticmethod
+        def backward(ctx, gout):
+            gk, ge = ctx.saved_tensors
+            return (gout * gk).to(torch.float32), (gout * ge).to(torch.float32), None, None, None, None, None, None
+
+    return PorousFlowLoss
+
+
+def __getattr__(name):
+    if name == "PorousFlowLoss":
+        cls = _autograd_function()
+        globals()[name] = cls
+        return cls
+    raise AttributeError(name)

@@ -1,0 +1,119 @@
+"""GPU discrete adjoint (lbm_adjoint, through the C-ABI) against the FP64 oracle adjoint
+(complex-step Jacobians) and against central finite differences of the FP64 oracle forward model.
+
+Bar: the FP32 adjoint (FP64 gradient accumulation) agrees with both to 1e-4 relative to the
+largest gradient component.
+"""
+import numpy as np
+import pytest
+
+from oracle import adjoint as adj
+from oracle import mrt_d2q8 as fl
+from tests.cases import Case, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1311_7239_gb300 import build, lbm
+
+    build.build()
+    return lbm
+
+
+def _run(lbm, case, T, kind, target, phip):
+    flow = case.flow()
+    with case.lattice(lbm) as lat:
+        if phip is not None:
+            lat.init_equilibrium(phip, 0.0, 0.0, phi_p_uniform=True)
+        else:
+            lat.init_equilibrium(1.0, 0.0, 0.0)
+        tgt = None
+        if target is not None:
+            import torch
+
+            tgt = tuple(torch.tensor(t, dtype=torch.float32, device="cuda") for t in target)
+        L, gk, ge = lat.adjoint(T, kind, tgt)
+        gk, ge = gk.cpu().numpy(), ge.cpu().numpy()
+    Lo, gko, geo = adj.gradient(flow, T, kind, None if target is None else tuple(np.float64(t) for t in target),
+                                p0=1.0 if phip is None else phip, phi_p_uniform=phip is not None)
+    return flow, (L, gk, ge), (Lo, gko, geo)
+
+
+CASES = {
+    "pressure-channel-flux": (Case(64, 32, nu=0.1, phi=0.35, K=0.05 * 32 * 32, het=True, eps_sd=0.03, corr=8.0, bc_x="pressure",
+                                   bc_y="wall", p_in=1.003, p_out=0.997), 60, "flux", True),
+    "lid-cavity-misfit": (Case(24, 20, nu=0.06, phi=0.5, K=4.0, het=True, eps_sd=0.05, corr=4.0, bc_x="wall", bc_y="wall",
+                               walls={"top": (0.08, 0.0)}), 40, "misfit", False),
+    "forced-channel-flux": (Case(20, 16, nu=0.08, phi=0.4, K=6.0, het=True, eps_sd=0.05, corr=4.0, ax=3e-4), 30, "flux", False),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_adjoint_matches_oracle_adjoint(lbm, name):
+    case, T, kind, phip = CASES[name]
+    rng = np.random.default_rng(7)
+    target = None
+    if kind == "misfit":
+        target = (0.01 * rng.standard_normal((case.ny, case.nx)), 0.01 * rng.standard_normal((case.ny, case.nx)))
+    flow, (L, gk, ge), (Lo, gko, geo) = _run(lbm, case, T, kind, target, case.p_rest() if phip else None)
+    assert abs(L - Lo) <= 1e-5 * abs(Lo) + 1e-9, (L, Lo)
+    sk, se = np.abs(gko).max(), np.abs(geo).max()
+    assert sk > 0 and se > 0
+    assert np.abs(gk - gko).max() <= 1e-4 * sk, (np.abs(gk - gko).max(), sk)
+    assert np.abs(ge - geo).max() <= 1e-4 * se, (np.abs(ge - geo).max(), se)
+
+
+def test_adjoint_matches_central_differences_at_64_cells(lbm):
+    """Config-4-like crop: pressure-driven heterogeneous channel, outlet flux, 64 random cells."""
+    case, T, kind, _ = CASES["pressure-channel-flux"]
+    phip = case.p_rest()
+    flow, (L, gk, ge), _ = _run(lbm, case, T, kind, None, phip)
+    rng = np.random.default_rng(64)
+    cells = [(int(rng.integers(0, case.ny)), int(rng.integers(0, case.nx))) for _ in range(64)]
+    sk, se = np.abs(gk).max(), np.abs(ge).max()
+
+    def loss(phi, K):
+        fl2 = fl.Flow(**{**flow.__dict__, "phi": phi, "K": K})
+        lk = np.log(K)
+        f = adj.initial_state(fl2, lk, phi, phip, (0.0, 0.0), True)
+        for _ in range(T):
+            f = adj.step(f, fl2, lk, phi)
+        return adj.loss_value(f, fl2, "flux")
+
+    for cell in cells:
+        for which, h in (("logK", 1e-4), ("phi", 1e-5)):
+            vals = []
+            for s in (1, -1):
+                phi, K = flow.phi.copy(), flow.K.copy()
+                if which == "logK":
+                    K[cell] *= np.exp(s * h)
+                else:
+                    phi[cell] += s * h
+                vals.append(loss(phi, K))
+            fd = (vals[0] - vals[1]) / (2 * h)
+            g, sc = (gk[cell], sk) if which == "logK" else (ge[cell], se)
+            assert abs(g - fd) <= 1e-4 * sc, (cell, which, g, fd, sc)
+
+
+def test_autograd_function(lbm):
+    import torch
+
+    from paper_1311_7239_gb300.lbm import PorousFlowLoss
+
+    case, T, kind, _ = CASES["forced-channel-flux"]
+    eps, K = case.medium()
+    logk = torch.tensor(np.log(K), dtype=torch.float32, device="cuda", requires_grad=True)
+    e = torch.tensor(eps, dtype=torch.float32, device="cuda", requires_grad=True)
+    loss = PorousFlowLoss.apply(logk, e, case.config(lbm), T, "flux", None)
+    (2.0 * loss).backward()
+    flow = case.flow()
+    Lo, gko, geo = adj.gradient(flow, T, "flux")
+    assert abs(loss.item() - Lo) <= 1e-5 * abs(Lo)
+    assert rel_l2(logk.grad.cpu().numpy(), 2 * gko) <= 1e-4
+    assert rel_l2(e.grad.cpu().numpy(), 2 * geo) <= 1e-4
