@@ -194,6 +194,40 @@ LBM_API int lbm_adjoint(lbm_ctx* ctx, int T, int loss_kind, const float* target_
  * parabola through the wall value and the two nearest cells; the sum is FP64.  Waits. */
 LBM_API int lbm_nusselt(lbm_ctx* ctx, int side, double* nu);
 
+/* ---------------------------------------------------------------------------------------------
+ * Batched ensembles: n independent isothermal lattices, each with its own lbm_config (size,
+ * boundaries, parameters, medium; one storage precision for all), advanced together by one
+ * persistent launch per time step over the concatenated work items of all lattices, with
+ * runs of 32 steps replayed as a captured CUDA graph.  The batch runs on cfgs[0].stream (NULL:
+ * a stream of its own).  Every lattice keeps per-cell medium fields (8 B per cell).
+ * ------------------------------------------------------------------------------------------- */
+typedef struct lbm_batch lbm_batch;
+
+/* Create the batch and initialise every lattice to the equilibrium at p = 1, u = 0. */
+LBM_API int lbm_batch_create(const lbm_config* cfgs, int n, lbm_batch** out);
+LBM_API void lbm_batch_destroy(lbm_batch* b);
+/* Medium of lattice d (as lbm_set_medium; waits for the stream). */
+LBM_API int lbm_batch_set_medium(lbm_batch* b, int d, const float* eps, const float* K);
+/* Equilibrium initial state of lattice d (d = -1: all), as lbm_init_equilibrium. */
+LBM_API int lbm_batch_init_equilibrium(lbm_batch* b, int d, double p0, double ux0, double uy0, int phi_p_uniform);
+/* Advance every lattice by n steps with the persistent batched kernel. */
+LBM_API int lbm_batch_step(lbm_batch* b, int n);
+/* The same n steps run lattice by lattice with the single-lattice kernel (for comparison). */
+LBM_API int lbm_batch_step_each(lbm_batch* b, int n);
+/* Launch shape of the batched kernel: threads per CTA (64, 128, 256) and CTAs per SM (1..32). */
+LBM_API int lbm_batch_set_launch(lbm_batch* b, int threads_per_cta, int ctas_per_sm);
+LBM_API int lbm_batch_get_launch(const lbm_batch* b, int* threads_per_cta, int* ctas_per_sm);
+/* Time `steps` steps for every launch shape on a copy of the current state, keep the fastest,
+ * restore the state; outputs may be NULL.  Waits for the stream. */
+LBM_API int lbm_batch_tune(lbm_batch* b, int steps, int* threads_per_cta, int* ctas_per_sm, float* ms_per_step);
+/* Read-outs of lattice d (float32 [ny_d][nx_d] / [8][ny_d][nx_d], host or device). */
+LBM_API int lbm_batch_macros(lbm_batch* b, int d, float* p, float* ux, float* uy);
+LBM_API int lbm_batch_get_populations(lbm_batch* b, int d, float* f);
+/* Total cells, steps taken since the last full initialisation, device bytes held. */
+LBM_API int lbm_batch_info(const lbm_batch* b, int64_t* cells, int64_t* steps, uint64_t* bytes);
+/* Wait for the batch's stream and report a deferred error. */
+LBM_API int lbm_batch_sync(lbm_batch* b);
+
 /* Wait for the context stream and report a deferred error (EUNSTABLE, ECUDA). */
 LBM_API int lbm_sync(lbm_ctx* ctx);
 

@@ -43,6 +43,49 @@ namespace lbm {
 // Records msg as the calling thread's last error and returns code (for entry points defined in
 // other translation units).
 int record_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
+// Kernel parameters of one lattice from its configuration (pointers left null).
+void params_from_config(const lbm_config& k, int prec, int pitch, int64_t plane, StepParams& P) {
+  memset(&P, 0, sizeof(P));
+  P.nx = (int)k.nx;
+  P.ny = (int)k.ny;
+  P.pitch = pitch;
+  P.plane = plane;
+  P.bc_x = (int)k.bc_x;
+  P.bc_y = (int)k.bc_y;
+  P.forch = k.forchheimer ? 1 : 0;
+  P.rho0 = (float)k.rho0;
+  P.inv_rho0 = (float)(1.0 / k.rho0);
+  P.nu = (float)k.nu;
+  P.s_e = (float)k.s_e;
+  P.s_q = (float)k.s_q;
+  const double tau_v = 3.0 * k.J * k.nu + 0.5;  // Eq. 21: J nu = c_s^2 (tau_v - 1/2)
+  P.s_v = (float)(1.0 / tau_v);
+  P.ax = (float)k.ax;
+  P.ay = (float)k.ay;
+  P.phi_u = (float)k.phi;
+  P.inv_phi_u = (float)(1.0 / k.phi);
+  P.c_lin_u = (float)(k.phi * k.nu / k.K);
+  P.c_nl_u = k.forchheimer ? (float)(1.75 / sqrt(150.0 * k.phi * k.K)) : 0.0f;
+  for (int w = 0; w < 4; ++w) {
+    P.Tdir[w] = isnan(k.T_wall[w]) ? 0 : 1;
+    P.Tw[w] = isnan(k.T_wall[w]) ? 0.0f : (float)k.T_wall[w];
+  }
+  P.p_in = (float)k.p_in;
+  P.p_out = (float)k.p_out;
+  P.p_rest = (float)k.p_rest;
+  const double sc = prec == PREC_FP32 ? 1.0 : ldexp(1.0, k.dev_scale_log2);
+  P.scale = (float)sc;
+  P.inv_scale = (float)(1.0 / sc);
+  P.zeta1 = k.thermal ? (float)(1.0 / k.tau_T) : 1.0f;
+  P.zeta3 = (float)k.zeta3;
+  P.zeta4 = (float)k.zeta4;
+  P.inv_sigma = k.sigma > 0 ? (float)(1.0 / k.sigma) : 1.0f;
+  P.varpi = 0.0f;  // Appendix B fixes varpi = 0
+  P.g_beta = (float)k.g_beta;
+  P.T0 = (float)k.T0;
+}
+
 }  // namespace lbm
 
 struct lbm_ctx {
@@ -199,6 +242,13 @@ int check_error_word(lbm_ctx* c) {
 }
 
 int validate(const lbm_config* c) {
+  return lbm::validate_config(c);
+}
+
+}  // namespace
+
+namespace lbm {
+int validate_config(const lbm_config* c) {
   if (c->abi_version != LBM_ABI_VERSION) return fail(LBM_EABI, "abi_version %u, library %u", c->abi_version, LBM_ABI_VERSION);
   if (c->nx < 2 || c->ny < 2 || c->nx > 65535 || c->ny > 65535) return fail(LBM_EINVAL, "nx, ny must be in [2, 65535]");
   if (c->precision > LBM_BF16_DEV) return fail(LBM_EINVAL, "unknown precision %u", c->precision);
@@ -215,50 +265,14 @@ int validate(const lbm_config* c) {
   }
   return LBM_OK;
 }
+}  // namespace lbm
+
+namespace {
 
 void fill_base(lbm_ctx* c) {
-  const lbm_config& k = c->cfg;
-  StepParams& P = c->base;
-  memset(&P, 0, sizeof(P));
-  P.nx = (int)k.nx;
-  P.ny = (int)k.ny;
-  P.pitch = c->pitch;
-  P.plane = c->plane;
-  P.bc_x = (int)k.bc_x;
-  P.bc_y = (int)k.bc_y;
-  P.forch = k.forchheimer ? 1 : 0;
-  P.rho0 = (float)k.rho0;
-  P.inv_rho0 = (float)(1.0 / k.rho0);
-  P.nu = (float)k.nu;
-  P.s_e = (float)k.s_e;
-  P.s_q = (float)k.s_q;
-  const double tau_v = 3.0 * k.J * k.nu + 0.5;  // Eq. 21: J nu = c_s^2 (tau_v - 1/2)
-  P.s_v = (float)(1.0 / tau_v);
-  P.ax = (float)k.ax;
-  P.ay = (float)k.ay;
-  P.phi_u = (float)k.phi;
-  P.inv_phi_u = (float)(1.0 / k.phi);
-  P.c_lin_u = (float)(k.phi * k.nu / k.K);
-  P.c_nl_u = k.forchheimer ? (float)(1.75 / sqrt(150.0 * k.phi * k.K)) : 0.0f;
-  P.uw = c->walls;
-  for (int w = 0; w < 4; ++w) {
-    P.Tdir[w] = isnan(k.T_wall[w]) ? 0 : 1;
-    P.Tw[w] = isnan(k.T_wall[w]) ? 0.0f : (float)k.T_wall[w];
-  }
-  P.p_in = (float)k.p_in;
-  P.p_out = (float)k.p_out;
-  P.p_rest = (float)k.p_rest;
-  const double sc = c->prec == PREC_FP32 ? 1.0 : ldexp(1.0, k.dev_scale_log2);
-  P.scale = (float)sc;
-  P.inv_scale = (float)(1.0 / sc);
-  P.zeta1 = k.thermal ? (float)(1.0 / k.tau_T) : 1.0f;
-  P.zeta3 = (float)k.zeta3;
-  P.zeta4 = (float)k.zeta4;
-  P.inv_sigma = k.sigma > 0 ? (float)(1.0 / k.sigma) : 1.0f;
-  P.varpi = 0.0f;  // Appendix B fixes varpi = 0
-  P.g_beta = (float)k.g_beta;
-  P.T0 = (float)k.T0;
-  P.err = c->err;
+  params_from_config(c->cfg, c->prec, c->pitch, c->plane, c->base);
+  c->base.uw = c->walls;
+  c->base.err = c->err;
 }
 
 void drop_graphs(lbm_ctx* c) {

@@ -11,6 +11,14 @@ namespace lbm {
 constexpr int kResidualMaxBlocks = 2048;  // partial-sum slots of the residual reduction
 
 int record_error(int code, const char* msg);
+}  // namespace lbm
+struct lbm_config;
+namespace lbm {
+int validate_config(const ::lbm_config* c);
+void params_from_config(const ::lbm_config& k, int prec, int pitch, int64_t plane, StepParams& P);
+int64_t batch_items(int nx, int ny, int bc_y, int nt);
+cudaError_t launch_step_batch(const StepParams* Pd, const int64_t* item_start, int n, int64_t total, int prec, int nt, int grid,
+                              cudaStream_t s);
 cudaError_t launch_step(const StepParams& P, int prec, bool het, bool thermal, cudaStream_t s);
 cudaError_t launch_medium(const float* eps, const float* K, float phi_u, float K_u, int nx, int ny, int pitch, float* phi_out,
                           float* K_out, unsigned int* err, int log_k, cudaStream_t s);

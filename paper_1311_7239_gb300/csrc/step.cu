@@ -121,21 +121,22 @@ __device__ void frame_group(const StepParams& P, const Frame& F, int k) {
   }
 }
 
-// One time step.  Blocks [0, frame_blocks) do the frame; the rest cover the lattice row by row,
-// gx blocks per row, and store every group that is not a frame group.
-template <int PREC, bool HET, bool THERMAL>
-__global__ void __launch_bounds__(kStepThreads) k_step(const StepParams P, int frame_blocks, int gx) {
+// Work item `item` of one lattice, for CTAs of NT threads: items [0, frame_blocks) do the frame,
+// the rest cover the lattice row by row, gx items per row, and store every group that is not a
+// frame group.  Every thread of the CTA calls this with the same item (warp shuffles inside).
+template <int PREC, bool HET, bool THERMAL, int NT>
+__device__ __forceinline__ void step_item(const StepParams& P, int frame_blocks, int gx, int item) {
   using S = Store<PREC>;
   using T = typename S::T;
   constexpr int C = kCellsPerThread;
-  if ((int)blockIdx.x < frame_blocks) {
+  if (item < frame_blocks) {
     const Frame F = frame_of(P.nx, P.ny, P.bc_y, C);
-    frame_group<PREC, HET, THERMAL>(P, F, blockIdx.x * kStepThreads + threadIdx.x);
+    frame_group<PREC, HET, THERMAL>(P, F, item * NT + (int)threadIdx.x);
     return;
   }
-  const int b = blockIdx.x - frame_blocks;
+  const int b = item - frame_blocks;
   const int y = b / gx;
-  const int x0 = ((b - y * gx) * kStepThreads + threadIdx.x) * C;
+  const int x0 = ((b - y * gx) * NT + (int)threadIdx.x) * C;
   const T* __restrict__ src = static_cast<const T*>(P.src);
   T* __restrict__ dst = static_cast<T*>(P.dst);
   const int lane = threadIdx.x & 31;
@@ -205,12 +206,24 @@ __global__ void __launch_bounds__(kStepThreads) k_step(const StepParams P, int f
   }
 }
 
+// One time step of one lattice: one CTA per work item.
+template <int PREC, bool HET, bool THERMAL>
+__global__ void __launch_bounds__(kStepThreads) k_step(const StepParams P, int frame_blocks, int gx) {
+  step_item<PREC, HET, THERMAL, kStepThreads>(P, frame_blocks, gx, blockIdx.x);
+}
+
+// Work items of one lattice for CTAs of nt threads.
+__host__ __device__ inline void items_of(int nx, int ny, int bc_y, int nt, int& frame_blocks, int& gx) {
+  const int per = nt * kCellsPerThread;
+  gx = (nx + per - 1) / per;
+  const Frame F = frame_of(nx, ny, bc_y, kCellsPerThread);
+  frame_blocks = (F.count + nt - 1) / nt;
+}
+
 template <int PREC, bool HET, bool THERMAL>
 static cudaError_t launch_step_t(const StepParams& P, cudaStream_t s) {
-  const int per_block = kStepThreads * kCellsPerThread;
-  const int gx = (P.nx + per_block - 1) / per_block;
-  const Frame F = frame_of(P.nx, P.ny, P.bc_y, kCellsPerThread);
-  const int fb = (F.count + kStepThreads - 1) / kStepThreads;
+  int fb, gx;
+  items_of(P.nx, P.ny, P.bc_y, kStepThreads, fb, gx);
   const long long blocks = (long long)fb + (long long)gx * P.ny;
   k_step<PREC, HET, THERMAL><<<(unsigned)blocks, kStepThreads, 0, s>>>(P, fb, gx);
   return cudaGetLastError();
@@ -222,12 +235,62 @@ static cudaError_t launch_step_p(const StepParams& P, bool het, bool thermal, cu
   return het ? launch_step_t<PREC, true, false>(P, s) : launch_step_t<PREC, false, false>(P, s);
 }
 
+// --------------------------------------------------------------------------------------------
+// Batched ensemble: one persistent launch advances every lattice of a batch by one step.
+// Item ranges of the lattices are concatenated (item_start, ascending); each CTA walks the items
+// gridDim.x apart and finds the lattice of an item by binary search.  Lattice d's parameters for
+// the current buffer parity are Pd[d].
+// --------------------------------------------------------------------------------------------
+template <int PREC, int NT>
+__global__ void __launch_bounds__(NT) k_step_batch(const StepParams* __restrict__ Pd, const int64_t* __restrict__ item_start, int n,
+                                                   int64_t total) {
+  for (int64_t it = blockIdx.x; it < total; it += gridDim.x) {
+    int lo = 0, hi = n - 1;  // last d with item_start[d] <= it
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (item_start[mid] <= it) lo = mid; else hi = mid - 1;
+    }
+    const StepParams P = Pd[lo];
+    int fb, gx;
+    items_of(P.nx, P.ny, P.bc_y, NT, fb, gx);
+    step_item<PREC, true, false, NT>(P, fb, gx, (int)(it - item_start[lo]));
+  }
+}
+
 cudaError_t launch_step(const StepParams& P, int prec, bool het, bool thermal, cudaStream_t s) {
   switch (prec) {
     case PREC_FP32: return launch_step_p<PREC_FP32>(P, het, thermal, s);
     case PREC_FP16: return launch_step_p<PREC_FP16>(P, het, thermal, s);
     default: return launch_step_p<PREC_BF16>(P, het, thermal, s);
   }
+}
+
+}  // namespace lbm
+
+namespace lbm {
+
+int64_t batch_items(int nx, int ny, int bc_y, int nt) {
+  int fb, gx;
+  items_of(nx, ny, bc_y, nt, fb, gx);
+  return (int64_t)fb + (int64_t)gx * ny;
+}
+
+template <int PREC>
+static cudaError_t launch_batch_p(const StepParams* Pd, const int64_t* item_start, int n, int64_t total, int nt, int grid,
+                                  cudaStream_t s) {
+  switch (nt) {
+    case 64: k_step_batch<PREC, 64><<<grid, 64, 0, s>>>(Pd, item_start, n, total); break;
+    case 256: k_step_batch<PREC, 256><<<grid, 256, 0, s>>>(Pd, item_start, n, total); break;
+    default: k_step_batch<PREC, 128><<<grid, 128, 0, s>>>(Pd, item_start, n, total); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_batch(const StepParams* Pd, const int64_t* item_start, int n, int64_t total, int prec, int nt, int grid,
+                              cudaStream_t s) {
+  if (prec == PREC_FP32) return launch_batch_p<PREC_FP32>(Pd, item_start, n, total, nt, grid, s);
+  if (prec == PREC_FP16) return launch_batch_p<PREC_FP16>(Pd, item_start, n, total, nt, grid, s);
+  return launch_batch_p<PREC_BF16>(Pd, item_start, n, total, nt, grid, s);
 }
 
 }  // namespace lbm

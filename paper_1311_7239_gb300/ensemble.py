@@ -1,0 +1,54 @@
+"""Configurations of a batched ensemble of independent porous cavities and channels.
+
+Each lattice draws its size, kind and Reynolds number from ``synth.ensemble_domains`` and its
+porosity / permeability field from ``synth.heterogeneous_medium`` (log K Gaussian with mean
+log(Da H^2), eps = clip(0.3 + 0.1 N, 0.1, 0.9), correlation length 32 cells).  Lattice parameters:
+  cavity  -- halfway walls, top wall moving at U = 0.1, nu = U H / Re;
+  channel -- periodic in x, walls in y, body force a_x chosen so that the Darcy-Brinkman centre
+             speed of the mean medium (the closed form behind Eq. 24 with F_phi = 0) is U = 0.05,
+             nu = max(U H / Re, 0.01).
+All lattices start from the rest state phi p = mean(eps) (uniform phi p over a varying porosity).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import synth
+
+
+def ensemble(lbm, n=512, seed=42, lo=64, hi=1024, precision=0, da=1e-3):
+    """(configs, media) for ``lbm.Batch``: media[d] = (eps, K) float32 arrays [ny, nx]."""
+    cfgs, media = [], []
+    for dom in synth.ensemble_domains(n, seed, lo, hi):
+        nx, ny, Re = dom["nx"], dom["ny"], dom["Re"]
+        eps, K = synth.heterogeneous_medium(ny, nx, H=ny, seed=dom["seed"], da_mean=da, corr_len=32.0)
+        eps = eps.astype(np.float32)
+        K = K.astype(np.float32)
+        phi_m = float(eps.mean())
+        K_m = float(np.exp(np.log(K.astype(np.float64)).mean()))
+        if dom["kind"] == "cavity":
+            U = 0.1
+            nu = U * ny / Re
+            kw = dict(bc_x=lbm.WALL, bc_y=lbm.WALL, u_wall=[(0, 0), (0, 0), (0, 0), (U, 0)])
+        else:
+            U = 0.05
+            nu = max(U * ny / Re, 0.01)
+            th = math.sqrt(phi_m / K_m)
+            x = min(th * ny / 2, 300.0)
+            G = U * nu / (K_m * (1.0 - 1.0 / math.cosh(x)))
+            kw = dict(bc_x=lbm.PERIODIC, bc_y=lbm.WALL, ax=G)
+        cfg = lbm.default_config(nx=nx, ny=ny, nu=nu, phi=phi_m, K=K_m, precision=precision, p_rest=phi_m, **kw)
+        cfgs.append(cfg)
+        media.append((eps, K))
+    return cfgs, media
+
+
+def build(lbm, cfgs, media):
+    """A ``lbm.Batch`` with every medium set and the rest state phi p = mean(eps) per lattice."""
+    b = lbm.Batch(cfgs)
+    for d, (eps, K) in enumerate(media):
+        b.set_medium(d, np.ascontiguousarray(eps), np.ascontiguousarray(K))
+        b.init_equilibrium(d, float(cfgs[d].p_rest), 0.0, 0.0, phi_p_uniform=True)
+    return b

@@ -87,6 +87,22 @@ SIGNATURES = {
     "lbm_sync": (ctypes.c_int, [_c_ctx]),
     "lbm_step_count": (ctypes.c_int, [_c_ctx, ctypes.POINTER(ctypes.c_int64)]),
     "lbm_memory_bytes": (ctypes.c_int, [_c_ctx, ctypes.POINTER(ctypes.c_uint64)]),
+    "lbm_batch_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "lbm_batch_destroy": (None, [ctypes.c_void_p]),
+    "lbm_batch_set_medium": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _f32p, _f32p]),
+    "lbm_batch_init_equilibrium": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                                  ctypes.c_double, ctypes.c_int]),
+    "lbm_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "lbm_batch_step_each": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "lbm_batch_set_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "lbm_batch_get_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "lbm_batch_tune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_float)]),
+    "lbm_batch_macros": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _f32p, _f32p, _f32p]),
+    "lbm_batch_get_populations": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _f32p]),
+    "lbm_batch_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                      ctypes.POINTER(ctypes.c_uint64)]),
+    "lbm_batch_sync": (ctypes.c_int, [ctypes.c_void_p]),
     "lbm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "lbm_last_error": (ctypes.c_char_p, []),
 }
@@ -290,6 +306,93 @@ class Lattice:
         v = ctypes.c_double()
         _check(lib().lbm_nusselt(self._h, int(side), ctypes.byref(v)), "lbm_nusselt")
         return v.value
+
+
+class Batch:
+    """Ensemble of independent lattices advanced together (``lbm_batch``)."""
+
+    def __init__(self, cfgs):
+        import torch
+
+        arr = (Config * len(cfgs))(*cfgs)
+        if not arr[0].stream:
+            arr[0].stream = torch.cuda.current_stream().cuda_stream or CUDA_STREAM_LEGACY
+        self.cfgs = list(arr)
+        self.shapes = [(int(c.ny), int(c.nx)) for c in arr]
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        h = ctypes.c_void_p()
+        _check(lib().lbm_batch_create(arr, len(cfgs), ctypes.byref(h)), "lbm_batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __len__(self):
+        return len(self.shapes)
+
+    def set_medium(self, d, eps=None, K=None):
+        _check(lib().lbm_batch_set_medium(self._h, int(d), _ptr(eps), _ptr(K)), "lbm_batch_set_medium")
+
+    def init_equilibrium(self, d=-1, p0=1.0, ux0=0.0, uy0=0.0, phi_p_uniform=False):
+        _check(lib().lbm_batch_init_equilibrium(self._h, int(d), p0, ux0, uy0, int(bool(phi_p_uniform))),
+               "lbm_batch_init_equilibrium")
+
+    def step(self, n=1):
+        _check(lib().lbm_batch_step(self._h, int(n)), "lbm_batch_step")
+
+    def step_each(self, n=1):
+        _check(lib().lbm_batch_step_each(self._h, int(n)), "lbm_batch_step_each")
+
+    def set_launch(self, threads_per_cta, ctas_per_sm):
+        _check(lib().lbm_batch_set_launch(self._h, int(threads_per_cta), int(ctas_per_sm)), "lbm_batch_set_launch")
+
+    def get_launch(self):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(lib().lbm_batch_get_launch(self._h, ctypes.byref(a), ctypes.byref(b)), "lbm_batch_get_launch")
+        return a.value, b.value
+
+    def tune(self, steps=20):
+        a, b, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        _check(lib().lbm_batch_tune(self._h, int(steps), ctypes.byref(a), ctypes.byref(b), ctypes.byref(ms)), "lbm_batch_tune")
+        return a.value, b.value, ms.value
+
+    def macros(self, d):
+        import torch
+
+        ny, nx = self.shapes[d]
+        out = [torch.empty(ny, nx, dtype=torch.float32, device=self.device) for _ in range(3)]
+        _check(lib().lbm_batch_macros(self._h, int(d), *(o.data_ptr() for o in out)), "lbm_batch_macros")
+        return tuple(out)
+
+    def get_populations(self, d):
+        import torch
+
+        ny, nx = self.shapes[d]
+        f = torch.empty(8, ny, nx, dtype=torch.float32, device=self.device)
+        _check(lib().lbm_batch_get_populations(self._h, int(d), f.data_ptr()), "lbm_batch_get_populations")
+        return f
+
+    def info(self):
+        c, s, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_uint64()
+        _check(lib().lbm_batch_info(self._h, ctypes.byref(c), ctypes.byref(s), ctypes.byref(b)), "lbm_batch_info")
+        return {"cells": c.value, "steps": s.value, "bytes": b.value}
+
+    def sync(self):
+        _check(lib().lbm_batch_sync(self._h), "lbm_batch_sync")
 
 
 def _autograd_function():

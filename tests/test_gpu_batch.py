@@ -1,0 +1,84 @@
+"""Batched ensembles (lbm_batch_*): the persistent batched kernel gives bitwise the results of the
+single-lattice kernel on every lattice, for every launch shape; the one-by-one mode and the
+autotuner leave results unchanged; a small lattice of the batch matches the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle import mrt_d2q8 as fl
+from paper_1311_7239_gb300 import ensemble
+from tests.cases import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1311_7239_gb300 import build, lbm
+
+    build.build()
+    return lbm
+
+
+def _singles(lbm, cfgs, media, steps):
+    import torch
+
+    out = []
+    for cfg, (eps, K) in zip(cfgs, media):
+        lat = lbm.Lattice(lbm.Config.from_buffer_copy(cfg))
+        lat.set_medium(torch.tensor(eps, device="cuda"), torch.tensor(K, device="cuda"))
+        lat.init_equilibrium(float(cfg.p_rest), 0.0, 0.0, phi_p_uniform=True)
+        lat.step(steps)
+        out.append(lat.get_populations().cpu().numpy())
+        lat.close()
+    return out
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_equals_single_lattices_bitwise(lbm, prec):
+    cfgs, media = ensemble.ensemble(lbm, n=7, seed=3, lo=8, hi=300, precision=prec)
+    steps = 45
+    want = _singles(lbm, cfgs, media, steps)
+    for shape in [(128, 4), (64, 8), (256, 2)]:
+        with ensemble.build(lbm, cfgs, media) as b:
+            b.set_launch(*shape)
+            b.step(steps)  # a graph of 32 + 13 launches
+            b.sync()
+            for d in range(len(cfgs)):
+                got = b.get_populations(d).cpu().numpy()
+                assert np.array_equal(got, want[d]), (shape, d)
+            assert b.info()["steps"] == steps
+
+
+def test_step_each_and_tune_leave_results_unchanged(lbm):
+    cfgs, media = ensemble.ensemble(lbm, n=5, seed=11, lo=16, hi=200)
+    with ensemble.build(lbm, cfgs, media) as a, ensemble.build(lbm, cfgs, media) as b:
+        nt, k, ms = a.tune(steps=3)
+        assert nt in (64, 128, 256) and 1 <= k <= 16 and ms > 0
+        assert a.get_launch() == (nt, k)
+        a.step(40)
+        b.step_each(40)
+        for d in range(len(cfgs)):
+            assert np.array_equal(a.get_populations(d).cpu().numpy(), b.get_populations(d).cpu().numpy())
+
+
+def test_batch_lattice_matches_oracle(lbm):
+    cfgs, media = ensemble.ensemble(lbm, n=3, seed=5, lo=12, hi=40)
+    steps = 300
+    with ensemble.build(lbm, cfgs, media) as b:
+        b.step(steps)
+        res = [tuple(t.cpu().numpy() for t in b.macros(d)) for d in range(3)]
+    for d, cfg in enumerate(cfgs):
+        eps, K = media[d]
+        kind_wall = cfg.bc_x == lbm.WALL
+        flow = fl.Flow(nx=cfg.nx, ny=cfg.ny, phi=eps.astype(np.float64), K=K.astype(np.float64), nu=cfg.nu,
+                       accel=np.array([cfg.ax, 0.0]), bc_x="wall" if kind_wall else "periodic", bc_y="wall",
+                       u_top=(cfg.u_wall[3][0], 0.0))
+        f = fl.run(fl.initial_state(flow, p0=cfg.p_rest / flow.phi), flow, steps)
+        ux, uy, p = fl.macroscopic(f, flow)
+        pg, uxg, uyg = res[d]
+        assert rel_l2(np.stack([uxg, uyg]), np.stack([ux, uy])) <= 1e-5
+        assert rel_l2(pg, p) <= 1e-5
