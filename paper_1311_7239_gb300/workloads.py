@@ -1,4 +1,6 @@
-"""Configurations of a batched ensemble of independent porous cavities and channels.
+"""Synthetic workloads shaped like the paper's test flows (Sec. 3): configurations and media.
+
+Batched ensemble of independent porous cavities and channels (``ensemble``, ``build``):
 
 Each lattice draws its size, kind and Reynolds number from ``synth.ensemble_domains`` and its
 porosity / permeability field from ``synth.heterogeneous_medium`` (log K Gaussian with mean
@@ -8,6 +10,14 @@ log(Da H^2), eps = clip(0.3 + 0.1 N, 0.1, 0.9), correlation length 32 cells).  L
              speed of the mean medium (the closed form behind Eq. 24 with F_phi = 0) is U = 0.05,
              nu = max(U H / Re, 0.01).
 All lattices start from the rest state phi p = mean(eps) (uniform phi p over a varying porosity).
+
+Pressure-driven heterogeneous channel for the adjoint (``adjoint_channel``): log K Gaussian with
+mean log(1e-3 H^2), sigma 1, correlation length 32; eps = clip(0.3 + 0.1 N, 0.1, 0.9); the four
+columns next to the inlet and the outlet hold the mean medium, so that the prescribed pressure
+columns meet a uniform porosity; nu = 0.1; p_in - p_out from the Darcy estimate of a mean speed
+of 0.01 (phi u = -K grad(phi p) / (rho0 nu), Eq. 2 without inertia and viscous terms).
+
+Lid-driven cavity and natural convection set-ups are in bench.py and the tests.
 """
 from __future__ import annotations
 
@@ -52,3 +62,20 @@ def build(lbm, cfgs, media):
         b.set_medium(d, np.ascontiguousarray(eps), np.ascontiguousarray(K))
         b.init_equilibrium(d, float(cfgs[d].p_rest), 0.0, 0.0, phi_p_uniform=True)
     return b
+
+
+def adjoint_channel(lbm, nx=2048, ny=1024, seed=1234, u_mean=0.01, nu=0.1, precision=0):
+    """(config, eps, logK) of the pressure-driven heterogeneous channel (float32 [ny, nx] fields)."""
+    eps, K = synth.heterogeneous_medium(ny, nx, H=ny, seed=seed, da_mean=1e-3, sigma_logk=1.0, corr_len=32.0, eps_mean=0.3,
+                                        eps_sd=0.1, eps_lo=0.1, eps_hi=0.9)
+    logk = np.log(K)
+    for cols in (slice(0, 4), slice(nx - 4, nx)):
+        eps[:, cols] = eps.mean()
+        logk[:, cols] = logk.mean()
+    phi_m = float(eps.mean())
+    K_m = float(np.exp(logk.mean()))
+    dphip = u_mean * phi_m * nu * (nx - 1) / K_m
+    dp = dphip / phi_m
+    cfg = lbm.default_config(nx=nx, ny=ny, nu=nu, phi=phi_m, K=K_m, bc_x=lbm.PRESSURE, bc_y=lbm.WALL, p_in=1.0 + dp / 2,
+                             p_out=1.0 - dp / 2, p_rest=phi_m, precision=precision)
+    return cfg, eps.astype(np.float32), logk.astype(np.float32)

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from oracle import mrt_d2q8 as fl
-from paper_1311_7239_gb300 import ensemble
+from paper_1311_7239_gb300 import workloads as ensemble
 from tests.cases import rel_l2
 
 pytestmark = pytest.mark.gpu
