@@ -15,6 +15,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -192,6 +193,113 @@ def accuracy_record():
         return None
 
 
+def thermal_form(lbm, L, steps, warmup, local_rank):
+    """Natural convection (D2Q8 flow + D2Q5 temperature in one pass), FP32: 104 B per update."""
+    import torch
+
+    from paper_1311_7239_gb300 import workloads
+
+    out = {}
+    peak, _ = peaks()
+    for prec, bpl in (("fp32", 104), ("fp16", 52)):
+        stream = torch.cuda.Stream()
+        cfg = workloads.natural_convection(lbm, L=L, precision=PREC[prec])
+        cfg.stream = stream.cuda_stream
+        lat = lbm.Lattice(cfg)
+        lat.step(warmup)
+        lat.sync()
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local_rank) as clk:
+            start.record(stream)
+            lat.step(steps)
+            stop.record(stream)
+            stop.synchronize()
+        lat.sync()
+        lat.close()
+        ms = start.elapsed_time(stop)
+        bw = bpl * L * L * steps / (ms * 1e-3) / 1e9
+        out[prec] = {"value": L * L * steps / (ms * 1e-3) / 1e6, "unit": "MLUPS", "achieved_gbs": bw, "roofline_frac": bw / peak,
+                     "algorithmic_bytes_per_lu": bpl, "steps": steps, "clocks": clk.summary()}
+    return {"workload": f"natural convection {L}x{L}, Ra=1e5, Pr=1, eps=0.6, Da=1e-2 (D2Q8 + D2Q5 fused)", **out}
+
+
+def ensemble_form(lbm, steps, local_rank):
+    """512 porous cavities/channels (sides 64..1024): batched persistent launch vs one by one."""
+    import torch
+
+    from paper_1311_7239_gb300 import workloads
+
+    res = {}
+    peak, _ = peaks()
+    for prec in ("fp32", "fp16"):
+        cfgs, media = workloads.ensemble(lbm, n=512, seed=42, precision=PREC[prec])
+        b = workloads.build(lbm, cfgs, media)
+        cells = b.info()["cells"]
+        nt, k, _ = b.tune(steps=4)
+        b.step(32)
+        b.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s = torch.cuda.current_stream()
+        with ClockSampler(local_rank) as clk:
+            e0.record(s)
+            b.step(steps)
+            e1.record(s)
+            e1.synchronize()
+        ms_b = e0.elapsed_time(e1)
+        each = max(2, steps // 16)
+        e0.record(s)
+        b.step_each(each)
+        e1.record(s)
+        e1.synchronize()
+        ms_e = e0.elapsed_time(e1)
+        b.sync()
+        b.close()
+        bpl = BYTES_PER_LU[prec] + 8  # + per-cell eps and K
+        mlups = cells * steps / (ms_b * 1e-3) / 1e6
+        res[prec] = {"batched_MLUPS": mlups, "one_by_one_MLUPS": cells * each / (ms_e * 1e-3) / 1e6,
+                     "batched_roofline_frac": mlups * 1e6 * bpl / 1e9 / peak, "algorithmic_bytes_per_lu": bpl,
+                     "launch": {"threads_per_cta": nt, "ctas_per_sm": k}, "steps": steps, "one_by_one_steps": each,
+                     "clocks": clk.summary()}
+        torch.cuda.empty_cache()
+    return {"workload": "512 heterogeneous porous cavities/channels, sides U{64..1024}, Re U[10,400], seed 42",
+            "cells": cells, **res}
+
+
+def adjoint_form(lbm, T):
+    """Pressure-driven heterogeneous channel 2048x1024: adjoint (gradient of the outlet flux w.r.t.
+    per-cell log K and eps, sqrt(T) checkpointing) time vs forward time."""
+    import torch
+
+    from paper_1311_7239_gb300 import workloads
+
+    cfg, eps, logk = workloads.adjoint_channel(lbm)
+    stream = torch.cuda.Stream()
+    cfg.stream = stream.cuda_stream
+    lat = lbm.Lattice(cfg)
+    lat.set_medium_log(torch.tensor(eps, device="cuda"), torch.tensor(logk, device="cuda"))
+    lat.init_equilibrium(float(cfg.p_rest), 0.0, 0.0, phi_p_uniform=True)
+    lat.step(8)
+    lat.sync()
+    lat.init_equilibrium(float(cfg.p_rest), 0.0, 0.0, phi_p_uniform=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.step(T)
+    e1.record(stream)
+    e1.synchronize()
+    fwd_ms = e0.elapsed_time(e1)
+    lat.init_equilibrium(float(cfg.p_rest), 0.0, 0.0, phi_p_uniform=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L, gk, ge = lat.adjoint(T, "flux")
+    adj_ms = (time.perf_counter() - t0) * 1e3
+    finite = bool(torch.isfinite(gk).all() and torch.isfinite(ge).all())
+    lat.close()
+    return {"workload": "pressure-driven heterogeneous channel 2048x1024, outlet-flux loss, T steps", "T": T,
+            "forward_ms": fwd_ms, "adjoint_ms": adj_ms, "adjoint_over_forward": adj_ms / fwd_ms, "loss": L,
+            "gradients_finite": finite, "checkpoint_interval": int(math.ceil(math.sqrt(T))),
+            "accuracy": "gradient vs FP64 oracle adjoint and central differences: tests/test_gpu_adjoint.py (1e-4 of max)"}
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
 
@@ -270,6 +378,10 @@ def run_gpu(args, rank, world, local_rank):
     }
     if not args.no_forms:
         line["forms"] = forms
+        line["forms"]["thermal"] = thermal_form(lbm, 2048, max(64, args.steps // 4), args.warmup, local_rank)
+        line["forms"]["adjoint"] = adjoint_form(lbm, T=args.adjoint_steps)
+        if not args.no_ensemble:
+            line["forms"]["ensemble"] = ensemble_form(lbm, max(64, args.steps // 16), local_rank)
     acc = accuracy_record()
     if acc:
         line["accuracy"] = acc
@@ -313,6 +425,8 @@ def main():
     ap.add_argument("--size", type=int, default=4096)
     ap.add_argument("--no-cpu", action="store_true", help="skip the timed CPU oracle baseline")
     ap.add_argument("--no-forms", action="store_true", help="skip the other storage precisions")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the 512-lattice ensemble form")
+    ap.add_argument("--adjoint-steps", type=int, default=4000, help="T of the adjoint form")
     ap.add_argument("--sweep", default="", help="comma-separated lattice sizes: print one line per size and precision")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -17,7 +17,10 @@ columns next to the inlet and the outlet hold the mean medium, so that the presc
 columns meet a uniform porosity; nu = 0.1; p_in - p_out from the Darcy estimate of a mean speed
 of 0.01 (phi u = -K grad(phi p) / (rho0 nu), Eq. 2 without inertia and viscous terms).
 
-Lid-driven cavity and natural convection set-ups are in bench.py and the tests.
+Natural convection in a square porous cavity (``natural_convection``, Sec. 3.4): Pr = 1,
+J = sigma = gamma = 1, zeta3 = zeta4 = 1.1, T_h = 21 (left), T_c = 1 (right), adiabatic top and
+bottom, tau_v and tau_T from Eq. 26 with Ma = 0.1 and c_sT^2 = 2/5; g beta from
+U = Ma / sqrt(3) = sqrt(g beta dT L).
 """
 from __future__ import annotations
 
@@ -79,3 +82,14 @@ def adjoint_channel(lbm, nx=2048, ny=1024, seed=1234, u_mean=0.01, nu=0.1, preci
     cfg = lbm.default_config(nx=nx, ny=ny, nu=nu, phi=phi_m, K=K_m, bc_x=lbm.PRESSURE, bc_y=lbm.WALL, p_in=1.0 + dp / 2,
                              p_out=1.0 - dp / 2, p_rest=phi_m, precision=precision)
     return cfg, eps.astype(np.float32), logk.astype(np.float32)
+
+
+def natural_convection(lbm, L=2048, Ra=1e5, Pr=1.0, phi=0.6, Da=1e-2, Ma=0.1, precision=0):
+    tau_v = 0.5 + Ma * L * math.sqrt(3.0 * Pr) / math.sqrt(Ra)
+    tau_T = 0.5 + (1.0 / 3.0) * (tau_v - 0.5) / (0.4 * Pr)
+    nu = (tau_v - 0.5) / 3.0
+    U = Ma / math.sqrt(3.0)
+    g_beta = U * U / (20.0 * L)
+    return lbm.default_config(nx=L, ny=L, bc_x=lbm.WALL, bc_y=lbm.WALL, nu=nu, phi=phi, K=Da * L * L, thermal=1, tau_T=tau_T,
+                              g_beta=g_beta, T0=11.0, T_wall=[21.0, 1.0, None, None], p_rest=phi, precision=precision,
+                              dev_scale_log2=8)
