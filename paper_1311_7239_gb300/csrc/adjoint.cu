@@ -19,6 +19,7 @@
 // Gradients accumulate in FP64; the adjoint state is stored in FP32 planes [8][ny][pitch].
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
+#include "tiles.cuh"
 
 namespace lbm {
 
@@ -180,8 +181,8 @@ __device__ __forceinline__ void gather_z(const StepParams& P, const void* buf, i
 struct AdjArgs {
   const float* nu_in;  // nu(t+1) after J_N^T (planes [8][ny][pitch])
   float* nu_out;       // nu(t)
-  double* g_l;         // dL/dlog K  [ny][nx]
-  double* g_phi;       // dL/dphi    [ny][nx]
+  double* g_l;         // dL/dlog K  [ny][pitch]
+  double* g_phi;       // dL/dphi    [ny][pitch]
 };
 
 // Seed: nu(T) = dL/dz(T) and the explicit theta-gradient of the loss; per-block loss partials.
@@ -223,8 +224,8 @@ __global__ void k_adj_seed(const StepParams P, AdjArgs A, int kind, const float*
     const int64_t o = (int64_t)y * P.pitch + x;
 #pragma unroll
     for (int i = 0; i < 8; ++i) A.nu_out[i * P.plane + o] = nu[i];
-    A.g_l[k] += gl;
-    A.g_phi[k] += gp;
+    A.g_l[o] += gl;
+    A.g_phi[o] += gp;
   }
   // block sum of the loss
   __shared__ double sh[32];
@@ -302,7 +303,7 @@ __global__ void k_adj_nee(const StepParams P, const void* buf, float* __restrict
 #pragma unroll
     for (int i = 0; i < 8; ++i)
       nu[i * P.plane + on] += nb_[i] + mb1 + (float)ex_of(i) * vb.jx + (float)ey_of(i) * vb.jy;
-    const int64_t kb = (int64_t)y * P.nx + xb, kn = (int64_t)y * P.nx + xn;
+    const int64_t kb = ob, kn = on;
     // boundary cell: phi_b p_b and 1/phi_b
     g_phi[kb] += (double)(3.0f * pb * W - cb.inv_phi * cb.inv_phi * ipb_b);
     double gl = 0.0, gp = 0.0;
@@ -312,12 +313,10 @@ __global__ void k_adj_nee(const StepParams P, const void* buf, float* __restrict
   }
 }
 
-// nu(t) = J_C(z(t))^T P^T nu~(t+1), gradient += (dC/dtheta)^T P^T nu~(t+1); z(t) from buf = b(t).
+// nu(t) = J_C(z(t))^T P^T nu~(t+1), gradient += (dC/dtheta)^T P^T nu~(t+1); z(t) gathered from
+// buf = b(t).  Generic form for one cell (frame cells): every boundary rule.
 template <int PREC, bool HET>
-__global__ void __launch_bounds__(128) k_adj_step(const StepParams P, const void* buf, AdjArgs A) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y;
-  if (x >= P.nx) return;
+__device__ void adj_cell(const StepParams& P, const void* buf, const AdjArgs& A, int x, int y) {
   // P^T: the slot (i, x) feeds the cell x + e_i, or the cell x itself through a wall
   float mu[8];
 #pragma unroll
@@ -339,9 +338,101 @@ __global__ void __launch_bounds__(128) k_adj_step(const StepParams P, const void
   const int64_t o = (int64_t)y * P.pitch + x;
 #pragma unroll
   for (int i = 0; i < 8; ++i) A.nu_out[i * P.plane + o] = nu[i];
-  const int64_t k = (int64_t)y * P.nx + x;
-  A.g_l[k] += gl;
-  A.g_phi[k] += gp;
+  A.g_l[o] += gl;
+  A.g_phi[o] += gp;
+}
+
+// Work item of the adjoint step (the forward kernel's tiling): frame items do whole frame groups
+// cell by cell; main items gather the forward state forwards and the adjoint state backwards
+// (mu_i(x) = nu~_i(x + e_i)) as aligned vectors with shuffled halos, and skip frame groups.
+template <int PREC, bool HET, int NT>
+__device__ __forceinline__ void adj_item(const StepParams& P, const void* buf, const AdjArgs& A, int frame_blocks, int gx, int item) {
+  using S = Store<PREC>;
+  using T = typename S::T;
+  using SF = Store<PREC_FP32>;
+  constexpr int C = kCellsPerThread;
+  if (item < frame_blocks) {
+    const Frame F = frame_of(P.nx, P.ny, P.bc_y, C);
+    const int k = item * NT + (int)threadIdx.x;
+    if (k >= F.count) return;
+    int x0, y;
+    if (F.wall_rows && k < 2 * F.groups_per_row) {
+      y = k < F.groups_per_row ? 0 : P.ny - 1;
+      x0 = (k % F.groups_per_row) * C;
+    } else {
+      const int k2 = k - (F.wall_rows ? 2 * F.groups_per_row : 0);
+      y = k2 / F.cols + F.wall_rows;
+      x0 = (k2 % F.cols == 0) ? 0 : (F.groups_per_row - 1) * C;
+    }
+#pragma unroll 1
+    for (int c = 0; c < C; ++c)
+      if (x0 + c < P.nx) adj_cell<PREC, HET>(P, buf, A, x0 + c, y);
+    return;
+  }
+  const int b = item - frame_blocks;
+  const int y = b / gx;
+  const int x0 = ((b - y * gx) * NT + (int)threadIdx.x) * C;
+  const int lane = threadIdx.x & 31;
+  const int xl = x0 < P.pitch - C ? x0 : P.pitch - C;
+  int ym = y - 1, yp = y + 1;
+  ym = ym < 0 ? P.ny - 1 : ym;
+  yp = yp >= P.ny ? 0 : yp;
+  const int64_t pl = P.plane;
+  const int64_t rm = (int64_t)ym * P.pitch, r0 = (int64_t)y * P.pitch, rp = (int64_t)yp * P.pitch;
+  const T* __restrict__ src = static_cast<const T*>(buf);
+  const float inv = P.inv_scale;
+  // forward state z(t): the pull of Eq. 15
+  float z[8][C];
+  gather4<PREC, 1>(src + 0 * pl + r0, xl, P.pitch, lane, inv, z[0]);
+  gather4<PREC, 0>(src + 1 * pl + rm, xl, P.pitch, lane, inv, z[1]);
+  gather4<PREC, -1>(src + 2 * pl + r0, xl, P.pitch, lane, inv, z[2]);
+  gather4<PREC, 0>(src + 3 * pl + rp, xl, P.pitch, lane, inv, z[3]);
+  gather4<PREC, 1>(src + 4 * pl + rm, xl, P.pitch, lane, inv, z[4]);
+  gather4<PREC, -1>(src + 5 * pl + rm, xl, P.pitch, lane, inv, z[5]);
+  gather4<PREC, -1>(src + 6 * pl + rp, xl, P.pitch, lane, inv, z[6]);
+  gather4<PREC, 1>(src + 7 * pl + rp, xl, P.pitch, lane, inv, z[7]);
+  // adjoint of the pull: mu_i(x) = nu~_i(x + e_i)
+  const float* __restrict__ nu_in = A.nu_in;
+  float mu[8][C];
+  gather4<PREC_FP32, -1>(nu_in + 0 * pl + r0, xl, P.pitch, lane, 1.0f, mu[0]);  // e1 = ( 1, 0)
+  gather4<PREC_FP32, 0>(nu_in + 1 * pl + rp, xl, P.pitch, lane, 1.0f, mu[1]);   // e2 = ( 0, 1)
+  gather4<PREC_FP32, 1>(nu_in + 2 * pl + r0, xl, P.pitch, lane, 1.0f, mu[2]);   // e3 = (-1, 0)
+  gather4<PREC_FP32, 0>(nu_in + 3 * pl + rm, xl, P.pitch, lane, 1.0f, mu[3]);   // e4 = ( 0,-1)
+  gather4<PREC_FP32, -1>(nu_in + 4 * pl + rp, xl, P.pitch, lane, 1.0f, mu[4]);  // e5 = ( 1, 1)
+  gather4<PREC_FP32, 1>(nu_in + 5 * pl + rp, xl, P.pitch, lane, 1.0f, mu[5]);   // e6 = (-1, 1)
+  gather4<PREC_FP32, 1>(nu_in + 6 * pl + rm, xl, P.pitch, lane, 1.0f, mu[6]);   // e7 = (-1,-1)
+  gather4<PREC_FP32, -1>(nu_in + 7 * pl + rm, xl, P.pitch, lane, 1.0f, mu[7]);  // e8 = ( 1,-1)
+  const bool wall_row = P.bc_y == BC_WALL && (y == 0 || y == P.ny - 1);
+  if (wall_row || x0 == 0 || x0 + C >= P.nx) return;
+  double gl[C], gp[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    float zc[8], mc[8], nc[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      zc[i] = z[i][c];
+      mc[i] = mu[i][c];
+    }
+    const Coef cf = coef_at<HET>(P, x0 + c, y);
+    gl[c] = 0.0;
+    gp[c] = 0.0;
+    collide_vjp(zc, cf, P.ax, P.ay, P, mc, nc, gl[c], gp[c]);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) z[i][c] = nc[i];
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) SF::store4(A.nu_out + i * pl + r0 + x0, z[i], 1.0f);
+  double2* g2l = reinterpret_cast<double2*>(A.g_l + r0 + x0);
+  double2* g2p = reinterpret_cast<double2*>(A.g_phi + r0 + x0);
+  double2 a0 = g2l[0], a1 = g2l[1], b0 = g2p[0], b1 = g2p[1];
+  a0.x += gl[0]; a0.y += gl[1]; a1.x += gl[2]; a1.y += gl[3];
+  b0.x += gp[0]; b0.y += gp[1]; b1.x += gp[2]; b1.y += gp[3];
+  g2l[0] = a0; g2l[1] = a1; g2p[0] = b0; g2p[1] = b1;
+}
+
+template <int PREC, bool HET>
+__global__ void __launch_bounds__(kStepThreads) k_adj_step(const StepParams P, const void* buf, AdjArgs A, int frame_blocks, int gx) {
+  adj_item<PREC, HET, kStepThreads>(P, buf, A, frame_blocks, gx, blockIdx.x);
 }
 
 // Initial state: z(0) = f_eq(p0, u0; phi) (Eq. 22): dL/dphi += sum_i nu_i d f_eq,i / d phi.
@@ -361,7 +452,7 @@ __global__ void k_adj_init(const StepParams P, const float* __restrict__ nu, dou
     const float d = w_of(i) * (pterm - P.rho0 * (4.5f * eu * eu - 1.5f * usq) * c.inv_phi * c.inv_phi);
     s += d * nu[i * P.plane + (int64_t)y * P.pitch + x];
   }
-  g_phi[(int64_t)y * P.nx + x] += (double)s;
+  g_phi[(int64_t)y * P.pitch + x] += (double)s;
 }
 
 // --------------------------------------------------------------------------------------------
@@ -396,8 +487,10 @@ cudaError_t launch_adj_nee(const StepParams& P, int prec, bool het, const void* 
 cudaError_t launch_adj_step(const StepParams& P, int prec, bool het, const void* buf, const float* nu_in, float* nu_out, double* g_l,
                             double* g_phi, cudaStream_t s) {
   AdjArgs A{nu_in, nu_out, g_l, g_phi};
-  dim3 grid((P.nx + 127) / 128, P.ny);
-#define CALL_ADJ(PR, H) k_adj_step<PR, H><<<grid, 128, 0, s>>>(P, buf, A)
+  int fb, gx;
+  items_of(P.nx, P.ny, P.bc_y, kStepThreads, fb, gx);
+  const unsigned blocks = (unsigned)((long long)fb + (long long)gx * P.ny);
+#define CALL_ADJ(PR, H) k_adj_step<PR, H><<<blocks, kStepThreads, 0, s>>>(P, buf, A, fb, gx)
   LBM_ADJ_DISPATCH(prec, het, CALL_ADJ);
 #undef CALL_ADJ
   return cudaGetLastError();

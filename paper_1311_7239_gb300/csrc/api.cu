@@ -660,6 +660,18 @@ int copy_out(lbm_ctx* c, void* user, const void* dev, size_t bytes, bool* waited
   return LBM_OK;
 }
 
+// pitched FP64 field [ny][pitch] -> dense caller array [ny][nx]
+int copy_out_rows(lbm_ctx* c, double* user, const double* dev, bool* waited) {
+  if (!user) return LBM_OK;
+  const int kind = pointer_kind(c, user);
+  if (kind < 0) return fail(LBM_EINVAL, "output in memory of another GPU");
+  LBM_CUDA(cudaMemcpy2DAsync(user, c->cfg.nx * sizeof(double), dev, (size_t)c->pitch * sizeof(double), c->cfg.nx * sizeof(double),
+                             c->cfg.ny, kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream),
+           "copy of gradient");
+  if (!kind) *waited = true;
+  return LBM_OK;
+}
+
 }  // namespace
 
 int lbm_adjoint(lbm_ctx* c, int T, int loss_kind, const float* target_ux, const float* target_uy, double* grad_logK,
@@ -682,9 +694,11 @@ int lbm_adjoint(lbm_ctx* c, int T, int loss_kind, const float* target_ux, const 
   float* nu[2];
   for (int b = 0; b < 2; ++b)
     if (!(nu[b] = static_cast<float*>(mem.get(nubytes, &e)))) return cuda_fail(e, "cudaMalloc(adjoint state)");
-  double* gl = static_cast<double*>(mem.get(n * sizeof(double), &e));
-  double* gp = gl ? static_cast<double*>(mem.get(n * sizeof(double), &e)) : nullptr;
+  const size_t gbytes = (size_t)c->plane * sizeof(double);  // pitched [ny][pitch]
+  double* gl = static_cast<double*>(mem.get(gbytes, &e));
+  double* gp = gl ? static_cast<double*>(mem.get(gbytes, &e)) : nullptr;
   if (!gp) return cuda_fail(e, "cudaMalloc(gradients)");
+  for (int b = 0; b < 2; ++b) LBM_CUDA(cudaMemsetAsync(nu[b], 0, nubytes, c->stream), "cudaMemset");
   std::vector<void*> ckpt(nck), seg(ck);
   for (int k = 0; k < nck; ++k)
     if (!(ckpt[k] = mem.get(fbytes, &e))) return cuda_fail(e, "cudaMalloc(checkpoints)");
@@ -697,8 +711,8 @@ int lbm_adjoint(lbm_ctx* c, int T, int loss_kind, const float* target_ux, const 
     if (any_host(c, ptrs, 2) && (rc = ensure_stage(c, 2 * n * sizeof(float)))) return rc;
     if ((rc = input_ptr(c, target_ux, n, 0, &tux)) || (rc = input_ptr(c, target_uy, n, n, &tuy))) return rc;
   }
-  LBM_CUDA(cudaMemsetAsync(gl, 0, n * sizeof(double), c->stream), "cudaMemset");
-  LBM_CUDA(cudaMemsetAsync(gp, 0, n * sizeof(double), c->stream), "cudaMemset");
+  LBM_CUDA(cudaMemsetAsync(gl, 0, gbytes, c->stream), "cudaMemset");
+  LBM_CUDA(cudaMemsetAsync(gp, 0, gbytes, c->stream), "cudaMemset");
   const bool pressure = c->cfg.bc_x == LBM_PRESSURE;
   // forward sweep, keeping the buffer before every ck-th step
   for (int t = 0; t < T; ++t) {
@@ -735,7 +749,7 @@ int lbm_adjoint(lbm_ctx* c, int T, int loss_kind, const float* target_ux, const 
            "adjoint initial state");
   bool waited = false;
   int rc;
-  if ((rc = copy_out(c, grad_logK, gl, n * sizeof(double), &waited)) || (rc = copy_out(c, grad_eps, gp, n * sizeof(double), &waited)) ||
+  if ((rc = copy_out_rows(c, grad_logK, gl, &waited)) || (rc = copy_out_rows(c, grad_eps, gp, &waited)) ||
       (rc = copy_out(c, loss, loss_dev, sizeof(double), &waited)))
     return rc;
   LBM_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");  // the temporaries are freed on return

@@ -1,0 +1,63 @@
+// Tiling shared by the forward and adjoint stream-collide kernels: a thread owns a group of
+// kCellsPerThread consecutive cells of one row; rows are read as aligned vectors and the one-cell
+// x-shift of a population comes from the neighbouring lane (warp shuffle); the groups touching a
+// wall row or the first/last column form the "frame" and are handled by dedicated work items.
+#pragma once
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kStepThreads = 128;
+constexpr int kCellsPerThread = 4;
+
+// out[c] = row[x0 + c - SH] for c = 0..3 (SH = +1: pull from x-1, SH = -1: from x+1, 0: aligned)
+template <int PREC, int SH>
+__device__ __forceinline__ void gather4(const typename Store<PREC>::T* __restrict__ row, int xl, int pitch, int lane,
+                                        float inv, float out[4]) {
+  using S = Store<PREC>;
+  float v[4];
+  S::load4(row + xl, v, inv);
+  if (SH == 0) {
+    out[0] = v[0]; out[1] = v[1]; out[2] = v[2]; out[3] = v[3];
+  } else if (SH == 1) {
+    float left = __shfl_up_sync(kFull, v[3], 1);
+    if (lane == 0) left = S::dec(row[xl > 0 ? xl - 1 : 0], inv);
+    out[0] = left; out[1] = v[0]; out[2] = v[1]; out[3] = v[2];
+  } else {
+    float right = __shfl_down_sync(kFull, v[0], 1);
+    if (lane == 31) right = S::dec(row[xl + 4 < pitch ? xl + 4 : pitch - 1], inv);
+    out[0] = v[1]; out[1] = v[2]; out[2] = v[3]; out[3] = right;
+  }
+}
+
+// Frame of the lattice: the groups of C cells that contain a wall-row cell or a cell of the first
+// or last column (the last group of a row also holds the row padding).  Their cells are gathered
+// with every boundary rule (pull_one: halfway bounce-back with wall velocity, periodic wrap,
+// pressure columns), collided and stored by dedicated blocks; the main blocks skip them.
+struct Frame {
+  int groups_per_row;  // G = ceil(nx / C)
+  int cols;            // frame groups per non-wall row: 1 if G == 1, else 2
+  int wall_rows;       // 1 if the bottom and top rows are walls
+  int count;           // number of frame groups
+};
+
+__host__ __device__ inline Frame frame_of(int nx, int ny, int bc_y, int C) {
+  Frame f;
+  f.groups_per_row = (nx + C - 1) / C;
+  f.cols = f.groups_per_row == 1 ? 1 : 2;
+  f.wall_rows = bc_y == BC_WALL ? 1 : 0;
+  f.count = (f.wall_rows ? 2 * f.groups_per_row : 0) + f.cols * (ny - (f.wall_rows ? 2 : 0));
+  return f;
+}
+
+// Work items of one lattice for CTAs of nt threads.
+__host__ __device__ inline void items_of(int nx, int ny, int bc_y, int nt, int& frame_blocks, int& gx) {
+  const int per = nt * kCellsPerThread;
+  gx = (nx + per - 1) / per;
+  const Frame F = frame_of(nx, ny, bc_y, kCellsPerThread);
+  frame_blocks = (F.count + nt - 1) / nt;
+}
+
+}  // namespace lbm
