@@ -248,16 +248,19 @@ __global__ void k_adj_loss_total(const double* __restrict__ partial, int nblocks
   }
 }
 
-// J_N^T in place on nu: one thread per row handles both pressure columns (they share a neighbour
-// column when nx = 3).  z(nb) is gathered from `buf`, the post-collision buffer whose gather is
-// the state at which N was applied.
+// J_N^T in place on nu: one thread per row and pressure column; when nx = 3 both columns share
+// their neighbour column, and one thread per row does both in turn.  z(nb) is gathered from
+// `buf`, the post-collision buffer whose gather is the state at which N was applied.
 template <int PREC, bool HET>
 __global__ void k_adj_nee(const StepParams P, const void* buf, float* __restrict__ nu, double* __restrict__ g_l,
                           double* __restrict__ g_phi) {
-  const int y = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool shared_nb = P.nx < 4;
+  const int y = shared_nb ? t : t >> 1;
   if (y >= P.ny) return;
   using T = typename Store<PREC>::T;
-  for (int side = 0; side < 2; ++side) {
+  const int s0 = shared_nb ? 0 : (t & 1), s1 = shared_nb ? 2 : s0 + 1;
+  for (int side = s0; side < s1; ++side) {
     const int xb = side ? P.nx - 1 : 0, xn = side ? P.nx - 2 : 1;
     const float pb = side ? P.p_out : P.p_in;
     const int64_t ob = (int64_t)y * P.pitch + xb, on = (int64_t)y * P.pitch + xn;
@@ -431,7 +434,7 @@ __device__ __forceinline__ void adj_item(const StepParams& P, const void* buf, c
 }
 
 template <int PREC, bool HET>
-__global__ void __launch_bounds__(kStepThreads) k_adj_step(const StepParams P, const void* buf, AdjArgs A, int frame_blocks, int gx) {
+__global__ void __launch_bounds__(kStepThreads, 5) k_adj_step(const StepParams P, const void* buf, AdjArgs A, int frame_blocks, int gx) {
   adj_item<PREC, HET, kStepThreads>(P, buf, A, frame_blocks, gx, blockIdx.x);
 }
 
@@ -477,8 +480,9 @@ cudaError_t launch_adj_seed(const StepParams& P, int prec, bool het, float* nu_o
 
 cudaError_t launch_adj_nee(const StepParams& P, int prec, bool het, const void* buf, float* nu, double* g_l, double* g_phi,
                            cudaStream_t s) {
-  const int blocks = (P.ny + 127) / 128;
-#define CALL_NEE(PR, H) k_adj_nee<PR, H><<<blocks, 128, 0, s>>>(P, buf, nu, g_l, g_phi)
+  const int threads = P.nx < 4 ? P.ny : 2 * P.ny;
+  const int blocks = (threads + 63) / 64;
+#define CALL_NEE(PR, H) k_adj_nee<PR, H><<<blocks, 64, 0, s>>>(P, buf, nu, g_l, g_phi)
   LBM_ADJ_DISPATCH(prec, het, CALL_NEE);
 #undef CALL_NEE
   return cudaGetLastError();
