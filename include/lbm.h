@@ -228,6 +228,13 @@ LBM_API int lbm_batch_info(const lbm_batch* b, int64_t* cells, int64_t* steps, u
 /* Wait for the batch's stream and report a deferred error. */
 LBM_API int lbm_batch_sync(lbm_batch* b);
 
+/* Checkpoint / resume: write the context's state (both population buffers, temperature
+ * populations, medium, step counters, configuration) to a file, and read it back into a context
+ * of the same size, precision and thermal mode; stepping after lbm_load continues bitwise as the
+ * saved context would have.  Both wait for the stream.  EINVAL on I/O or format errors. */
+LBM_API int lbm_save(lbm_ctx* ctx, const char* path);
+LBM_API int lbm_load(lbm_ctx* ctx, const char* path);
+
 /* Wait for the context stream and report a deferred error (EUNSTABLE, ECUDA). */
 LBM_API int lbm_sync(lbm_ctx* ctx);
 

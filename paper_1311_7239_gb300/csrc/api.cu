@@ -6,6 +6,9 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <stdlib.h>
+
+#include <atomic>
 #include <new>
 #include <vector>
 
@@ -127,7 +130,23 @@ constexpr int kGraphSteps = 32;  // steps per captured graph (even: a replay end
 
 bool thermal_of(const lbm_ctx* c) { return c->cfg.thermal != 0; }
 
+// Allocation fault injection for tests: LBM_FAULT_ALLOC=k makes the k-th device allocation of
+// the process (counting from 1) fail as if the device were out of memory.
+std::atomic<long> g_alloc_count{0};
+
+bool inject_alloc_fault() {
+  static const long k = [] {
+    const char* v = getenv("LBM_FAULT_ALLOC");
+    return v ? atol(v) : 0L;
+  }();
+  return k > 0 && g_alloc_count.fetch_add(1) + 1 == k;
+}
+
 int dev_alloc(lbm_ctx* c, void** p, size_t bytes, const char* what) {
+  if (inject_alloc_fault()) {
+    *p = nullptr;
+    return fail(LBM_ENOMEM, "%s: injected allocation failure (LBM_FAULT_ALLOC)", what);
+  }
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     *p = nullptr;
@@ -754,6 +773,136 @@ int lbm_adjoint(lbm_ctx* c, int T, int loss_kind, const float* target_ux, const 
     return rc;
   LBM_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");  // the temporaries are freed on return
   return check_error_word(c);
+}
+
+namespace {
+
+constexpr uint32_t kSaveMagic = 0x4C424D53u;  // "LBMS"
+constexpr uint32_t kSaveVersion = 1u;
+
+struct SaveHeader {
+  uint32_t magic, version, config_size, precision;
+  uint32_t nx, ny, pitch, thermal;
+  int32_t cur, het, init_phip, pad;
+  int64_t steps, history;
+  double init_p0, init_ux, init_uy;
+  uint64_t pop_bytes, therm_bytes, medium_bytes;
+};
+
+int io_fail(FILE* f, const char* what) {
+  if (f) fclose(f);
+  return fail(LBM_EINVAL, "%s", what);
+}
+
+}  // namespace
+
+int lbm_save(lbm_ctx* c, const char* path) {
+  if (!c || !path) return fail(LBM_EINVAL, "null argument");
+  SaveHeader h;
+  memset(&h, 0, sizeof(h));
+  h.magic = kSaveMagic;
+  h.version = kSaveVersion;
+  h.config_size = (uint32_t)sizeof(lbm_config);
+  h.precision = (uint32_t)c->prec;
+  h.nx = c->cfg.nx;
+  h.ny = c->cfg.ny;
+  h.pitch = (uint32_t)c->pitch;
+  h.thermal = c->cfg.thermal ? 1u : 0u;
+  h.cur = c->cur;
+  h.het = c->het ? 1 : 0;
+  h.init_phip = c->init_phip;
+  h.steps = c->steps;
+  h.history = c->history;
+  h.init_p0 = c->init_p0;
+  h.init_ux = c->init_ux;
+  h.init_uy = c->init_uy;
+  h.pop_bytes = 8 * (uint64_t)c->plane * c->elem;
+  h.therm_bytes = c->cfg.thermal ? 5 * (uint64_t)c->plane * c->elem : 0;
+  h.medium_bytes = c->het ? (uint64_t)c->plane * sizeof(float) : 0;
+  std::vector<char> host(h.pop_bytes > h.medium_bytes ? h.pop_bytes : h.medium_bytes);
+  LBM_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
+  FILE* f = fopen(path, "wb");
+  if (!f) return fail(LBM_EINVAL, "cannot open %s for writing", path);
+  lbm_config cfg = c->cfg;
+  cfg.stream = nullptr;
+  if (fwrite(&h, sizeof(h), 1, f) != 1 || fwrite(&cfg, sizeof(cfg), 1, f) != 1) return io_fail(f, "write failed");
+  // both population buffers (the previous one serves the residual), temperature, medium
+  for (int b = 0; b < 2; ++b) {
+    if (cudaMemcpy(host.data(), c->f[b], h.pop_bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return io_fail(f, "device read failed");
+    if (fwrite(host.data(), 1, h.pop_bytes, f) != h.pop_bytes) return io_fail(f, "write failed");
+    if (h.therm_bytes) {
+      if (cudaMemcpy(host.data(), c->g[b], h.therm_bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return io_fail(f, "device read failed");
+      if (fwrite(host.data(), 1, h.therm_bytes, f) != h.therm_bytes) return io_fail(f, "write failed");
+    }
+  }
+  if (h.medium_bytes) {
+    float* fields[2] = {c->phi, c->K};
+    for (int k = 0; k < 2; ++k) {
+      if (cudaMemcpy(host.data(), fields[k], h.medium_bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return io_fail(f, "device read failed");
+      if (fwrite(host.data(), 1, h.medium_bytes, f) != h.medium_bytes) return io_fail(f, "write failed");
+    }
+  }
+  if (fclose(f) != 0) return fail(LBM_EINVAL, "close of %s failed", path);
+  return LBM_OK;
+}
+
+int lbm_load(lbm_ctx* c, const char* path) {
+  if (!c || !path) return fail(LBM_EINVAL, "null argument");
+  FILE* f = fopen(path, "rb");
+  if (!f) return fail(LBM_EINVAL, "cannot open %s", path);
+  SaveHeader h;
+  lbm_config cfg;
+  if (fread(&h, sizeof(h), 1, f) != 1 || h.magic != kSaveMagic) return io_fail(f, "not a liblbm state file");
+  if (h.version != kSaveVersion || h.config_size != sizeof(lbm_config)) return io_fail(f, "state file of another format version");
+  if (fread(&cfg, sizeof(cfg), 1, f) != 1) return io_fail(f, "truncated state file");
+  if (h.nx != c->cfg.nx || h.ny != c->cfg.ny || (int)h.precision != c->prec || (h.thermal != 0) != (c->cfg.thermal != 0) ||
+      (int)h.pitch != c->pitch)
+    return io_fail(f, "state file does not match the context (size, precision or thermal)");
+  if (h.pop_bytes != 8 * (uint64_t)c->plane * c->elem) return io_fail(f, "state file layout mismatch");
+  std::vector<char> host(h.pop_bytes > h.medium_bytes ? h.pop_bytes : h.medium_bytes);
+  LBM_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
+  for (int b = 0; b < 2; ++b) {
+    if (fread(host.data(), 1, h.pop_bytes, f) != h.pop_bytes) return io_fail(f, "truncated state file");
+    if (cudaMemcpy(c->f[b], host.data(), h.pop_bytes, cudaMemcpyHostToDevice) != cudaSuccess) return io_fail(f, "device write failed");
+    if (h.therm_bytes) {
+      if (fread(host.data(), 1, h.therm_bytes, f) != h.therm_bytes) return io_fail(f, "truncated state file");
+      if (cudaMemcpy(c->g[b], host.data(), h.therm_bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+        return io_fail(f, "device write failed");
+    }
+  }
+  drop_graphs(c);
+  if (h.medium_bytes) {
+    const size_t fields = (size_t)c->plane * sizeof(float);
+    int rc = LBM_OK;
+    if (!c->phi) rc = dev_alloc(c, reinterpret_cast<void**>(&c->phi), fields, "cudaMalloc(porosity)");
+    if (rc == LBM_OK && !c->K) rc = dev_alloc(c, reinterpret_cast<void**>(&c->K), fields, "cudaMalloc(permeability)");
+    if (rc) {
+      fclose(f);
+      return rc;
+    }
+    float* dst[2] = {c->phi, c->K};
+    for (int k = 0; k < 2; ++k) {
+      if (fread(host.data(), 1, h.medium_bytes, f) != h.medium_bytes) return io_fail(f, "truncated state file");
+      if (cudaMemcpy(dst[k], host.data(), h.medium_bytes, cudaMemcpyHostToDevice) != cudaSuccess) return io_fail(f, "device write failed");
+    }
+  }
+  fclose(f);
+  c->het = h.het != 0;
+  c->cur = h.cur;
+  c->steps = h.steps;
+  c->history = h.history;
+  c->init_p0 = h.init_p0;
+  c->init_ux = h.init_ux;
+  c->init_uy = h.init_uy;
+  c->init_phip = h.init_phip;
+  // the file's parameters (walls, rates, medium constants) replace the context's
+  cfg.stream = c->cfg.stream;
+  c->cfg = cfg;
+  fill_base(c);
+  float w[8];
+  for (int i = 0; i < 8; ++i) w[i] = (float)cfg.u_wall[i / 2][i % 2];
+  LBM_CUDA(cudaMemcpy(c->walls, w, sizeof(w), cudaMemcpyHostToDevice), "copy of wall velocities");
+  return LBM_OK;
 }
 
 int lbm_sync(lbm_ctx* c) {

@@ -85,6 +85,8 @@ SIGNATURES = {
                                    ctypes.c_void_p]),
     "lbm_residual_noalloc": (ctypes.c_int, [_f32p, _f32p, _f32p, _f32p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "lbm_sync": (ctypes.c_int, [_c_ctx]),
+    "lbm_save": (ctypes.c_int, [_c_ctx, ctypes.c_char_p]),
+    "lbm_load": (ctypes.c_int, [_c_ctx, ctypes.c_char_p]),
     "lbm_step_count": (ctypes.c_int, [_c_ctx, ctypes.POINTER(ctypes.c_int64)]),
     "lbm_memory_bytes": (ctypes.c_int, [_c_ctx, ctypes.POINTER(ctypes.c_uint64)]),
     "lbm_batch_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
@@ -234,6 +236,12 @@ class Lattice:
 
     def sync(self):
         _check(lib().lbm_sync(self._h), "lbm_sync")
+
+    def save(self, path):
+        _check(lib().lbm_save(self._h, os.fsencode(path)), "lbm_save")
+
+    def load(self, path):
+        _check(lib().lbm_load(self._h, os.fsencode(path)), "lbm_load")
 
     def step_count(self):
         v = ctypes.c_int64()

@@ -1,0 +1,85 @@
+"""Runtime services around the step: checkpoint/resume is bitwise, and host-side allocation
+faults come back as clean status codes."""
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+from tests.cases import Case
+
+pytestmark = pytest.mark.gpu
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1311_7239_gb300 import build, lbm
+
+    build.build()
+    return lbm
+
+
+@pytest.mark.parametrize("thermal", [False, True])
+def test_save_load_resumes_bitwise(lbm, tmp_path, thermal):
+    if thermal:
+        from tests.test_gpu_parity import _thermal_case
+
+        case = _thermal_case(L=40)
+    else:
+        case = Case(70, 40, nu=0.05, phi=0.5, K=3.0, het=True, bc_x="wall", bc_y="wall", walls={"top": (0.08, 0.0)})
+    path = str(tmp_path / "state.lbm")
+    with case.lattice(lbm) as a:
+        a.step(37)
+        a.save(path)
+        a.step(45)
+        fa = a.get_populations()
+        ra = a.residual()
+    cfg = case.config(lbm)
+    with lbm.Lattice(cfg) as b:  # fresh context, uniform medium until the load brings the saved one
+        b.load(path)
+        assert b.step_count() == 37
+        b.step(45)
+        fb = b.get_populations()
+        rb = b.residual()
+    if thermal:
+        assert np.array_equal(fa[0].cpu().numpy(), fb[0].cpu().numpy()) and np.array_equal(fa[1].cpu().numpy(), fb[1].cpu().numpy())
+    else:
+        assert np.array_equal(fa.cpu().numpy(), fb.cpu().numpy())
+    assert ra == rb
+
+
+def test_load_rejects_mismatched_state(lbm, tmp_path):
+    path = str(tmp_path / "state.lbm")
+    with Case(30, 20).lattice(lbm) as a:
+        a.save(path)
+    with Case(31, 20).lattice(lbm) as b:
+        with pytest.raises(lbm.LbmError) as e:
+            b.load(path)
+        assert e.value.code == lbm.EINVAL
+    with Case(30, 20).lattice(lbm) as b:
+        with pytest.raises(lbm.LbmError):
+            b.load(str(tmp_path / "missing.lbm"))
+
+
+@pytest.mark.parametrize("k", [1, 3, 5])
+def test_injected_allocation_failure_is_enomem(lbm, k):
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "from paper_1311_7239_gb300 import lbm\n"
+        "try:\n"
+        "    lbm.Lattice(nx=64, ny=32)\n"
+        "    print('created')\n"
+        "except lbm.LbmError as e:\n"
+        "    print('code', e.code)\n"
+        "lat = lbm.Lattice(nx=64, ny=32); lat.step(3); lat.sync(); print('second ok')\n" % ROOT
+    )
+    r = subprocess.run([sys.executable, "-c", code], env=dict(os.environ, LBM_FAULT_ALLOC=str(k)), capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert "code -2" in r.stdout and "second ok" in r.stdout
