@@ -60,7 +60,7 @@ def source_hash():
     only reported while these are unchanged)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1311_7239_gb300", "csrc")
-    for f in ("lbm_device.cuh", "step.cu"):
+    for f in ("lbm_device.cuh", "tiles.cuh", "step.cu"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
