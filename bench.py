@@ -417,6 +417,44 @@ def run_gpu(args, rank, world, local_rank):
     return 0
 
 
+def run_case(args, local_rank):
+    """One small run of a kernel family, for profiler captures (no timing output)."""
+    import torch
+
+    from paper_1311_7239_gb300 import lbm, workloads
+
+    torch.cuda.set_device(local_rank)
+    if args.case == "adjoint":  # 1024x512 heterogeneous pressure channel, T = 64
+        cfg, eps, logk = workloads.adjoint_channel(lbm, nx=1024, ny=512)
+        lat = lbm.Lattice(cfg)
+        lat.set_medium_log(torch.tensor(eps, device="cuda"), torch.tensor(logk, device="cuda"))
+        lat.init_equilibrium(float(cfg.p_rest), 0.0, 0.0, phi_p_uniform=True)
+        L, _, _ = lat.adjoint(64, "flux")
+        lat.close()
+        print(json.dumps({"case": "adjoint", "loss": L}))
+    elif args.case == "batch":  # 64 lattices of the ensemble, FP32, launch 64 x 8
+        cfgs, media = workloads.ensemble(lbm, n=64, seed=42)
+        b = workloads.build(lbm, cfgs, media)
+        b.set_launch(64, 8)
+        b.step(8)
+        b.sync()
+        print(json.dumps({"case": "batch", **b.info()}))
+        b.close()
+    elif args.case in ("fp16", "thermal"):  # 2048^2 cavity FP16 storage / natural convection FP32
+        stream = torch.cuda.Stream()
+        if args.case == "fp16":
+            cfg = make_lattice(lbm, 2048, "fp16", stream).cfg
+        else:
+            cfg = workloads.natural_convection(lbm, L=2048)
+            cfg.stream = stream.cuda_stream
+        lat = lbm.Lattice(cfg)
+        lat.step(10)
+        lat.sync()
+        lat.close()
+        print(json.dumps({"case": args.case, "steps": 10}))
+    return 0
+
+
 def run_sweep(args, local_rank):
     """Throughput over lattice sizes (one JSON line per size and storage precision)."""
     import torch
@@ -453,6 +491,8 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the other storage precisions")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 512-lattice ensemble form")
     ap.add_argument("--adjoint-steps", type=int, default=4000, help="T of the adjoint form")
+    ap.add_argument("--case", default="", choices=["", "adjoint", "batch", "fp16", "thermal"],
+                    help="run one small case of a kernel family (for profiler captures) and exit")
     ap.add_argument("--sweep", default="", help="comma-separated lattice sizes: print one line per size and precision")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -464,6 +504,8 @@ def main():
         return run_reference(args, rank, world)
     if args.sweep:
         return run_sweep(args, local_rank)
+    if args.case:
+        return run_case(args, local_rank)
     return run_gpu(args, rank, world, local_rank)
 
 
