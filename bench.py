@@ -440,6 +440,26 @@ def run_case(args, local_rank):
         b.sync()
         print(json.dumps({"case": "batch", **b.info()}))
         b.close()
+    elif args.case == "nusselt":  # natural convection run to steady state, Nu vs Table 1 (3.451)
+        L = args.size
+        cfg = workloads.natural_convection(lbm, L=L, precision=PREC[args.precision])
+        stream = torch.cuda.Stream()
+        cfg.stream = stream.cuda_stream
+        lat = lbm.Lattice(cfg)
+        chunk, steps, prev, hist = 50000 if L > 512 else 20000, 0, None, []
+        t0 = time.perf_counter()
+        while steps < args.steps:
+            lat.step(chunk)
+            steps += chunk
+            nl, nr = lat.nusselt(lbm.LEFT), lat.nusselt(lbm.RIGHT)
+            hist.append((steps, nl, nr))
+            if prev is not None and abs(nl - prev) <= 2e-5 * nl and abs(nl - nr) <= 1e-3 * nl:
+                break
+            prev = nl
+        lat.close()
+        print(json.dumps({"case": "nusselt", "L": L, "precision": args.precision, "steps": steps, "Nu_left": nl, "Nu_right": nr,
+                          "table1_present": 3.451, "rel_diff": abs(nl - 3.451) / 3.451, "seconds": time.perf_counter() - t0,
+                          "history": hist[-5:]}))
     elif args.case in ("fp16", "thermal"):  # 2048^2 cavity FP16 storage / natural convection FP32
         stream = torch.cuda.Stream()
         if args.case == "fp16":
@@ -491,7 +511,7 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the other storage precisions")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 512-lattice ensemble form")
     ap.add_argument("--adjoint-steps", type=int, default=4000, help="T of the adjoint form")
-    ap.add_argument("--case", default="", choices=["", "adjoint", "batch", "fp16", "thermal"],
+    ap.add_argument("--case", default="", choices=["", "adjoint", "batch", "fp16", "thermal", "nusselt"],
                     help="run one small case of a kernel family (for profiler captures) and exit")
     ap.add_argument("--sweep", default="", help="comma-separated lattice sizes: print one line per size and precision")
     args = ap.parse_args()
