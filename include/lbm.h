@@ -81,7 +81,8 @@ typedef struct lbm_config {
   double u_wall[4][2];  /* wall velocities (left, right, bottom, top); a moving lid is u_wall[LBM_TOP] */
   double p_in, p_out;   /* pressures of the x = 0 and x = nx-1 columns when bc_x == LBM_PRESSURE */
   double p_rest;        /* reference phi*p of the stored deviations: f_rest,i = 3 w_i p_rest (Eq. 22, u = 0) */
-  int32_t dev_scale_log2; /* FP16/BF16 storage holds (f - f_rest) * 2^dev_scale_log2; ignored for FP32 */
+  int32_t dev_scale_log2; /* FP16 storage holds (f - f_rest) * 2^dev_scale_log2 (away from FP16 subnormals);
+                             FP32 and BF16 store f - f_rest unscaled */
   /* temperature equation (used when thermal == 1) */
   double tau_T;         /* zeta_1 = zeta_2 = 1/tau_T (Eq. B.7) */
   double zeta3, zeta4;  /* remaining rates (1.1 in Sec. 3.4) */

@@ -77,7 +77,7 @@ void params_from_config(const lbm_config& k, int prec, int pitch, int64_t plane,
   P.p_in = (float)k.p_in;
   P.p_out = (float)k.p_out;
   P.p_rest = (float)k.p_rest;
-  const double sc = prec == PREC_FP32 ? 1.0 : ldexp(1.0, k.dev_scale_log2);
+  const double sc = prec == PREC_FP16 ? ldexp(1.0, k.dev_scale_log2) : 1.0;  // only FP16 needs the shift
   P.scale = (float)sc;
   P.inv_scale = (float)(1.0 / sc);
   P.zeta1 = k.thermal ? (float)(1.0 / k.tau_T) : 1.0f;

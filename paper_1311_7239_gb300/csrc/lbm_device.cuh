@@ -91,19 +91,20 @@ template <> struct Store<PREC_FP16> {
     *reinterpret_cast<uint2*>(p) = raw;
   }
 };
+// BF16 keeps FP32's exponent range, so its deviations are stored unscaled (scale = 1).
 template <> struct Store<PREC_BF16> {
   using T = __nv_bfloat16;
-  __device__ static __forceinline__ float dec(T v, float inv) { return __bfloat162float(v) * inv; }
-  __device__ static __forceinline__ T enc(float v, float sc) { return __float2bfloat16_rn(v * sc); }
-  __device__ static __forceinline__ void load4(const T* p, float o[4], float inv) {
+  __device__ static __forceinline__ float dec(T v, float) { return __bfloat162float(v); }
+  __device__ static __forceinline__ T enc(float v, float) { return __float2bfloat16_rn(v); }
+  __device__ static __forceinline__ void load4(const T* p, float o[4], float) {
     const uint2 raw = *reinterpret_cast<const uint2*>(p);
     const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw.x));
     const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw.y));
-    o[0] = a.x * inv; o[1] = a.y * inv; o[2] = b.x * inv; o[3] = b.y * inv;
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
   }
-  __device__ static __forceinline__ void store4(T* p, const float o[4], float sc) {
-    __nv_bfloat162 a = __floats2bfloat162_rn(o[0] * sc, o[1] * sc);
-    __nv_bfloat162 b = __floats2bfloat162_rn(o[2] * sc, o[3] * sc);
+  __device__ static __forceinline__ void store4(T* p, const float o[4], float) {
+    __nv_bfloat162 a = __floats2bfloat162_rn(o[0], o[1]);
+    __nv_bfloat162 b = __floats2bfloat162_rn(o[2], o[3]);
     uint2 raw;
     raw.x = *reinterpret_cast<unsigned int*>(&a);
     raw.y = *reinterpret_cast<unsigned int*>(&b);
