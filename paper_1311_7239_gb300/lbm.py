@@ -378,6 +378,34 @@ class Batch:
         _check(lib().lbm_batch_tune(self._h, int(steps), ctypes.byref(a), ctypes.byref(b), ctypes.byref(ms)), "lbm_batch_tune")
         return a.value, b.value, ms.value
 
+    def tune_cached(self, path=None, steps=20):
+        """Launch shape from a JSON cache on disk (keyed by GPU, storage precision, lattice count and
+        total cells rounded to a power of two); a miss runs ``tune`` and records the result."""
+        import json
+
+        import torch
+
+        path = path or os.environ.get("LBM_TUNE_CACHE") or os.path.join(os.path.expanduser("~"), ".cache", "lbm_gb300_tune.json")
+        cells = sum(a * b for a, b in self.shapes)
+        key = f"{torch.cuda.get_device_name()}|prec{int(self.cfgs[0].precision)}|n{len(self)}|cells2^{int(math.log2(max(cells, 1)))}"
+        try:
+            with open(path) as fh:
+                cache = json.load(fh)
+        except (OSError, ValueError):
+            cache = {}
+        if key in cache:
+            nt, k = cache[key]["threads_per_cta"], cache[key]["ctas_per_sm"]
+            self.set_launch(nt, k)
+            return nt, k, cache[key]["ms_per_step"], True
+        nt, k, ms = self.tune(steps)
+        cache[key] = {"threads_per_cta": nt, "ctas_per_sm": k, "ms_per_step": ms}
+        os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+        tmp = path + ".tmp"
+        with open(tmp, "w") as fh:
+            json.dump(cache, fh, indent=1)
+        os.replace(tmp, path)
+        return nt, k, ms, False
+
     def macros(self, d):
         import torch
 

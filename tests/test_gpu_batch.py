@@ -82,3 +82,14 @@ def test_batch_lattice_matches_oracle(lbm):
         pg, uxg, uyg = res[d]
         assert rel_l2(np.stack([uxg, uyg]), np.stack([ux, uy])) <= 1e-5
         assert rel_l2(pg, p) <= 1e-5
+
+
+def test_tuning_choice_is_cached_on_disk(lbm, tmp_path):
+    cfgs, media = ensemble.ensemble(lbm, n=4, seed=2, lo=16, hi=96)
+    path = str(tmp_path / "tune.json")
+    with ensemble.build(lbm, cfgs, media) as b:
+        nt, k, ms, hit = b.tune_cached(path, steps=2)
+        assert not hit
+    with ensemble.build(lbm, cfgs, media) as b:
+        nt2, k2, ms2, hit2 = b.tune_cached(path, steps=2)
+        assert hit2 and (nt2, k2) == (nt, k) and b.get_launch() == (nt, k)

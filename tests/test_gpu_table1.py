@@ -57,11 +57,18 @@ def steady_nusselt(lbm, L, Da, Ra, phi, Ma=0.1, chunk=20000, max_steps=2_000_000
     return nu_l, nu_r, steps
 
 
-@pytest.mark.parametrize("Ra", [1e4, 1e5])
-def test_table1_nusselt_da1e2_phi06(lbm, Ra):
-    present, ref4, ref7, grid = _table()[(1e-2, Ra, 0.6)]
-    nu_l, nu_r, steps = steady_nusselt(lbm, grid, 1e-2, Ra, 0.6)
-    spread = max(abs(present - ref4), abs(present - ref7)) / present
-    print(f"Ra={Ra:g}: Nu_left={nu_l:.4f} Nu_right={nu_r:.4f} after {steps} steps; Table 1 present {present} "
-          f"(refs {ref4}, {ref7}); rel. diff {abs(nu_l - present) / present:.3%}")
+# Rows with tau_v > 0.53 at Ma = 0.1 on the paper's grid (Da = 1e-4, Ra >= 1e7 and the Da = 1e-6
+# rows would need tau_v within 0.01 of 1/2 there, or a smaller Mach number than stated).
+ROWS = [(1e-2, ra, phi) for ra in (1e3, 1e4, 1e5) for phi in (0.4, 0.6, 0.9)] + \
+       [(1e-4, ra, phi) for ra in (1e5, 1e6) for phi in (0.4, 0.6, 0.9)]
+
+
+@pytest.mark.parametrize("Da,Ra,phi", ROWS)
+def test_table1_nusselt(lbm, Da, Ra, phi):
+    present, ref4, ref7, grid = _table()[(Da, Ra, phi)]
+    nu_l, nu_r, steps = steady_nusselt(lbm, grid, Da, Ra, phi)
+    refs = [r for r in (ref4, ref7) if r is not None]
+    spread = max(abs(present - r) for r in refs) / present
+    print(f"Da={Da:g} Ra={Ra:g} phi={phi}: Nu_left={nu_l:.4f} Nu_right={nu_r:.4f} after {steps} steps; Table 1 present "
+          f"{present} (refs {refs}); rel. diff {abs(nu_l - present) / present:.3%}")
     assert abs(nu_l - present) <= max(0.02, spread) * present
