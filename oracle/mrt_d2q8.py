@@ -101,16 +101,20 @@ class Flow:
     p_in: float = 1.0
     p_out: float = 1.0
 
-    def tau_v(self) -> float:
-        """Eq. 21 with upsilon_e = J * upsilon (Eq. 5): tau_v = upsilon_e / c_s^2 + 1/2."""
-        return self.J * self.nu / C_S2 + 0.5
+    def tau_v(self):
+        """Eq. 21 with upsilon_e = J * upsilon (Eq. 5): tau_v = upsilon_e / c_s^2 + 1/2.
+
+        J may be a field (ny, nx): the region-dependent s_v = 1/[1/2 + J upsilon / c_s^2] of Sec. 3.2."""
+        return np.asarray(self.J) * self.nu / C_S2 + 0.5
 
     def relaxation(self) -> np.ndarray:
-        """Diagonal of Lambda, Eq. 13, with the values of Sec. 3 (s1 = s3 = s5 = 1)."""
+        """Diagonal of Lambda, Eq. 13, with the values of Sec. 3 (s1 = s3 = s5 = 1); shape (8,), or
+        (8, ny, nx) when J is a field."""
         if self.rates is not None:
             return np.asarray(self.rates, dtype=np.float64)
         s_v = 1.0 / self.tau_v()
-        return np.array([1.0, self.s_e, 1.0, self.s_q, 1.0, self.s_q, s_v, s_v])
+        one = np.ones_like(s_v)
+        return np.stack([one, self.s_e * one, one, self.s_q * one, one, self.s_q * one, s_v, s_v])
 
 
 def ergun_F(phi):
@@ -239,7 +243,9 @@ def collide(f, flow: Flow, phi=None, K=None, ax=None, ay=None):
     Fx, Fy = body_force(ux, uy, phi, K, flow.nu, flow.forchheimer, ax, ay)
     m_eq = equilibrium_moments(p, ux, uy, phi, rho0)
     S = forcing_moments(ux, uy, Fx, Fy, phi, rho0)
-    lam = flow.relaxation().reshape((8,) + (1,) * (f.ndim - 1))
+    lam = flow.relaxation()
+    if lam.ndim == 1:
+        lam = lam.reshape((8,) + (1,) * (f.ndim - 1))
     m_plus = m - lam * (m - m_eq) + (1.0 - lam / 2.0) * S
     return np.einsum("ik,k...->i...", M_INV, m_plus), ux, uy, p
 

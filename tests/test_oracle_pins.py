@@ -305,3 +305,26 @@ def test_pressure_driven_channel_with_nee_columns():
     pc = p[H // 2]
     assert abs(pc[0] - flow.p_in) < 1e-4 * dp + 1e-12
     assert np.allclose(np.diff(pc), -G, rtol=2e-2)
+
+
+@pytest.mark.parametrize("J", [1.0, 4.0])
+def test_partially_porous_couette_with_viscosity_ratio(J):
+    """Sec. 3.2 with J = upsilon_e / upsilon in the porous half (s_v per region, J = 1 in the free
+    half), F_phi = 0.  From Eq. 23 and continuity of u and of the shear stress upsilon_e u' at
+    y = H/2: porous part d0 sinh(th y)/sinh(th H/2), th = sqrt(phi/(K J)); free part
+    d0 + s (y - H/2) with s = J d0 th coth(th H/2), and u(H) = u0."""
+    H, nu, u0 = 32, 0.16, 0.01
+    K = 1e-3 * H * H
+    lower = np.arange(H)[:, None] < H // 2
+    phi = np.where(lower, 0.1, 1.0) * np.ones((H, 2))
+    Kf = np.where(lower, K, 1e30) * np.ones((H, 2))
+    Jf = np.where(lower, J, 1.0) * np.ones((H, 2))
+    flow = fl.Flow(nx=2, ny=H, phi=phi, K=Kf, nu=nu, J=Jf, forchheimer=False, u_top=(u0, 0.0))
+    f = _steady(flow, fl.initial_state(flow, p0=1.0 / phi), 80000, tol=1e-11)
+    ux = fl.macroscopic(f, flow)[0][:, 0]
+    th = np.sqrt(0.1 / (K * J))
+    d0 = u0 / (1 + J * th * (H / 2) / np.tanh(th * H / 2))
+    s = J * d0 * th / np.tanh(th * H / 2)
+    y = np.arange(H) + 0.5
+    exact = np.where(y < H / 2, d0 * np.sinh(th * y) / np.sinh(th * H / 2), d0 + s * (y - H / 2))
+    assert np.abs(ux - exact).max() < 1.5e-2 * u0, np.abs(ux - exact).max() / u0
