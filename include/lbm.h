@@ -114,6 +114,12 @@ LBM_API void lbm_destroy(lbm_ctx* ctx);
  * Either may be NULL to keep a uniform value (cfg.phi / cfg.K).  Requires 0 < eps <= 1 and
  * K > 0 (checked on the device; EINVAL).  Does not change the populations. */
 LBM_API int lbm_set_medium(lbm_ctx* ctx, const float* eps, const float* K);
+/* Per-cell viscosity ratio J = upsilon_e / upsilon (Eq. 5), float32 [ny][nx], e.g. J > 1 in a porous
+ * layer and 1 in free fluid (Sec. 3.2): the viscous rate becomes s_v = 1 / (1/2 + J nu / c_s^2)
+ * per cell (Eq. 21), while the Darcy drag of Eq. 3 keeps the fluid viscosity nu.  NULL returns to
+ * the uniform cfg.J.  Switches the context to per-cell medium fields (8 B + 4 B per cell read per
+ * step).  Requires J > 0 (EINVAL); waits for the stream. */
+LBM_API int lbm_set_viscosity_ratio(lbm_ctx* ctx, const float* J);
 /* The same with log K given instead of K (K = exp(logK) per cell; the parameterisation of the
  * adjoint's gradient). */
 LBM_API int lbm_set_medium_log(lbm_ctx* ctx, const float* eps, const float* logK);

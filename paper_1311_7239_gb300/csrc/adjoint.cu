@@ -94,7 +94,7 @@ __device__ void collide_vjp(const float z[8], const Coef& c, float ax, float ay,
   const float w3 = (b13 + bx) * (1.0f / 6.0f), w4 = (-2.0f * b13 + bx) * (1.0f / 12.0f);
   const float w5 = (b24 + by) * (1.0f / 6.0f), w6 = (-2.0f * b24 + by) * (1.0f / 12.0f);
   const float w7 = (mu[0] - mu[1] + mu[2] - mu[3]) * 0.25f, w8 = (mu[4] - mu[5] + mu[6] - mu[7]) * 0.25f;
-  const float s_e = P.s_e, s_q = P.s_q, s_v = P.s_v, hv = 1.0f - 0.5f * s_v;
+  const float s_e = P.s_e, s_q = P.s_q, s_v = c.s_v, hv = 1.0f - 0.5f * s_v;
   float mb1 = 0.f, mb2 = 0.f, mb3 = 0.f, mb4 = 0.f, mb5 = 0.f, mb6 = 0.f, mb7 = 0.f, mb8 = 0.f;
   float ubx = 0.f, uby = 0.f, Fbx = 0.f, Fby = 0.f, Pb = 0.f, S2b = 0.f, ipb = 0.f, phib = 0.f;
   // k2 = -s_e (m2 + phi p) + (1 - s_e/2) S2

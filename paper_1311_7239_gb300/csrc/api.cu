@@ -105,6 +105,7 @@ struct lbm_ctx {
   int cur = 0;
   float* phi = nullptr;
   float* K = nullptr;
+  float* sv = nullptr;  // per-cell viscous rate (heterogeneous mode), when a viscosity-ratio field is set
   bool het = false;
   unsigned int* err = nullptr;   // device error word
   float* walls = nullptr;        // wall velocities [4][2] read by the kernels
@@ -248,6 +249,7 @@ StepParams params_for(const lbm_ctx* c, bool forward_dst = true) {
   P.gdst = c->g[c->cur ^ 1];
   P.phi = c->het ? c->phi : nullptr;
   P.K = c->het ? c->K : nullptr;
+  P.sv = c->het ? c->sv : nullptr;
   (void)forward_dst;
   return P;
 }
@@ -312,6 +314,7 @@ void release(lbm_ctx* c) {
   }
   cudaFree(c->phi);
   cudaFree(c->K);
+  cudaFree(c->sv);
   cudaFree(c->err);
   cudaFree(c->walls);
   cudaFree(c->probe);
@@ -427,7 +430,7 @@ void lbm_destroy(lbm_ctx* ctx) { release(ctx); }
 static int set_medium(lbm_ctx* c, const float* eps, const float* K, int log_k) {
   if (!c) return fail(LBM_EINVAL, "null context");
   drop_graphs(c);  // captured steps bake in the medium mode
-  if (!eps && !K) {
+  if (!eps && !K && !c->sv) {
     c->het = false;
     return LBM_OK;
   }
@@ -457,6 +460,51 @@ static int set_medium(lbm_ctx* c, const float* eps, const float* K, int log_k) {
 }
 
 int lbm_set_medium(lbm_ctx* c, const float* eps, const float* K) { return set_medium(c, eps, K, 0); }
+
+int lbm_set_viscosity_ratio(lbm_ctx* c, const float* J) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  drop_graphs(c);
+  if (!J) {
+    cudaStreamSynchronize(c->stream);
+    if (c->sv) {
+      cudaFree(c->sv);
+      c->bytes -= (uint64_t)c->plane * sizeof(float);
+      c->sv = nullptr;
+    }
+    return LBM_OK;
+  }
+  const size_t n = (size_t)c->cfg.nx * c->cfg.ny;
+  int rc = LBM_OK;
+  if (!c->sv && (rc = dev_alloc(c, reinterpret_cast<void**>(&c->sv), (size_t)c->plane * sizeof(float), "cudaMalloc(viscous rate)")))
+    return rc;
+  if (!c->het) {  // per-cell rates need the heterogeneous kernels: materialise the uniform medium
+    if ((rc = set_medium(c, nullptr, nullptr, 0)) && rc != LBM_OK) return rc;
+    if (!c->het) {
+      const size_t fields = (size_t)c->plane * sizeof(float);
+      if (!c->phi && (rc = dev_alloc(c, reinterpret_cast<void**>(&c->phi), fields, "cudaMalloc(porosity)"))) return rc;
+      if (!c->K && (rc = dev_alloc(c, reinterpret_cast<void**>(&c->K), fields, "cudaMalloc(permeability)"))) return rc;
+      LBM_CUDA(launch_medium(nullptr, nullptr, (float)c->cfg.phi, (float)c->cfg.K, (int)c->cfg.nx, (int)c->cfg.ny, c->pitch, c->phi, c->K,
+                             c->err, 0, c->stream),
+               "medium kernel");
+      c->het = true;
+    }
+  }
+  const void* ptrs[1] = {J};
+  if (any_host(c, ptrs, 1) && (rc = ensure_stage(c, n * sizeof(float)))) return rc;
+  const float* dJ = nullptr;
+  if ((rc = input_ptr(c, J, n, 0, &dJ))) return rc;
+  LBM_CUDA(cudaMemsetAsync(c->err, 0, sizeof(unsigned int), c->stream), "cudaMemset");
+  LBM_CUDA(launch_viscous_rate(dJ, (int)c->cfg.nx, (int)c->cfg.ny, c->pitch, (float)c->cfg.nu, c->sv, c->err, c->stream),
+           "viscous-rate kernel");
+  unsigned int h = 0;
+  LBM_CUDA(cudaMemcpyAsync(&h, c->err, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "read of error word");
+  LBM_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
+  if (h & 2u) {
+    LBM_CUDA(cudaMemsetAsync(c->err, 0, sizeof(unsigned int), c->stream), "cudaMemset");
+    return fail(LBM_EINVAL, "viscosity ratio out of range: need J > 0");
+  }
+  return LBM_OK;
+}
 
 int lbm_set_medium_log(lbm_ctx* c, const float* eps, const float* logK) { return set_medium(c, eps, logK, 1); }
 
@@ -778,7 +826,7 @@ int lbm_adjoint(lbm_ctx* c, int T, int loss_kind, const float* target_ux, const 
 namespace {
 
 constexpr uint32_t kSaveMagic = 0x4C424D53u;  // "LBMS"
-constexpr uint32_t kSaveVersion = 1u;
+constexpr uint32_t kSaveVersion = 2u;
 
 struct SaveHeader {
   uint32_t magic, version, config_size, precision;
@@ -786,7 +834,7 @@ struct SaveHeader {
   int32_t cur, het, init_phip, pad;
   int64_t steps, history;
   double init_p0, init_ux, init_uy;
-  uint64_t pop_bytes, therm_bytes, medium_bytes;
+  uint64_t pop_bytes, therm_bytes, medium_bytes, sv_bytes;
 };
 
 int io_fail(FILE* f, const char* what) {
@@ -819,6 +867,7 @@ int lbm_save(lbm_ctx* c, const char* path) {
   h.pop_bytes = 8 * (uint64_t)c->plane * c->elem;
   h.therm_bytes = c->cfg.thermal ? 5 * (uint64_t)c->plane * c->elem : 0;
   h.medium_bytes = c->het ? (uint64_t)c->plane * sizeof(float) : 0;
+  h.sv_bytes = (c->het && c->sv) ? (uint64_t)c->plane * sizeof(float) : 0;
   std::vector<char> host(h.pop_bytes > h.medium_bytes ? h.pop_bytes : h.medium_bytes);
   LBM_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
   FILE* f = fopen(path, "wb");
@@ -841,6 +890,10 @@ int lbm_save(lbm_ctx* c, const char* path) {
       if (cudaMemcpy(host.data(), fields[k], h.medium_bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return io_fail(f, "device read failed");
       if (fwrite(host.data(), 1, h.medium_bytes, f) != h.medium_bytes) return io_fail(f, "write failed");
     }
+  }
+  if (h.sv_bytes) {
+    if (cudaMemcpy(host.data(), c->sv, h.sv_bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return io_fail(f, "device read failed");
+    if (fwrite(host.data(), 1, h.sv_bytes, f) != h.sv_bytes) return io_fail(f, "write failed");
   }
   if (fclose(f) != 0) return fail(LBM_EINVAL, "close of %s failed", path);
   return LBM_OK;
@@ -885,6 +938,21 @@ int lbm_load(lbm_ctx* c, const char* path) {
       if (fread(host.data(), 1, h.medium_bytes, f) != h.medium_bytes) return io_fail(f, "truncated state file");
       if (cudaMemcpy(dst[k], host.data(), h.medium_bytes, cudaMemcpyHostToDevice) != cudaSuccess) return io_fail(f, "device write failed");
     }
+  }
+  if (h.sv_bytes) {
+    if (!c->sv) {
+      int rc = dev_alloc(c, reinterpret_cast<void**>(&c->sv), (size_t)h.sv_bytes, "cudaMalloc(viscous rate)");
+      if (rc) {
+        fclose(f);
+        return rc;
+      }
+    }
+    if (fread(host.data(), 1, h.sv_bytes, f) != h.sv_bytes) return io_fail(f, "truncated state file");
+    if (cudaMemcpy(c->sv, host.data(), h.sv_bytes, cudaMemcpyHostToDevice) != cudaSuccess) return io_fail(f, "device write failed");
+  } else if (c->sv) {
+    cudaFree(c->sv);
+    c->bytes -= (uint64_t)c->plane * sizeof(float);
+    c->sv = nullptr;
   }
   fclose(f);
   c->het = h.het != 0;

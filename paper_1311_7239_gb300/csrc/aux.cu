@@ -32,6 +32,27 @@ __global__ void k_medium(const float* __restrict__ eps, const float* __restrict_
   K_out[o] = k;
 }
 
+// viscous rate field from a viscosity-ratio field: s_v = 1 / (1/2 + J nu / c_s^2) (Eq. 21, Sec. 3.2)
+__global__ void k_viscous_rate(const float* __restrict__ J, int nx, int ny, int pitch, float nu, float* __restrict__ sv,
+                               unsigned int* err) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  if (y >= ny || x >= pitch) return;
+  const int64_t o = (int64_t)y * pitch + x;
+  if (x >= nx) {
+    sv[o] = 1.0f;
+    return;
+  }
+  const float j = J[(int64_t)y * nx + x];
+  if (!(j > 0.0f && j < 1e30f)) atomicOr(err, 2u);
+  sv[o] = 1.0f / (0.5f + 3.0f * j * nu);
+}
+
+cudaError_t launch_viscous_rate(const float* J, int nx, int ny, int pitch, float nu, float* sv, unsigned int* err, cudaStream_t s) {
+  k_viscous_rate<<<dim3((pitch + 255) / 256, ny), 256, 0, s>>>(J, nx, ny, pitch, nu, sv, err);
+  return cudaGetLastError();
+}
+
 // --------------------------------------------------------------------------------------------
 // helpers for the inverse of the gather
 // --------------------------------------------------------------------------------------------

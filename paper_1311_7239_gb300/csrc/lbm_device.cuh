@@ -31,6 +31,7 @@ struct StepParams {
   void* gdst;
   const float* phi;  // per-cell porosity [ny][pitch], or nullptr for uniform
   const float* K;    // per-cell permeability [ny][pitch], or nullptr for uniform
+  const float* sv;   // per-cell viscous rate s_v = 1/(1/2 + 3 J nu) [ny][pitch] (heterogeneous mode), or nullptr
   int nx, ny, pitch;
   int64_t plane;     // elements per plane = ny * pitch
   int bc_x, bc_y;
@@ -117,6 +118,7 @@ template <> struct Store<PREC_BF16> {
 // ---------------------------------------------------------------------------------------------
 struct Coef {
   float phi, inv_phi;
+  float s_v;    // viscous relaxation rate s7 = s8 (Eq. 13, Eq. 21 with upsilon_e = J upsilon)
   float c_lin;  // phi nu / K          (linear Darcy drag of Eq. 3)
   float c_nl;   // phi F_phi / sqrt(K)  (Forchheimer drag of Eq. 3; = 1.75 / sqrt(150 phi K) by Eq. 4)
 };
@@ -130,7 +132,7 @@ template <bool HET>
 __device__ __forceinline__ Coef coef_at(const StepParams& P, int x, int y) {
   Coef c;
   if (!HET) {
-    c.phi = P.phi_u; c.inv_phi = P.inv_phi_u; c.c_lin = P.c_lin_u; c.c_nl = P.c_nl_u;
+    c.phi = P.phi_u; c.inv_phi = P.inv_phi_u; c.c_lin = P.c_lin_u; c.c_nl = P.c_nl_u; c.s_v = P.s_v;
   } else {
     const int64_t o = (int64_t)y * P.pitch + x;
     const float ph = __ldg(P.phi + o);
@@ -139,6 +141,7 @@ __device__ __forceinline__ Coef coef_at(const StepParams& P, int x, int y) {
     c.inv_phi = fast_rcp(ph);
     c.c_lin = ph * P.nu * fast_rcp(k);
     c.c_nl = P.forch ? 1.75f * rsqrtf(150.0f * ph * k) : 0.0f;
+    c.s_v = P.sv ? __ldg(P.sv + o) : P.s_v;
   }
   return c;
 }
@@ -204,7 +207,7 @@ __device__ __forceinline__ void collide_d2q8(float d[8], const Coef& c, float ax
   // -rho0 u, and m4 + rho0 u_x = (m4 + m3) + rho0 F_x / 2 by Eq. 17: that form avoids subtracting
   // two O(u) numbers.  Adding the increments to the pulled populations (instead of rebuilding
   // them from m+) keeps FP32 rounding at about one unit of d per step.
-  const float s_e = P.s_e, s_q = P.s_q, s_v = P.s_v;
+  const float s_e = P.s_e, s_q = P.s_q, s_v = c.s_v;
   const float rFx = rho0 * Fx, rFy = rho0 * Fy;
   const float S2 = rho0 * 0.8f * (ux * Fx + uy * Fy) * c.inv_phi;
   const float k2 = -s_e * (m2 + phip_dev) + (1.0f - 0.5f * s_e) * S2;  // e_eq = -phi p

@@ -22,6 +22,7 @@ cudaError_t launch_step_batch(const StepParams* Pd, const int64_t* item_start, i
 cudaError_t launch_step(const StepParams& P, int prec, bool het, bool thermal, cudaStream_t s);
 cudaError_t launch_medium(const float* eps, const float* K, float phi_u, float K_u, int nx, int ny, int pitch, float* phi_out,
                           float* K_out, unsigned int* err, int log_k, cudaStream_t s);
+cudaError_t launch_viscous_rate(const float* J, int nx, int ny, int pitch, float nu, float* sv, unsigned int* err, cudaStream_t s);
 cudaError_t launch_init(const StepParams& P, int prec, bool het, bool thermal, float p0, float ux0, float uy0, int phip_uniform,
                         float T_init, bool flow, bool temp, cudaStream_t s);
 cudaError_t launch_import(const StepParams& P, int prec, const float* f, const float* g, cudaStream_t s);

@@ -71,6 +71,7 @@ SIGNATURES = {
     "lbm_destroy": (None, [_c_ctx]),
     "lbm_set_medium": (ctypes.c_int, [_c_ctx, _f32p, _f32p]),
     "lbm_set_medium_log": (ctypes.c_int, [_c_ctx, _f32p, _f32p]),
+    "lbm_set_viscosity_ratio": (ctypes.c_int, [_c_ctx, _f32p]),
     "lbm_init_equilibrium": (ctypes.c_int, [_c_ctx, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int]),
     "lbm_init_temperature": (ctypes.c_int, [_c_ctx, ctypes.c_double]),
     "lbm_step": (ctypes.c_int, [_c_ctx, ctypes.c_int]),
@@ -220,6 +221,9 @@ class Lattice:
     # set-up -------------------------------------------------------------------------------
     def set_medium(self, eps=None, K=None):
         _check(lib().lbm_set_medium(self._h, _ptr(eps), _ptr(K)), "lbm_set_medium")
+
+    def set_viscosity_ratio(self, J=None):
+        _check(lib().lbm_set_viscosity_ratio(self._h, _ptr(J)), "lbm_set_viscosity_ratio")
 
     def set_medium_log(self, eps=None, logK=None):
         _check(lib().lbm_set_medium_log(self._h, _ptr(eps), _ptr(logK)), "lbm_set_medium_log")

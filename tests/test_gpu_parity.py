@@ -242,3 +242,40 @@ def test_graph_replay_equals_single_launches(lbm):
         gb = b.get_populations().cpu().numpy()
         assert a.step_count() == b.step_count() == 165
     assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+
+
+def _jcase(nx, ny, J_lo, het_phi=True):
+    """Partially porous channel with the viscosity ratio J_lo in the lower (porous) half."""
+    lower = np.arange(ny)[:, None] < ny // 2
+    case = Case(nx, ny, nu=0.16, phi=0.5, K=1e-3 * ny * ny, forch=False, walls={"top": (0.01, 0.0)}, het=het_phi)
+    Jf = (np.where(lower, J_lo, 1.0) * np.ones((ny, nx))).astype(np.float32)
+    return case, Jf
+
+
+def test_viscosity_ratio_field_one_step_and_trajectory(lbm):
+    """Per-cell J (region-dependent s_v of Sec. 3.2): one step from a random state element by
+    element, and a 400-step trajectory, against the oracle with the same J field."""
+    import torch
+
+    case, Jf = _jcase(37, 22, 4.0)
+    flow = case.flow()
+    flow.J = Jf.astype(np.float64)
+    f0 = random_state(flow, seed=5)
+    with case.lattice(lbm) as lat:
+        lat.set_viscosity_ratio(torch.tensor(Jf, device="cuda"))
+        lat.set_populations(to_gpu(f0))
+        lat.step(1)
+        got = lat.get_populations().cpu().numpy()
+    assert np.abs(got - fl.step(f0, flow)).max() <= 2e-6
+    with case.lattice(lbm) as lat:
+        lat.set_viscosity_ratio(Jf)  # host array
+        lat.init_equilibrium(case.p_rest(), 0.0, 0.0, phi_p_uniform=True)
+        lat.step(400)
+        p, ux, uy = (t.cpu().numpy() for t in lat.macros())
+        with pytest.raises(lbm.LbmError) as e:
+            lat.set_viscosity_ratio(np.zeros_like(Jf))
+        assert e.value.code == lbm.EINVAL
+    f = fl.run(fl.initial_state(flow, p0=case.p_rest() / flow.phi), flow, 400)
+    uxo, uyo, po = fl.macroscopic(f, flow)
+    assert rel_l2(np.stack([ux, uy]), np.stack([uxo, uyo])) <= 1e-5
+    assert rel_l2(p, po) <= 1e-5
