@@ -251,6 +251,43 @@ def thermal_form(lbm, L, steps, warmup, local_rank):
     return {"workload": f"natural convection {L}x{L}, Ra=1e5, Pr=1, eps=0.6, Da=1e-2 (D2Q8 + D2Q5 fused)", **out}
 
 
+def heterogeneous_form(lbm, L, steps, warmup, local_rank):
+    """The bench cavity with a random medium (eps, K per cell: 72 B per update) and, in addition,
+    a per-cell viscosity ratio (J = 4 in the lower half: 76 B per update)."""
+    import numpy as np
+    import torch
+
+    from paper_1311_7239_gb300 import synth
+
+    peak, _ = peaks()
+    prm = cavity_params(L)
+    eps, K = synth.heterogeneous_medium(L, L, H=L, seed=7, da_mean=1e-3, corr_len=32.0, eps_mean=0.4, eps_sd=0.05, eps_lo=0.2)
+    J = np.where(np.arange(L)[:, None] < L // 2, 4.0, 1.0).astype(np.float32) * np.ones((L, L), np.float32)
+    out = {}
+    for name, bpl, with_j in (("medium", 72, False), ("medium_and_J", 76, True)):
+        stream = torch.cuda.Stream()
+        lat = make_lattice(lbm, L, "fp32", stream)
+        lat.set_medium(torch.tensor(eps, dtype=torch.float32, device="cuda"), torch.tensor(K, dtype=torch.float32, device="cuda"))
+        if with_j:
+            lat.set_viscosity_ratio(torch.tensor(J, device="cuda"))
+        lat.init_equilibrium(prm["phi"], 0.0, 0.0, phi_p_uniform=True)
+        lat.step(warmup)
+        lat.sync()
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local_rank) as clk:
+            start.record(stream)
+            lat.step(steps)
+            stop.record(stream)
+            stop.synchronize()
+        lat.sync()
+        lat.close()
+        ms = start.elapsed_time(stop)
+        bw = bpl * L * L * steps / (ms * 1e-3) / 1e9
+        out[name] = {"value": L * L * steps / (ms * 1e-3) / 1e6, "unit": "MLUPS", "achieved_gbs": bw, "roofline_frac": bw / peak,
+                     "algorithmic_bytes_per_lu": bpl, "steps": steps, "clocks": clk.summary()}
+    return {"workload": f"lid-driven cavity {L}x{L}, random eps/K (and J = 4 in the lower half), FP32", **out}
+
+
 def ensemble_form(lbm, steps, local_rank):
     """512 porous cavities/channels (sides 64..1024): batched persistent launch vs one by one."""
     import torch
@@ -405,6 +442,7 @@ def run_gpu(args, rank, world, local_rank):
     if not args.no_forms:
         line["forms"] = forms
         line["forms"]["thermal"] = thermal_form(lbm, 2048, max(64, args.steps // 4), args.warmup, local_rank)
+        line["forms"]["heterogeneous"] = heterogeneous_form(lbm, args.size, max(64, args.steps // 4), args.warmup, local_rank)
         line["forms"]["adjoint"] = adjoint_form(lbm, T=args.adjoint_steps)
         if not args.no_ensemble:
             line["forms"]["ensemble"] = ensemble_form(lbm, max(64, args.steps // 16), local_rank)
