@@ -31,10 +31,13 @@ __device__ void frame_group(const StepParams& P, const Frame& F, int k) {
   }
   const T* src = static_cast<const T*>(P.src);
   const T* gsrc = static_cast<const T*>(P.gsrc);
-  float d[8][C], g[5][C];
+  T* dst = static_cast<T*>(P.dst);
+  T* gdst = static_cast<T*>(P.gdst);
+  // one cell at a time, stored as soon as it is collided (few live registers on this rare path)
 #pragma unroll 1
   for (int c = 0; c < C; ++c) {
     const int x = x0 + c;
+    const int64_t o = (int64_t)y * P.pitch + x;
     float dc[8], gc[5];
     if (x < P.nx) {
       if (P.bc_x == BC_PRESSURE && (x == 0 || x == P.nx - 1))
@@ -57,24 +60,12 @@ __device__ void frame_group(const StepParams& P, const Frame& F, int k) {
 #pragma unroll
       for (int i = 0; i < 5; ++i) gc[i] = 0.0f;
     }
-    // constant-index copies keep d, g in registers of the unrolled store below
 #pragma unroll
-    for (int cc = 0; cc < C; ++cc)
-      if (cc == c) {
+    for (int i = 0; i < 8; ++i) dst[i * P.plane + o] = S::enc(dc[i], P.scale);
+    if (THERMAL) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) d[i][cc] = dc[i];
-#pragma unroll
-        for (int i = 0; i < 5; ++i) g[i][cc] = gc[i];
-      }
-  }
-  const int64_t r0 = (int64_t)y * P.pitch + x0;
-  T* dst = static_cast<T*>(P.dst);
-#pragma unroll
-  for (int i = 0; i < 8; ++i) S::store4(dst + i * P.plane + r0, d[i], P.scale);
-  if (THERMAL) {
-    T* gdst = static_cast<T*>(P.gdst);
-#pragma unroll
-    for (int i = 0; i < 5; ++i) S::store4(gdst + i * P.plane + r0, g[i], P.scale);
+      for (int i = 0; i < 5; ++i) gdst[i * P.plane + o] = S::enc(gc[i], P.scale);
+    }
   }
 }
 
