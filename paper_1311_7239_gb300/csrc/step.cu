@@ -176,32 +176,43 @@ static cudaError_t launch_step_p(const StepParams& P, bool het, bool thermal, cu
 }
 
 // --------------------------------------------------------------------------------------------
-// Batched ensemble: one persistent launch advances every lattice of a batch by one step.
-// Item ranges of the lattices are concatenated (item_start, ascending); each CTA walks the items
-// gridDim.x apart and finds the lattice of an item by binary search.  Lattice d's parameters for
-// the current buffer parity are Pd[d].
-// --------------------------------------------------------------------------------------------
-template <int PREC, int NT>
-__global__ void __launch_bounds__(NT) k_step_batch(const StepParams* __restrict__ Pd, const int64_t* __restrict__ item_start, int n,
-                                                   int64_t total) {
-  for (int64_t it = blockIdx.x; it < total; it += gridDim.x) {
-    int lo = 0, hi = n - 1;  // last d with item_start[d] <= it
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (item_start[mid] <= it) lo = mid; else hi = mid - 1;
-    }
-    const StepParams P = Pd[lo];
-    int fb, gx;
-    items_of(P.nx, P.ny, P.bc_y, NT, fb, gx);
-    step_item<PREC, true, false, NT>(P, fb, gx, (int)(it - item_start[lo]));
-  }
-}
-
 cudaError_t launch_step(const StepParams& P, int prec, bool het, bool thermal, cudaStream_t s) {
   switch (prec) {
     case PREC_FP32: return launch_step_p<PREC_FP32>(P, het, thermal, s);
     case PREC_FP16: return launch_step_p<PREC_FP16>(P, het, thermal, s);
     default: return launch_step_p<PREC_BF16>(P, het, thermal, s);
+  }
+}
+
+// --------------------------------------------------------------------------------------------
+// Batched ensemble: one persistent launch advances every lattice of a batch by one step.
+// Item ranges of the lattices are concatenated (item_start, ascending); CTA b walks the
+// contiguous range [b * chunk, (b + 1) * chunk) of items, so it looks its lattice up once (binary
+// search) and then only steps to the next lattice when the range crosses into it.  Lattice d's
+// parameters for the current buffer parity are Pd[d].
+// --------------------------------------------------------------------------------------------
+template <int PREC, int NT>
+__global__ void __launch_bounds__(NT) k_step_batch(const StepParams* __restrict__ Pd, const int64_t* __restrict__ item_start, int n,
+                                                   int64_t total) {
+  const int64_t chunk = (total + gridDim.x - 1) / gridDim.x;
+  const int64_t begin = (int64_t)blockIdx.x * chunk;
+  const int64_t end = begin + chunk < total ? begin + chunk : total;
+  if (begin >= end) return;
+  int lo = 0, hi = n - 1;  // last d with item_start[d] <= begin
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (item_start[mid] <= begin) lo = mid; else hi = mid - 1;
+  }
+  int64_t next = lo + 1 < n ? item_start[lo + 1] : total;
+  for (int64_t it = begin; it < end; ++it) {
+    while (it >= next) {
+      ++lo;
+      next = lo + 1 < n ? item_start[lo + 1] : total;
+    }
+    const StepParams& P = Pd[lo];
+    int fb, gx;
+    items_of(P.nx, P.ny, P.bc_y, NT, fb, gx);
+    step_item<PREC, true, false, NT>(P, fb, gx, (int)(it - item_start[lo]));
   }
 }
 
