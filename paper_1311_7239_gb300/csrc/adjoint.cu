@@ -349,12 +349,12 @@ __device__ void adj_cell(const StepParams& P, const void* buf, const AdjArgs& A,
 // cell by cell; main items gather the forward state forwards and the adjoint state backwards
 // (mu_i(x) = nu~_i(x + e_i)) as aligned vectors with shuffled halos, and skip frame groups.
 template <int PREC, bool HET, int NT>
-__device__ __forceinline__ void adj_item(const StepParams& P, const void* buf, const AdjArgs& A, int frame_blocks, int gx, int item) {
+__device__ __forceinline__ void adj_item(const StepParams& P, const void* buf, const AdjArgs& A, const Tiling& tl, int item) {
   using S = Store<PREC>;
   using T = typename S::T;
   using SF = Store<PREC_FP32>;
   constexpr int C = kCellsPerThread;
-  if (item < frame_blocks) {
+  if (item < tl.frame_blocks) {
     const Frame F = frame_of(P.nx, P.ny, P.bc_y, C);
     const int k = item * NT + (int)threadIdx.x;
     if (k >= F.count) return;
@@ -372,9 +372,8 @@ __device__ __forceinline__ void adj_item(const StepParams& P, const void* buf, c
       if (x0 + c < P.nx) adj_cell<PREC, HET>(P, buf, A, x0 + c, y);
     return;
   }
-  const int b = item - frame_blocks;
-  const int y = b / gx;
-  const int x0 = ((b - y * gx) * NT + (int)threadIdx.x) * C;
+  int x0, y;
+  const bool has_group = main_group(tl, P.ny, NT, item - tl.frame_blocks, (int)threadIdx.x, x0, y);
   const int lane = threadIdx.x & 31;
   const int xl = x0 < P.pitch - C ? x0 : P.pitch - C;
   int ym = y - 1, yp = y + 1;
@@ -406,7 +405,7 @@ __device__ __forceinline__ void adj_item(const StepParams& P, const void* buf, c
   gather4<PREC_FP32, 1>(nu_in + 6 * pl + rm, xl, P.pitch, lane, 1.0f, mu[6]);   // e7 = (-1,-1)
   gather4<PREC_FP32, -1>(nu_in + 7 * pl + rm, xl, P.pitch, lane, 1.0f, mu[7]);  // e8 = ( 1,-1)
   const bool wall_row = P.bc_y == BC_WALL && (y == 0 || y == P.ny - 1);
-  if (wall_row || x0 == 0 || x0 + C >= P.nx) return;
+  if (!has_group || wall_row || x0 == 0 || x0 + C >= P.nx) return;
   double gl[C], gp[C];
 #pragma unroll
   for (int c = 0; c < C; ++c) {
@@ -434,8 +433,8 @@ __device__ __forceinline__ void adj_item(const StepParams& P, const void* buf, c
 }
 
 template <int PREC, bool HET>
-__global__ void __launch_bounds__(kStepThreads, 5) k_adj_step(const StepParams P, const void* buf, AdjArgs A, int frame_blocks, int gx) {
-  adj_item<PREC, HET, kStepThreads>(P, buf, A, frame_blocks, gx, blockIdx.x);
+__global__ void __launch_bounds__(kStepThreads, 5) k_adj_step(const StepParams P, const void* buf, AdjArgs A, Tiling tl) {
+  adj_item<PREC, HET, kStepThreads>(P, buf, A, tl, blockIdx.x);
 }
 
 // Initial state: z(0) = f_eq(p0, u0; phi) (Eq. 22): dL/dphi += sum_i nu_i d f_eq,i / d phi.
@@ -491,10 +490,9 @@ cudaError_t launch_adj_nee(const StepParams& P, int prec, bool het, const void* 
 cudaError_t launch_adj_step(const StepParams& P, int prec, bool het, const void* buf, const float* nu_in, float* nu_out, double* g_l,
                             double* g_phi, cudaStream_t s) {
   AdjArgs A{nu_in, nu_out, g_l, g_phi};
-  int fb, gx;
-  items_of(P.nx, P.ny, P.bc_y, kStepThreads, fb, gx);
-  const unsigned blocks = (unsigned)((long long)fb + (long long)gx * P.ny);
-#define CALL_ADJ(PR, H) k_adj_step<PR, H><<<blocks, kStepThreads, 0, s>>>(P, buf, A, fb, gx)
+  const Tiling tl = tiling_of(P.nx, P.ny, P.bc_y, kStepThreads);
+  const unsigned blocks = (unsigned)((long long)tl.frame_blocks + main_items(tl, P.ny));
+#define CALL_ADJ(PR, H) k_adj_step<PR, H><<<blocks, kStepThreads, 0, s>>>(P, buf, A, tl)
   LBM_ADJ_DISPATCH(prec, het, CALL_ADJ);
 #undef CALL_ADJ
   return cudaGetLastError();

@@ -73,18 +73,17 @@ __device__ void frame_group(const StepParams& P, const Frame& F, int k) {
 // the rest cover the lattice row by row, gx items per row, and store every group that is not a
 // frame group.  Every thread of the CTA calls this with the same item (warp shuffles inside).
 template <int PREC, bool HET, bool THERMAL, int NT>
-__device__ __forceinline__ void step_item(const StepParams& P, int frame_blocks, int gx, int item) {
+__device__ __forceinline__ void step_item(const StepParams& P, const Tiling& tl, int item) {
   using S = Store<PREC>;
   using T = typename S::T;
   constexpr int C = kCellsPerThread;
-  if (item < frame_blocks) {
+  if (item < tl.frame_blocks) {
     const Frame F = frame_of(P.nx, P.ny, P.bc_y, C);
     frame_group<PREC, HET, THERMAL>(P, F, item * NT + (int)threadIdx.x);
     return;
   }
-  const int b = item - frame_blocks;
-  const int y = b / gx;
-  const int x0 = ((b - y * gx) * NT + (int)threadIdx.x) * C;
+  int x0, y;
+  const bool has_group = main_group(tl, P.ny, NT, item - tl.frame_blocks, (int)threadIdx.x, x0, y);
   const T* __restrict__ src = static_cast<const T*>(P.src);
   T* __restrict__ dst = static_cast<T*>(P.dst);
   const int lane = threadIdx.x & 31;
@@ -118,7 +117,7 @@ __device__ __forceinline__ void step_item(const StepParams& P, int frame_blocks,
   }
   // (after the shuffles) frame groups and groups past the row are not stored here
   const bool wall_row = P.bc_y == BC_WALL && (y == 0 || y == P.ny - 1);
-  if (wall_row || x0 == 0 || x0 + C >= P.nx) return;
+  if (!has_group || wall_row || x0 == 0 || x0 + C >= P.nx) return;
 
   float check = 0.0f;
 #pragma unroll
@@ -156,16 +155,15 @@ __device__ __forceinline__ void step_item(const StepParams& P, int frame_blocks,
 
 // One time step of one lattice: one CTA per work item.
 template <int PREC, bool HET, bool THERMAL>
-__global__ void __launch_bounds__(kStepThreads) k_step(const StepParams P, int frame_blocks, int gx) {
-  step_item<PREC, HET, THERMAL, kStepThreads>(P, frame_blocks, gx, blockIdx.x);
+__global__ void __launch_bounds__(kStepThreads) k_step(const StepParams P, Tiling tl) {
+  step_item<PREC, HET, THERMAL, kStepThreads>(P, tl, blockIdx.x);
 }
 
 template <int PREC, bool HET, bool THERMAL>
 static cudaError_t launch_step_t(const StepParams& P, cudaStream_t s) {
-  int fb, gx;
-  items_of(P.nx, P.ny, P.bc_y, kStepThreads, fb, gx);
-  const long long blocks = (long long)fb + (long long)gx * P.ny;
-  k_step<PREC, HET, THERMAL><<<(unsigned)blocks, kStepThreads, 0, s>>>(P, fb, gx);
+  const Tiling tl = tiling_of(P.nx, P.ny, P.bc_y, kStepThreads);
+  const long long blocks = (long long)tl.frame_blocks + main_items(tl, P.ny);
+  k_step<PREC, HET, THERMAL><<<(unsigned)blocks, kStepThreads, 0, s>>>(P, tl);
   return cudaGetLastError();
 }
 
@@ -210,9 +208,8 @@ __global__ void __launch_bounds__(NT) k_step_batch(const StepParams* __restrict_
       next = lo + 1 < n ? item_start[lo + 1] : total;
     }
     const StepParams& P = Pd[lo];
-    int fb, gx;
-    items_of(P.nx, P.ny, P.bc_y, NT, fb, gx);
-    step_item<PREC, true, false, NT>(P, fb, gx, (int)(it - item_start[lo]));
+    const Tiling tl = tiling_of(P.nx, P.ny, P.bc_y, NT);
+    step_item<PREC, true, false, NT>(P, tl, (int)(it - item_start[lo]));
   }
 }
 
@@ -221,9 +218,8 @@ __global__ void __launch_bounds__(NT) k_step_batch(const StepParams* __restrict_
 namespace lbm {
 
 int64_t batch_items(int nx, int ny, int bc_y, int nt) {
-  int fb, gx;
-  items_of(nx, ny, bc_y, nt, fb, gx);
-  return (int64_t)fb + (int64_t)gx * ny;
+  const Tiling tl = tiling_of(nx, ny, bc_y, nt);
+  return (int64_t)tl.frame_blocks + main_items(tl, ny);
 }
 
 template <int PREC>

@@ -52,12 +52,46 @@ __host__ __device__ inline Frame frame_of(int nx, int ny, int bc_y, int C) {
   return f;
 }
 
-// Work items of one lattice for CTAs of nt threads.
-__host__ __device__ inline void items_of(int nx, int ny, int bc_y, int nt, int& frame_blocks, int& gx) {
-  const int per = nt * kCellsPerThread;
-  gx = (nx + per - 1) / per;
+// Work items of one lattice for CTAs of nt threads: the frame items first, then the main items.
+// A row of G = ceil(nx / C) groups takes gx = ceil(G / nt) items when G > nt; shorter rows are
+// packed rows_per_item = nt / G to an item (thread t of the item: row t / G, group t % G).
+struct Tiling {
+  int frame_blocks, gx, rows_per_item, groups;
+};
+
+__host__ __device__ inline Tiling tiling_of(int nx, int ny, int bc_y, int nt) {
+  Tiling t;
+  t.groups = (nx + kCellsPerThread - 1) / kCellsPerThread;
   const Frame F = frame_of(nx, ny, bc_y, kCellsPerThread);
-  frame_blocks = (F.count + nt - 1) / nt;
+  t.frame_blocks = (F.count + nt - 1) / nt;
+  if (t.groups <= nt) {
+    t.gx = 1;
+    t.rows_per_item = nt / t.groups;
+  } else {
+    t.gx = (t.groups + nt - 1) / nt;
+    t.rows_per_item = 1;
+  }
+  return t;
+}
+
+__host__ __device__ inline int64_t main_items(const Tiling& t, int ny) {
+  return t.rows_per_item > 1 ? (int64_t)((ny + t.rows_per_item - 1) / t.rows_per_item) : (int64_t)t.gx * ny;
+}
+
+// Row and first cell of thread `tid` in main item b; false for a thread with no group (it still
+// takes part in the loads and shuffles, on a clamped row, and stores nothing).
+__device__ __forceinline__ bool main_group(const Tiling& t, int ny, int nt, int b, int tid, int& x0, int& y) {
+  if (t.rows_per_item > 1) {
+    const int r = tid / t.groups;
+    y = b * t.rows_per_item + r;
+    x0 = (tid - r * t.groups) * kCellsPerThread;
+    const bool ok = r < t.rows_per_item && y < ny;
+    if (!ok) y = ny - 1;
+    return ok;
+  }
+  y = b / t.gx;
+  x0 = ((b - y * t.gx) * nt + tid) * kCellsPerThread;
+  return true;
 }
 
 }  // namespace lbm
