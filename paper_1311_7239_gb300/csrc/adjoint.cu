@@ -354,22 +354,10 @@ __device__ __forceinline__ void adj_item(const StepParams& P, const void* buf, c
   using T = typename S::T;
   using SF = Store<PREC_FP32>;
   constexpr int C = kCellsPerThread;
-  if (item < tl.frame_blocks) {
+  if (item < tl.frame_blocks) {  // one frame cell per thread
     const Frame F = frame_of(P.nx, P.ny, P.bc_y, C);
-    const int k = item * NT + (int)threadIdx.x;
-    if (k >= F.count) return;
-    int x0, y;
-    if (F.wall_rows && k < 2 * F.groups_per_row) {
-      y = k < F.groups_per_row ? 0 : P.ny - 1;
-      x0 = (k % F.groups_per_row) * C;
-    } else {
-      const int k2 = k - (F.wall_rows ? 2 * F.groups_per_row : 0);
-      y = k2 / F.cols + F.wall_rows;
-      x0 = (k2 % F.cols == 0) ? 0 : (F.groups_per_row - 1) * C;
-    }
-#pragma unroll 1
-    for (int c = 0; c < C; ++c)
-      if (x0 + c < P.nx) adj_cell<PREC, HET>(P, buf, A, x0 + c, y);
+    int x, y;
+    if (frame_cell(F, P.ny, item * NT + (int)threadIdx.x, x, y) && x < P.nx) adj_cell<PREC, HET>(P, buf, A, x, y);
     return;
   }
   int x0, y;

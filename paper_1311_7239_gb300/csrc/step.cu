@@ -15,57 +15,42 @@
 namespace lbm {
 
 template <int PREC, bool HET, bool THERMAL>
-__device__ void frame_group(const StepParams& P, const Frame& F, int k) {
+__device__ void frame_step(const StepParams& P, const Frame& F, int k) {
   using S = Store<PREC>;
   using T = typename S::T;
-  constexpr int C = kCellsPerThread;
-  if (k >= F.count) return;
-  int x0, y;
-  if (F.wall_rows && k < 2 * F.groups_per_row) {
-    y = k < F.groups_per_row ? 0 : P.ny - 1;
-    x0 = (k % F.groups_per_row) * C;
-  } else {
-    const int k2 = k - (F.wall_rows ? 2 * F.groups_per_row : 0);
-    y = k2 / F.cols + F.wall_rows;
-    x0 = (k2 % F.cols == 0) ? 0 : (F.groups_per_row - 1) * C;
-  }
-  const T* src = static_cast<const T*>(P.src);
-  const T* gsrc = static_cast<const T*>(P.gsrc);
+  int x, y;
+  if (!frame_cell(F, P.ny, k, x, y)) return;
+  const int64_t o = (int64_t)y * P.pitch + x;
   T* dst = static_cast<T*>(P.dst);
   T* gdst = static_cast<T*>(P.gdst);
-  // one cell at a time, stored as soon as it is collided (few live registers on this rare path)
-#pragma unroll 1
-  for (int c = 0; c < C; ++c) {
-    const int x = x0 + c;
-    const int64_t o = (int64_t)y * P.pitch + x;
-    float dc[8], gc[5];
-    if (x < P.nx) {
-      if (P.bc_x == BC_PRESSURE && (x == 0 || x == P.nx - 1))
-        pressure_column<PREC, HET>(P, src, x, y, dc);
-      else
-        pull_cell<PREC>(P, src, x, y, dc);
-      float ay = P.ay;
-      if (THERMAL) {
-        pull_cell_g<PREC>(P, gsrc, x, y, gc);
-        ay += P.g_beta * (gc[0] + gc[1] + gc[2] + gc[3] + gc[4]);
-      }
-      const Coef cf = coef_at<HET>(P, x, y);
-      float ux, uy, phip;
-      collide_d2q8(dc, cf, P.ax, ay, P, ux, uy, phip);
-      if (!(fabsf(ux) + fabsf(uy) < 1e30f)) atomicOr(P.err, 1u);
-      if (THERMAL) collide_d2q5(gc, ux, uy, P);
-    } else {  // row padding: zeros (never gathered by a lattice cell)
-#pragma unroll
-      for (int i = 0; i < 8; ++i) dc[i] = 0.0f;
-#pragma unroll
-      for (int i = 0; i < 5; ++i) gc[i] = 0.0f;
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) dst[i * P.plane + o] = S::enc(dc[i], P.scale);
+  float dc[8], gc[5];
+  if (x < P.nx) {
+    const T* src = static_cast<const T*>(P.src);
+    if (P.bc_x == BC_PRESSURE && (x == 0 || x == P.nx - 1))
+      pressure_column<PREC, HET>(P, src, x, y, dc);
+    else
+      pull_cell<PREC>(P, src, x, y, dc);
+    float ay = P.ay;
     if (THERMAL) {
-#pragma unroll
-      for (int i = 0; i < 5; ++i) gdst[i * P.plane + o] = S::enc(gc[i], P.scale);
+      pull_cell_g<PREC>(P, static_cast<const T*>(P.gsrc), x, y, gc);
+      ay += P.g_beta * (gc[0] + gc[1] + gc[2] + gc[3] + gc[4]);
     }
+    const Coef cf = coef_at<HET>(P, x, y);
+    float ux, uy, phip;
+    collide_d2q8(dc, cf, P.ax, ay, P, ux, uy, phip);
+    if (!(fabsf(ux) + fabsf(uy) < 1e30f)) atomicOr(P.err, 1u);
+    if (THERMAL) collide_d2q5(gc, ux, uy, P);
+  } else {  // row padding: zeros (never gathered by a lattice cell)
+#pragma unroll
+    for (int i = 0; i < 8; ++i) dc[i] = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) gc[i] = 0.0f;
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) dst[i * P.plane + o] = S::enc(dc[i], P.scale);
+  if (THERMAL) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) gdst[i * P.plane + o] = S::enc(gc[i], P.scale);
   }
 }
 
@@ -79,7 +64,7 @@ __device__ __forceinline__ void step_item(const StepParams& P, const Tiling& tl,
   constexpr int C = kCellsPerThread;
   if (item < tl.frame_blocks) {
     const Frame F = frame_of(P.nx, P.ny, P.bc_y, C);
-    frame_group<PREC, HET, THERMAL>(P, F, item * NT + (int)threadIdx.x);
+    frame_step<PREC, HET, THERMAL>(P, F, item * NT + (int)threadIdx.x);
     return;
   }
   int x0, y;

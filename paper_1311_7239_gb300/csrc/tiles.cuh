@@ -59,11 +59,28 @@ struct Tiling {
   int frame_blocks, gx, rows_per_item, groups;
 };
 
+// Row and column of frame cell k (frame group k / C, cell k % C of the group).
+__device__ __forceinline__ bool frame_cell(const Frame& F, int ny, int k, int& x, int& y) {
+  const int grp = k / kCellsPerThread;
+  if (grp >= F.count) return false;
+  int x0;
+  if (F.wall_rows && grp < 2 * F.groups_per_row) {
+    y = grp < F.groups_per_row ? 0 : ny - 1;
+    x0 = (grp % F.groups_per_row) * kCellsPerThread;
+  } else {
+    const int k2 = grp - (F.wall_rows ? 2 * F.groups_per_row : 0);
+    y = k2 / F.cols + F.wall_rows;
+    x0 = (k2 % F.cols == 0) ? 0 : (F.groups_per_row - 1) * kCellsPerThread;
+  }
+  x = x0 + (k - grp * kCellsPerThread);
+  return true;
+}
+
 __host__ __device__ inline Tiling tiling_of(int nx, int ny, int bc_y, int nt) {
   Tiling t;
   t.groups = (nx + kCellsPerThread - 1) / kCellsPerThread;
   const Frame F = frame_of(nx, ny, bc_y, kCellsPerThread);
-  t.frame_blocks = (F.count + nt - 1) / nt;
+  t.frame_blocks = (int)(((int64_t)F.count * kCellsPerThread + nt - 1) / nt);  // one thread per frame cell
   if (t.groups <= nt) {
     t.gx = 1;
     t.rows_per_item = nt / t.groups;
