@@ -221,7 +221,8 @@ LBM_API int lbm_batch_init_equilibrium(lbm_batch* b, int d, double p0, double ux
 LBM_API int lbm_batch_step(lbm_batch* b, int n);
 /* The same n steps run lattice by lattice with the single-lattice kernel (for comparison). */
 LBM_API int lbm_batch_step_each(lbm_batch* b, int n);
-/* Launch shape of the batched kernel: threads per CTA (64, 128, 256) and CTAs per SM (1..32). */
+/* Launch shape of the batched kernel: threads per CTA (64, 128, 256) and CTAs per SM (1..32,
+ * lowered to the kernel's occupancy limit so that every persistent CTA is resident). */
 LBM_API int lbm_batch_set_launch(lbm_batch* b, int threads_per_cta, int ctas_per_sm);
 LBM_API int lbm_batch_get_launch(const lbm_batch* b, int* threads_per_cta, int* ctas_per_sm);
 /* Time `steps` steps for every launch shape on a copy of the current state, keep the fastest,

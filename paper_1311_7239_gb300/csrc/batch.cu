@@ -115,6 +115,9 @@ int set_launch(lbm_batch* b, int nt, int ctas_per_sm) {
   LBM_BCUDA(cudaMemcpy(b->item_start, start.data(), b->n * sizeof(int64_t), cudaMemcpyHostToDevice), "copy of the item table");
   b->total_items = total;
   b->nt = nt;
+  // persistent CTAs must all be resident: no more per SM than the kernel's occupancy allows
+  const int kmax = batch_max_ctas_per_sm(b->prec, nt);
+  if (ctas_per_sm > kmax) ctas_per_sm = kmax;
   b->ctas_per_sm = ctas_per_sm;
   const int64_t g = (int64_t)b->sms * ctas_per_sm;
   b->grid = (int)(g < total ? g : total);
@@ -387,7 +390,7 @@ int lbm_batch_tune(lbm_batch* b, int steps, int* threads_per_cta, int* ctas_per_
   LBM_BCUDA(cudaMalloc(&save, pool_bytes), "cudaMalloc(tuning copy)");
   cudaMemcpyAsync(save, b->pool[b->cur], pool_bytes, cudaMemcpyDeviceToDevice, b->stream);
   const int nts[3] = {64, 128, 256};
-  const int ks[4] = {2, 4, 8, 16};
+  const int ks[5] = {1, 2, 4, 8, 16};
   float best = 1e30f;
   int best_nt = b->nt, best_k = b->ctas_per_sm;
   cudaEvent_t e0, e1;
@@ -395,8 +398,8 @@ int lbm_batch_tune(lbm_batch* b, int steps, int* threads_per_cta, int* ctas_per_
   cudaEventCreate(&e1);
   int rc = LBM_OK;
   for (int a = 0; a < 3 && rc == LBM_OK; ++a)
-    for (int c = 0; c < 4 && rc == LBM_OK; ++c) {
-      if (nts[a] * ks[c] > 2048) continue;  // resident-thread limit of an SM
+    for (int c = 0; c < 5 && rc == LBM_OK; ++c) {
+      if (ks[c] > batch_max_ctas_per_sm(b->prec, nts[a])) continue;  // persistent CTAs must be resident
       if ((rc = set_launch(b, nts[a], ks[c]))) break;
       if ((rc = launch_once(b, b->cur, b->stream))) break;  // warm-up
       cudaEventRecord(e0, b->stream);

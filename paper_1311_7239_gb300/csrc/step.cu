@@ -218,6 +218,19 @@ static cudaError_t launch_batch_p(const StepParams* Pd, const int64_t* item_star
   return cudaGetLastError();
 }
 
+// Largest number of CTAs of the batched kernel (prec, nt) resident on one SM.
+int batch_max_ctas_per_sm(int prec, int nt) {
+  int k = 0;
+  const void* fn = nullptr;
+#define LBM_BATCH_FN(PR)                                                      \
+  (nt == 64 ? (const void*)k_step_batch<PR, 64> : nt == 256 ? (const void*)k_step_batch<PR, 256> \
+                                                            : (const void*)k_step_batch<PR, 128>)
+  fn = prec == PREC_FP32 ? LBM_BATCH_FN(PREC_FP32) : prec == PREC_FP16 ? LBM_BATCH_FN(PREC_FP16) : LBM_BATCH_FN(PREC_BF16);
+#undef LBM_BATCH_FN
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, fn, nt, 0) != cudaSuccess) return 1;
+  return k > 0 ? k : 1;
+}
+
 cudaError_t launch_step_batch(const StepParams* Pd, const int64_t* item_start, int n, int64_t total, int prec, int nt, int grid,
                               cudaStream_t s) {
   if (prec == PREC_FP32) return launch_batch_p<PREC_FP32>(Pd, item_start, n, total, nt, grid, s);
