@@ -217,12 +217,13 @@ LBM_API void lbm_batch_destroy(lbm_batch* b);
 LBM_API int lbm_batch_set_medium(lbm_batch* b, int d, const float* eps, const float* K);
 /* Equilibrium initial state of lattice d (d = -1: all), as lbm_init_equilibrium. */
 LBM_API int lbm_batch_init_equilibrium(lbm_batch* b, int d, double p0, double ux0, double uy0, int phi_p_uniform);
-/* Advance every lattice by n steps with the persistent batched kernel. */
+/* Advance every lattice by n steps with the batched kernel (one launch per step for the batch). */
 LBM_API int lbm_batch_step(lbm_batch* b, int n);
 /* The same n steps run lattice by lattice with the single-lattice kernel (for comparison). */
 LBM_API int lbm_batch_step_each(lbm_batch* b, int n);
-/* Launch shape of the batched kernel: threads per CTA (64, 128, 256) and CTAs per SM (1..32,
- * lowered to the kernel's occupancy limit so that every persistent CTA is resident). */
+/* Launch shape of the batched kernel: threads per CTA (64, 128, 256) and CTAs per SM: 0 = one CTA
+ * per work item (a lattice table of 4 bytes per item is kept on the device), 1..32 = a persistent
+ * grid of SMs x k CTAs, k lowered to the kernel's occupancy limit so that every CTA is resident. */
 LBM_API int lbm_batch_set_launch(lbm_batch* b, int threads_per_cta, int ctas_per_sm);
 LBM_API int lbm_batch_get_launch(const lbm_batch* b, int* threads_per_cta, int* ctas_per_sm);
 /* Time `steps` steps for every launch shape on a copy of the current state, keep the fastest,

@@ -4,8 +4,9 @@
 // Memory: the population buffers of all lattices live in two pools (A-B streaming for the whole
 // batch), each lattice's planes at its own offset with its own pitch; the medium fields and
 // wall velocities likewise.  Per step, the work items of all lattices (frame groups and row
-// chunks, exactly as for a single lattice) are concatenated and a grid of SMs x k CTAs walks them;
-// the CTA size and k are tuning parameters (lbm_batch_tune times the choices on the live batch).
+// chunks, exactly as for a single lattice) are concatenated and either one CTA per item (k = 0,
+// with a per-item lattice table) or a persistent grid of SMs x k CTAs walks them; the CTA size
+// and k are tuning parameters (lbm_batch_tune times the choices on the live batch).
 #include <math.h>
 #include <string.h>
 
@@ -52,6 +53,8 @@ struct lbm_batch {
   std::vector<StepParams> hp[2];
   StepParams* dp[2] = {nullptr, nullptr};
   int64_t* item_start = nullptr;
+  int* item_lattice = nullptr;  // lattice of each work item (one-CTA-per-item form only)
+  int64_t item_lattice_cap = 0;
   int64_t total_items = 0;
   int nt = 128, ctas_per_sm = 4, grid = 0, sms = 0;
   int cur = 0;
@@ -96,6 +99,7 @@ void release(lbm_batch* b) {
   cudaFree(b->err);
   cudaFree(b->stage);
   cudaFree(b->item_start);
+  cudaFree(b->item_lattice);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }
@@ -105,7 +109,7 @@ StepParams params_of(const lbm_batch* b, int d, int cur) { return b->hp[cur][d];
 
 int set_launch(lbm_batch* b, int nt, int ctas_per_sm) {
   if (nt != 64 && nt != 128 && nt != 256) return fail_msg(LBM_EINVAL, "threads per CTA must be 64, 128 or 256");
-  if (ctas_per_sm < 1 || ctas_per_sm > 32) return fail_msg(LBM_EINVAL, "CTAs per SM must be in [1, 32]");
+  if (ctas_per_sm < 0 || ctas_per_sm > 32) return fail_msg(LBM_EINVAL, "CTAs per SM must be in [0, 32]");
   std::vector<int64_t> start(b->n);
   int64_t total = 0;
   for (int d = 0; d < b->n; ++d) {
@@ -115,18 +119,42 @@ int set_launch(lbm_batch* b, int nt, int ctas_per_sm) {
   LBM_BCUDA(cudaMemcpy(b->item_start, start.data(), b->n * sizeof(int64_t), cudaMemcpyHostToDevice), "copy of the item table");
   b->total_items = total;
   b->nt = nt;
+  drop_graphs(b);
+  if (ctas_per_sm == 0) {  // one CTA per work item
+    if (total > 0x7fffffffLL) return fail_msg(LBM_EINVAL, "too many work items for one CTA per item");
+    if (b->item_lattice_cap < total) {
+      cudaStreamSynchronize(b->stream);
+      cudaFree(b->item_lattice);
+      b->bytes -= (uint64_t)b->item_lattice_cap * sizeof(int);
+      b->item_lattice = nullptr;
+      b->item_lattice_cap = 0;
+      int rc = balloc(b, reinterpret_cast<void**>(&b->item_lattice), (size_t)total * sizeof(int), "cudaMalloc(item lattice table)");
+      if (rc) return rc;
+      b->item_lattice_cap = total;
+    }
+    std::vector<int> lat((size_t)total);
+    for (int d = 0; d < b->n; ++d) {
+      const int64_t e = d + 1 < b->n ? start[d + 1] : total;
+      for (int64_t i = start[d]; i < e; ++i) lat[(size_t)i] = d;
+    }
+    LBM_BCUDA(cudaMemcpy(b->item_lattice, lat.data(), (size_t)total * sizeof(int), cudaMemcpyHostToDevice), "copy of the item lattice table");
+    b->ctas_per_sm = 0;
+    b->grid = (int)total;
+    return LBM_OK;
+  }
   // persistent CTAs must all be resident: no more per SM than the kernel's occupancy allows
   const int kmax = batch_max_ctas_per_sm(b->prec, nt);
   if (ctas_per_sm > kmax) ctas_per_sm = kmax;
   b->ctas_per_sm = ctas_per_sm;
   const int64_t g = (int64_t)b->sms * ctas_per_sm;
   b->grid = (int)(g < total ? g : total);
-  drop_graphs(b);
   return LBM_OK;
 }
 
 int launch_once(lbm_batch* b, int cur, cudaStream_t s) {
-  LBM_BCUDA(launch_step_batch(b->dp[cur], b->item_start, b->n, b->total_items, b->prec, b->nt, b->grid, s), "batched step kernel");
+  LBM_BCUDA(launch_step_batch(b->dp[cur], b->item_start, b->ctas_per_sm == 0 ? b->item_lattice : nullptr, b->n, b->total_items, b->prec,
+                              b->nt, b->grid, s),
+            "batched step kernel");
   return LBM_OK;
 }
 
@@ -135,7 +163,8 @@ int capture(lbm_batch* b, int cur) {
   LBM_BCUDA(cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
   cudaError_t le = cudaSuccess;
   for (int k = 0; k < kBatchGraphSteps && le == cudaSuccess; ++k)
-    le = launch_step_batch(b->dp[cur ^ (k & 1)], b->item_start, b->n, b->total_items, b->prec, b->nt, b->grid, b->capture_stream);
+    le = launch_step_batch(b->dp[cur ^ (k & 1)], b->item_start, b->ctas_per_sm == 0 ? b->item_lattice : nullptr, b->n, b->total_items,
+                           b->prec, b->nt, b->grid, b->capture_stream);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(b->capture_stream, &g);
   if (le != cudaSuccess || e != cudaSuccess) {
@@ -276,7 +305,7 @@ int lbm_batch_create(const lbm_config* cfgs, int n, lbm_batch** out) {
     release(b);
     return fail_msg(LBM_ECUDA, "batch parameter upload");
   }
-  if ((rc = set_launch(b, 128, 4)) || (rc = lbm_batch_init_equilibrium(b, -1, 1.0, 0.0, 0.0, 0))) {
+  if ((rc = set_launch(b, 64, 0)) || (rc = lbm_batch_init_equilibrium(b, -1, 1.0, 0.0, 0.0, 0))) {
     release(b);
     return rc;
   }
@@ -390,7 +419,7 @@ int lbm_batch_tune(lbm_batch* b, int steps, int* threads_per_cta, int* ctas_per_
   LBM_BCUDA(cudaMalloc(&save, pool_bytes), "cudaMalloc(tuning copy)");
   cudaMemcpyAsync(save, b->pool[b->cur], pool_bytes, cudaMemcpyDeviceToDevice, b->stream);
   const int nts[3] = {64, 128, 256};
-  const int ks[5] = {1, 2, 4, 8, 16};
+  const int ks[6] = {0, 1, 2, 4, 8, 16};  // 0: one CTA per work item
   float best = 1e30f;
   int best_nt = b->nt, best_k = b->ctas_per_sm;
   cudaEvent_t e0, e1;
@@ -398,7 +427,7 @@ int lbm_batch_tune(lbm_batch* b, int steps, int* threads_per_cta, int* ctas_per_
   cudaEventCreate(&e1);
   int rc = LBM_OK;
   for (int a = 0; a < 3 && rc == LBM_OK; ++a)
-    for (int c = 0; c < 5 && rc == LBM_OK; ++c) {
+    for (int c = 0; c < 6 && rc == LBM_OK; ++c) {
       if (ks[c] > batch_max_ctas_per_sm(b->prec, nts[a])) continue;  // persistent CTAs must be resident
       if ((rc = set_launch(b, nts[a], ks[c]))) break;
       if ((rc = launch_once(b, b->cur, b->stream))) break;  // warm-up

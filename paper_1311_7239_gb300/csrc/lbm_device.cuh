@@ -128,22 +128,30 @@ struct Coef {
 __device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ float fast_sqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
 
+__device__ __forceinline__ float f4_get(const float4& v, int c) { return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w; }
+
+// Coefficients of a cell with porosity ph, permeability k and viscous rate sv (Eqs. 3-4, 13).
+__device__ __forceinline__ Coef coef_of(const StepParams& P, float ph, float k, float sv) {
+  Coef c;
+  c.phi = ph;
+  c.inv_phi = fast_rcp(ph);
+  c.c_lin = ph * P.nu * fast_rcp(k);
+  c.c_nl = P.forch ? 1.75f * rsqrtf(150.0f * ph * k) : 0.0f;
+  c.s_v = sv;
+  return c;
+}
+
+__device__ __forceinline__ Coef coef_uniform(const StepParams& P) {
+  Coef c;
+  c.phi = P.phi_u; c.inv_phi = P.inv_phi_u; c.c_lin = P.c_lin_u; c.c_nl = P.c_nl_u; c.s_v = P.s_v;
+  return c;
+}
+
 template <bool HET>
 __device__ __forceinline__ Coef coef_at(const StepParams& P, int x, int y) {
-  Coef c;
-  if (!HET) {
-    c.phi = P.phi_u; c.inv_phi = P.inv_phi_u; c.c_lin = P.c_lin_u; c.c_nl = P.c_nl_u; c.s_v = P.s_v;
-  } else {
-    const int64_t o = (int64_t)y * P.pitch + x;
-    const float ph = __ldg(P.phi + o);
-    const float k = __ldg(P.K + o);
-    c.phi = ph;
-    c.inv_phi = fast_rcp(ph);
-    c.c_lin = ph * P.nu * fast_rcp(k);
-    c.c_nl = P.forch ? 1.75f * rsqrtf(150.0f * ph * k) : 0.0f;
-    c.s_v = P.sv ? __ldg(P.sv + o) : P.s_v;
-  }
-  return c;
+  if (!HET) return coef_uniform(P);
+  const int64_t o = (int64_t)y * P.pitch + x;
+  return coef_of(P, __ldg(P.phi + o), __ldg(P.K + o), P.sv ? __ldg(P.sv + o) : P.s_v);
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -18,8 +18,8 @@ int validate_config(const ::lbm_config* c);
 void params_from_config(const ::lbm_config& k, int prec, int pitch, int64_t plane, StepParams& P);
 int64_t batch_items(int nx, int ny, int bc_y, int nt);
 int batch_max_ctas_per_sm(int prec, int nt);
-cudaError_t launch_step_batch(const StepParams* Pd, const int64_t* item_start, int n, int64_t total, int prec, int nt, int grid,
-                              cudaStream_t s);
+cudaError_t launch_step_batch(const StepParams* Pd, const int64_t* item_start, const int* item_lattice, int n, int64_t total, int prec,
+                              int nt, int grid, cudaStream_t s);
 cudaError_t launch_step(const StepParams& P, int prec, bool het, bool thermal, cudaStream_t s);
 cudaError_t launch_medium(const float* eps, const float* K, float phi_u, float K_u, int nx, int ny, int pitch, float* phi_out,
                           float* K_out, unsigned int* err, int log_k, cudaStream_t s);

@@ -80,6 +80,13 @@ __device__ __forceinline__ void step_item(const StepParams& P, const Tiling& tl,
   const int64_t pl = P.plane;
   const int64_t rm = (int64_t)ym * P.pitch, r0 = (int64_t)y * P.pitch, rp = (int64_t)yp * P.pitch;
   const float inv = P.inv_scale;
+  // medium of the four cells, issued ahead of the populations (aligned: x0 and the pitch are
+  // multiples of 4 and the fields are allocated like the populations)
+  float4 ph4, k4;
+  if (HET) {
+    ph4 = __ldg(reinterpret_cast<const float4*>(P.phi + r0 + xl));
+    k4 = __ldg(reinterpret_cast<const float4*>(P.K + r0 + xl));
+  }
 
   // pull streaming, Eq. 15: d_i(x) = d+_i(x - e_i)
   float d[8][C];
@@ -110,7 +117,7 @@ __device__ __forceinline__ void step_item(const StepParams& P, const Tiling& tl,
     float dc[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) dc[i] = d[i][c];
-    const Coef cf = coef_at<HET>(P, x0 + c, y);
+    const Coef cf = HET ? coef_of(P, f4_get(ph4, c), f4_get(k4, c), P.sv ? __ldg(P.sv + r0 + x0 + c) : P.s_v) : coef_uniform(P);
     float ay = P.ay;
     if (THERMAL) ay += P.g_beta * (g[0][c] + g[1][c] + g[2][c] + g[3][c] + g[4][c]);  // a = g beta (T - T0) j
     float ux, uy, phip;
@@ -138,9 +145,11 @@ __device__ __forceinline__ void step_item(const StepParams& P, const Tiling& tl,
   }
 }
 
-// One time step of one lattice: one CTA per work item.
+// One time step of one lattice: one CTA per work item.  Register caps keep 8 CTAs (32 warps) per
+// SM resident for the flow alone (64 registers, no spill) and 6 with the temperature populations
+// (80 registers; 5 for FP16 storage, whose conversions would spill at 80).
 template <int PREC, bool HET, bool THERMAL>
-__global__ void __launch_bounds__(kStepThreads) k_step(const StepParams P, Tiling tl) {
+__global__ void __launch_bounds__(kStepThreads, THERMAL ? (PREC == PREC_FP16 ? 5 : 6) : 8) k_step(const StepParams P, Tiling tl) {
   step_item<PREC, HET, THERMAL, kStepThreads>(P, tl, blockIdx.x);
 }
 
@@ -168,15 +177,42 @@ cudaError_t launch_step(const StepParams& P, int prec, bool het, bool thermal, c
 }
 
 // --------------------------------------------------------------------------------------------
-// Batched ensemble: one persistent launch advances every lattice of a batch by one step.
-// Item ranges of the lattices are concatenated (item_start, ascending); CTA b walks the
-// contiguous range [b * chunk, (b + 1) * chunk) of items, so it looks its lattice up once (binary
-// search) and then only steps to the next lattice when the range crosses into it.  Lattice d's
-// parameters for the current buffer parity are Pd[d].
+// Batched ensemble: one launch advances every lattice of a batch by one step.  The work items of
+// the lattices are concatenated (item_start, ascending); lattice d's parameters for the current
+// buffer parity are Pd[d], copied once per CTA into shared memory (the streamed populations would
+// otherwise evict them from L1 between items).  Two launch forms:
+//   k_step_batch_items  one CTA per work item; item_lattice[item] names the item's lattice;
+//   k_step_batch        persistent: CTA b walks the contiguous range [b * chunk, (b + 1) * chunk)
+//                       of items, looks its lattice up once (binary search) and moves on to the
+//                       next lattice only when the range crosses into it.
 // --------------------------------------------------------------------------------------------
+template <int NT>
+__device__ __forceinline__ void load_params(StepParams& sP, const StepParams* __restrict__ Pd, int d) {
+  static_assert(sizeof(StepParams) % 8 == 0, "parameters are copied as 8-byte words");
+  const unsigned long long* from = reinterpret_cast<const unsigned long long*>(Pd + d);
+  unsigned long long* to = reinterpret_cast<unsigned long long*>(&sP);
+  for (int i = threadIdx.x; i < (int)(sizeof(StepParams) / 8); i += NT) to[i] = from[i];
+}
+
+// Register caps (measured on a 512-lattice ensemble): the streaming rate follows the number of
+// resident warps, so the per-item form is held to 64 registers (32 warps per SM, a few bytes of
+// spill) and the persistent form to 85 (24 warps); uncapped they take 72-108 registers and run
+// 1.2-1.5x slower.
 template <int PREC, int NT>
-__global__ void __launch_bounds__(NT) k_step_batch(const StepParams* __restrict__ Pd, const int64_t* __restrict__ item_start, int n,
+__global__ void __launch_bounds__(NT, 1024 / NT) k_step_batch_items(const StepParams* __restrict__ Pd, const int64_t* __restrict__ item_start,
+                                                         const int* __restrict__ item_lattice) {
+  __shared__ StepParams sP;
+  const int d = item_lattice[blockIdx.x];
+  load_params<NT>(sP, Pd, d);
+  __syncthreads();
+  const Tiling tl = tiling_of(sP.nx, sP.ny, sP.bc_y, NT);
+  step_item<PREC, true, false, NT>(sP, tl, (int)((int64_t)blockIdx.x - item_start[d]));
+}
+
+template <int PREC, int NT>
+__global__ void __launch_bounds__(NT, 768 / NT) k_step_batch(const StepParams* __restrict__ Pd, const int64_t* __restrict__ item_start, int n,
                                                    int64_t total) {
+  __shared__ StepParams sP;
   const int64_t chunk = (total + gridDim.x - 1) / gridDim.x;
   const int64_t begin = (int64_t)blockIdx.x * chunk;
   const int64_t end = begin + chunk < total ? begin + chunk : total;
@@ -186,15 +222,24 @@ __global__ void __launch_bounds__(NT) k_step_batch(const StepParams* __restrict_
     const int mid = (lo + hi + 1) >> 1;
     if (item_start[mid] <= begin) lo = mid; else hi = mid - 1;
   }
+  int64_t first = item_start[lo];
   int64_t next = lo + 1 < n ? item_start[lo + 1] : total;
+  load_params<NT>(sP, Pd, lo);
+  __syncthreads();
+  Tiling tl = tiling_of(sP.nx, sP.ny, sP.bc_y, NT);
   for (int64_t it = begin; it < end; ++it) {
-    while (it >= next) {
-      ++lo;
-      next = lo + 1 < n ? item_start[lo + 1] : total;
+    if (it >= next) {  // the range crosses into the next lattice(s): uniform over the CTA
+      while (it >= next) {
+        ++lo;
+        next = lo + 1 < n ? item_start[lo + 1] : total;
+      }
+      first = item_start[lo];
+      __syncthreads();  // every thread is done with the previous parameters
+      load_params<NT>(sP, Pd, lo);
+      __syncthreads();
+      tl = tiling_of(sP.nx, sP.ny, sP.bc_y, NT);
     }
-    const StepParams& P = Pd[lo];
-    const Tiling tl = tiling_of(P.nx, P.ny, P.bc_y, NT);
-    step_item<PREC, true, false, NT>(P, tl, (int)(it - item_start[lo]));
+    step_item<PREC, true, false, NT>(sP, tl, (int)(it - first));
   }
 }
 
@@ -207,18 +252,27 @@ int64_t batch_items(int nx, int ny, int bc_y, int nt) {
   return (int64_t)tl.frame_blocks + main_items(tl, ny);
 }
 
+template <int PREC, int NT>
+static void launch_batch_t(const StepParams* Pd, const int64_t* item_start, const int* item_lattice, int n, int64_t total, int grid,
+                           cudaStream_t s) {
+  if (item_lattice)
+    k_step_batch_items<PREC, NT><<<(unsigned)total, NT, 0, s>>>(Pd, item_start, item_lattice);
+  else
+    k_step_batch<PREC, NT><<<grid, NT, 0, s>>>(Pd, item_start, n, total);
+}
+
 template <int PREC>
-static cudaError_t launch_batch_p(const StepParams* Pd, const int64_t* item_start, int n, int64_t total, int nt, int grid,
-                                  cudaStream_t s) {
+static cudaError_t launch_batch_p(const StepParams* Pd, const int64_t* item_start, const int* item_lattice, int n, int64_t total,
+                                  int nt, int grid, cudaStream_t s) {
   switch (nt) {
-    case 64: k_step_batch<PREC, 64><<<grid, 64, 0, s>>>(Pd, item_start, n, total); break;
-    case 256: k_step_batch<PREC, 256><<<grid, 256, 0, s>>>(Pd, item_start, n, total); break;
-    default: k_step_batch<PREC, 128><<<grid, 128, 0, s>>>(Pd, item_start, n, total); break;
+    case 64: launch_batch_t<PREC, 64>(Pd, item_start, item_lattice, n, total, grid, s); break;
+    case 256: launch_batch_t<PREC, 256>(Pd, item_start, item_lattice, n, total, grid, s); break;
+    default: launch_batch_t<PREC, 128>(Pd, item_start, item_lattice, n, total, grid, s); break;
   }
   return cudaGetLastError();
 }
 
-// Largest number of CTAs of the batched kernel (prec, nt) resident on one SM.
+// Largest number of CTAs of the persistent batched kernel (prec, nt) resident on one SM.
 int batch_max_ctas_per_sm(int prec, int nt) {
   int k = 0;
   const void* fn = nullptr;
@@ -231,11 +285,11 @@ int batch_max_ctas_per_sm(int prec, int nt) {
   return k > 0 ? k : 1;
 }
 
-cudaError_t launch_step_batch(const StepParams* Pd, const int64_t* item_start, int n, int64_t total, int prec, int nt, int grid,
-                              cudaStream_t s) {
-  if (prec == PREC_FP32) return launch_batch_p<PREC_FP32>(Pd, item_start, n, total, nt, grid, s);
-  if (prec == PREC_FP16) return launch_batch_p<PREC_FP16>(Pd, item_start, n, total, nt, grid, s);
-  return launch_batch_p<PREC_BF16>(Pd, item_start, n, total, nt, grid, s);
+cudaError_t launch_step_batch(const StepParams* Pd, const int64_t* item_start, const int* item_lattice, int n, int64_t total, int prec,
+                              int nt, int grid, cudaStream_t s) {
+  if (prec == PREC_FP32) return launch_batch_p<PREC_FP32>(Pd, item_start, item_lattice, n, total, nt, grid, s);
+  if (prec == PREC_FP16) return launch_batch_p<PREC_FP16>(Pd, item_start, item_lattice, n, total, nt, grid, s);
+  return launch_batch_p<PREC_BF16>(Pd, item_start, item_lattice, n, total, nt, grid, s);
 }
 
 }  // namespace lbm

@@ -5,12 +5,14 @@ Batched ensemble of independent porous cavities and channels (``ensemble``, ``bu
 Each lattice draws its size, kind and Reynolds number from ``synth.ensemble_domains`` and its
 porosity / permeability field from ``synth.heterogeneous_medium`` (log K Gaussian with mean
 log(Da H^2), eps = clip(0.3 + 0.1 N, 0.1, 0.9), correlation length 32 cells).  Lattice parameters:
-  cavity  -- halfway walls, top wall moving at U = 0.05, nu = max(U H / Re, 0.02);
+  cavity  -- halfway walls, top wall moving at U = 0.03, nu = max(U H / Re, 0.02);
   channel -- periodic in x, walls in y, body force a_x chosen so that the Darcy-Brinkman centre
              speed of the mean medium (the closed form behind Eq. 24 with F_phi = 0) is U = 0.02,
              nu = max(U H / Re, 0.02).
-The floor on nu keeps tau_v >= 0.56 and the speeds keep |u| / sqrt(eps) well below c_s where the
-porosity is lowest (eps >= 0.1): the equilibrium of Eq. 11 carries |u|^2 / eps.
+The floor on nu keeps tau_v >= 0.56 and the speeds keep |u| / (c_s sqrt(eps)) <= 0.16 where the
+porosity is lowest (eps >= 0.1): the equilibrium of Eq. 11 carries |u|^2 / eps.  With a lid at
+U = 0.05 (0.27 over eps = 0.1) FP32 stays bounded but FP16 and BF16 deviation storage diverge at
+the lid within a few thousand steps.
 All lattices start from the rest state phi p = mean(eps) (uniform phi p over a varying porosity).
 
 Pressure-driven heterogeneous channel for the adjoint (``adjoint_channel``): log K Gaussian with
@@ -44,7 +46,7 @@ def ensemble(lbm, n=512, seed=42, lo=64, hi=1024, precision=0, da=1e-3):
         phi_m = float(eps.mean())
         K_m = float(np.exp(np.log(K.astype(np.float64)).mean()))
         if dom["kind"] == "cavity":
-            U = 0.05
+            U = 0.03
             nu = max(U * ny / Re, 0.02)
             kw = dict(bc_x=lbm.WALL, bc_y=lbm.WALL, u_wall=[(0, 0), (0, 0), (0, 0), (U, 0)])
         else:
