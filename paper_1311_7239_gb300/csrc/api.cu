@@ -87,6 +87,32 @@ void params_from_config(const lbm_config& k, int prec, int pitch, int64_t plane,
   P.varpi = 0.0f;  // Appendix B fixes varpi = 0
   P.g_beta = (float)k.g_beta;
   P.T0 = (float)k.T0;
+  // constants of the two-cell collision (moments of the stored deviations s d)
+  const double rs = k.rho0 * sc, sv = 1.0 / tau_v, hv = 1.0 - 0.5 * sv;
+  PairConst& q = P.pc;
+  q.inv_rho0s = (float)(1.0 / rs);
+  q.nphip = (float)(-2.0 / 3.0 * rs);
+  q.nse8 = (float)(-k.s_e / 8.0);
+  q.sq6 = (float)(k.s_q / 6.0);
+  q.nsq12 = (float)(-k.s_q / 12.0);
+  q.r3 = (float)(rs / 3.0);
+  q.r12 = (float)(rs / 12.0);
+  q.hay = (float)(0.5 * k.ay);
+  q.cq = (float)(-0.25 * sv);
+  const double c_lin = k.phi * k.nu / k.K, c_nl = k.forchheimer ? 1.75 / sqrt(150.0 * k.phi * k.K) : 0.0;
+  const double l0 = 0.5 + 0.25 * c_lin;
+  q.u_inv_phi = (float)(1.0 / k.phi);
+  q.u_l0 = (float)l0;
+  q.u_l0sq = (float)(l0 * l0);
+  q.u_l1 = (float)(0.5 * c_nl);
+  q.u_nclin = (float)(-c_lin);
+  q.u_ncnl = (float)(-c_nl);
+  q.u_c2 = (float)(0.1 * (1.0 - 0.5 * k.s_e) * rs / k.phi);
+  q.u_nR = (float)(-rs / k.phi);
+  q.u_cf7 = (float)(0.5 * hv * rs / k.phi);
+  q.u_cf8 = (float)(0.25 * hv * rs / k.phi);
+  q.u_hx = (float)(0.5 * k.phi * k.ax);
+  q.u_hy = (float)(0.5 * k.phi * k.ay);
 }
 
 }  // namespace lbm

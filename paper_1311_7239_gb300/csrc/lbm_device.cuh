@@ -23,6 +23,20 @@ namespace lbm {
 enum : int { PREC_FP32 = 0, PREC_FP16 = 1, PREC_BF16 = 2 };
 enum : int { BC_PERIODIC = 0, BC_WALL = 1, BC_PRESSURE = 2 };
 
+// Constants of the two-cell collision (collide_pair), derived on the host from the configuration.
+// Moments there are taken of the stored (scaled) deviations s d, so every constant that turns a
+// physical quantity into a moment increment carries the storage scale s (1 for FP32 and BF16).
+struct PairConst {
+  float inv_rho0s;             // 1 / (rho0 s)
+  float nphip;                 // -(2/3) rho0 s                 (Eq. 20)
+  float nse8, sq6, nsq12;      // -s_e / 8, s_q / 6, -s_q / 12   (Lambda times the diagonal of M^-1)
+  float r3, r12;               // rho0 s / 3, rho0 s / 12        (rho0 F through M^-1)
+  float hay;                   // a_y / 2
+  float cq;                    // -s_v / 4
+  // medium coefficients of the uniform medium (see PairCoef) and phi a / 2
+  float u_inv_phi, u_l0, u_l0sq, u_l1, u_nclin, u_ncnl, u_c2, u_nR, u_cf7, u_cf8, u_hx, u_hy;
+};
+
 // Everything a step kernel needs, passed by value.
 struct StepParams {
   const void* src;   // current post-collision planes (8)
@@ -49,6 +63,7 @@ struct StepParams {
   float Tw[4];
   int Tdir[4];        // 1 = wall temperature prescribed, 0 = adiabatic
   unsigned int* err;  // bit 0: non-finite velocity
+  PairConst pc;
 };
 
 // D2Q8 velocities of Eq. 7 and the weights w_i listed after Eq. 20 (w_1..4 = 1/9, w_5..8 = 1/36).
@@ -61,8 +76,14 @@ __device__ __forceinline__ float w_of(int i) { return i < 4 ? (1.0f / 9.0f) : (1
 // storage codecs
 // ---------------------------------------------------------------------------------------------
 template <int PREC> struct Store;
+// dec/enc and load4/store4 convert between stored and true deviations (the FP16 scale); decr,
+// load4r and store4r move the stored values unchanged.
 template <> struct Store<PREC_FP32> {
   using T = float;
+  __device__ static __forceinline__ float decr(T v) { return v; }
+  __device__ static __forceinline__ void load4r(const T* p, float o[4]) { load4(p, o, 1.0f); }
+  __device__ static __forceinline__ void store4r(T* p, const float o[4]) { store4(p, o, 1.0f); }
+  __device__ static __forceinline__ void store2r(T* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
   __device__ static __forceinline__ float dec(T v, float) { return v; }
   __device__ static __forceinline__ T enc(float v, float) { return v; }
   __device__ static __forceinline__ void load4(const T* p, float o[4], float) {
@@ -75,6 +96,22 @@ template <> struct Store<PREC_FP32> {
 };
 template <> struct Store<PREC_FP16> {
   using T = __half;
+  __device__ static __forceinline__ float decr(T v) { return __half2float(v); }
+  __device__ static __forceinline__ void load4r(const T* p, float o[4]) {
+    const uint2 raw = *reinterpret_cast<const uint2*>(p);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&raw.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&raw.y));
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+  }
+  __device__ static __forceinline__ void store4r(T* p, const float o[4]) {
+    __half2 a = __floats2half2_rn(o[0], o[1]);
+    __half2 b = __floats2half2_rn(o[2], o[3]);
+    uint2 raw;
+    raw.x = *reinterpret_cast<unsigned int*>(&a);
+    raw.y = *reinterpret_cast<unsigned int*>(&b);
+    *reinterpret_cast<uint2*>(p) = raw;
+  }
+  __device__ static __forceinline__ void store2r(T* p, float2 v) { *reinterpret_cast<__half2*>(p) = __float22half2_rn(v); }
   __device__ static __forceinline__ float dec(T v, float inv) { return __half2float(v) * inv; }
   __device__ static __forceinline__ T enc(float v, float sc) { return __float2half_rn(v * sc); }
   __device__ static __forceinline__ void load4(const T* p, float o[4], float inv) {
@@ -95,6 +132,10 @@ template <> struct Store<PREC_FP16> {
 // BF16 keeps FP32's exponent range, so its deviations are stored unscaled (scale = 1).
 template <> struct Store<PREC_BF16> {
   using T = __nv_bfloat16;
+  __device__ static __forceinline__ float decr(T v) { return __bfloat162float(v); }
+  __device__ static __forceinline__ void load4r(const T* p, float o[4]) { load4(p, o, 1.0f); }
+  __device__ static __forceinline__ void store4r(T* p, const float o[4]) { store4(p, o, 1.0f); }
+  __device__ static __forceinline__ void store2r(T* p, float2 v) { *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(v); }
   __device__ static __forceinline__ float dec(T v, float) { return __bfloat162float(v); }
   __device__ static __forceinline__ T enc(float v, float) { return __float2bfloat16_rn(v); }
   __device__ static __forceinline__ void load4(const T* p, float o[4], float) {
@@ -245,6 +286,94 @@ __device__ __forceinline__ void collide_d2q8(float d[8], const Coef& c, float ax
   ux_out = ux;
   uy_out = uy;
   phip_out = phip_dev;
+}
+
+// ---------------------------------------------------------------------------------------------
+// The same collision for two cells at once, on the packed FP32 pairs of sm_100+ (FADD2, FMUL2,
+// FFMA2: one instruction for both cells, each lane rounded as the scalar operation).  d holds the
+// stored deviations s d of the two cells (s: storage scale), so the scale is folded into the
+// constants instead of being applied on every load and store; u is returned in lattice units.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Medium coefficients of a cell pair (Eqs. 3-4, 13, 18), scaled as PairConst says (uniform medium:
+// the same for both cells, from the host).
+struct PairCoef {
+  float2 inv_phi;     // 1 / phi
+  float2 l0, l0sq;    // l0 = 1/2 + c_lin / 4 and l0^2 (Eq. 18)
+  float2 l1;          // l1 = c_nl / 2
+  float2 nclin, ncnl; // -c_lin = -phi nu / K, -c_nl = -1.75 / sqrt(150 phi K)
+  float2 c2;          // 0.1 (1 - s_e/2) rho0 s / phi     (S2 / 8 = c2 (u . F))
+  float2 cq;          // -s_v / 4
+  float2 nR;          // -rho0 s / phi
+  float2 cf7, cf8;    // (1 - s_v/2) rho0 s / (2 phi), / (4 phi)
+};
+
+__device__ __forceinline__ PairCoef pair_coef_uniform(const PairConst& K) {
+  PairCoef c;
+  c.inv_phi = f2(K.u_inv_phi); c.l0 = f2(K.u_l0); c.l0sq = f2(K.u_l0sq); c.l1 = f2(K.u_l1);
+  c.nclin = f2(K.u_nclin); c.ncnl = f2(K.u_ncnl); c.c2 = f2(K.u_c2); c.cq = f2(K.cq); c.nR = f2(K.u_nR);
+  c.cf7 = f2(K.u_cf7); c.cf8 = f2(K.u_cf8);
+  return c;
+}
+
+// hx, hy: phi a / 2 of the two cells.  d: in, stored pre-collision deviations; out, post-collision.
+__device__ __forceinline__ void collide_pair(float2 d[8], const PairCoef& c, float2 hx, float2 hy, const PairConst& K, float2& ux,
+                                             float2& uy) {
+  // m = M d, Eq. 10 (as collide_d2q8)
+  const float2 a13 = add2(d[0], d[2]), a24 = add2(d[1], d[3]);
+  const float2 d13 = sub2(d[0], d[2]), d24 = sub2(d[1], d[3]);
+  const float2 s57 = add2(d[4], d[6]), s68 = add2(d[5], d[7]);
+  const float2 t57 = sub2(d[4], d[6]), t68 = sub2(d[5], d[7]);
+  const float2 diag = add2(s57, s68), A = add2(a13, a24);
+  const float2 m1 = add2(A, diag), m2 = sub2(diag, A);
+  const float2 dxs = sub2(t57, t68), dys = add2(t57, t68);
+  const float2 m3 = add2(d13, dxs), m5 = add2(d24, dys);
+  const float2 m7 = sub2(a13, a24), m8 = sub2(s57, s68);
+
+  // Eqs. 18-19: v = j / rho0 + phi a / 2, |u| = |v| / (l0 + sqrt(l0^2 + l1 |v|))
+  const float2 vx = fma2(m3, f2(K.inv_rho0s), hx), vy = fma2(m5, f2(K.inv_rho0s), hy);
+  const float2 vsq = fma2(vx, vx, mul2(vy, vy));
+  const float2 vmag = mul2(vsq, make_float2(vsq.x > 0.0f ? rsqrtf(vsq.x) : 0.0f, vsq.y > 0.0f ? rsqrtf(vsq.y) : 0.0f));
+  const float2 t = fma2(c.l1, vmag, c.l0sq);  // >= l0^2 >= 1/4
+  const float2 den = add2(c.l0, mul2(t, make_float2(rsqrtf(t.x), rsqrtf(t.y))));
+  const float2 inv = make_float2(fast_rcp(den.x), fast_rcp(den.y));
+  ux = mul2(vx, inv);
+  uy = mul2(vy, inv);
+  const float2 umag = mul2(vmag, inv);
+  // Eq. 20: phi p - p_rest = 3/5 (m1 - 2/3 rho0 |u|^2 / phi)   (times s)
+  const float2 phip = mul2(f2(0.6f), fma2(f2(K.nphip), mul2(fma2(ux, ux, mul2(uy, uy)), c.inv_phi), m1));
+  // Eq. 3: F = -(c_lin + c_nl |u|) u + phi a
+  const float2 nd = fma2(c.ncnl, umag, c.nclin);
+  const float2 Fx = fma2(nd, ux, add2(hx, hx)), Fy = fma2(nd, uy, add2(hy, hy));
+
+  // increments k = m+ - m (Eqs. 11-14, as collide_d2q8) times the diagonal of M^-1:
+  //   q2 = k2/8, X = k3/6 - k4/6 = rho0 F_x / 3 + s_q (m4 + m3) / 6, P_x = k3/6 + k4/12 =
+  //   rho0 F_x / 12 - s_q (m4 + m3) / 12 (k4 = -s_q (m4 + m3) - rho0 F_x), q7 = k7/4, q8 = k8/4
+  const float2 pxF = mul2(ux, Fx), pyF = mul2(uy, Fy);
+  const float2 q2 = fma2(f2(K.nse8), add2(m2, phip), mul2(c.c2, add2(pxF, pyF)));
+  const float2 gx = fma2(f2(2.0f), dxs, neg2(d13)), gy = fma2(f2(2.0f), dys, neg2(d24));  // m4 + m3, m6 + m5
+  const float2 X = fma2(f2(K.sq6), gx, mul2(f2(K.r3), Fx)), Y = fma2(f2(K.sq6), gy, mul2(f2(K.r3), Fy));
+  const float2 Px = fma2(f2(K.nsq12), gx, mul2(f2(K.r12), Fx)), Py = fma2(f2(K.nsq12), gy, mul2(f2(K.r12), Fy));
+  const float2 q7 = fma2(c.cq, fma2(c.nR, fma2(ux, ux, neg2(mul2(uy, uy))), m7), mul2(c.cf7, sub2(pxF, pyF)));
+  const float2 q8 = fma2(c.cq, fma2(c.nR, mul2(ux, uy), m8), mul2(c.cf8, fma2(ux, Fy, mul2(uy, Fx))));
+
+  // d+ = d + M^-1 k (as collide_d2q8, with shared partial sums)
+  const float2 B = sub2(q7, q2), Cn = add2(q7, q2);
+  d[0] = add2(d[0], add2(B, X));
+  d[2] = add2(d[2], sub2(B, X));
+  d[1] = add2(d[1], sub2(Y, Cn));
+  d[3] = sub2(d[3], add2(Y, Cn));
+  const float2 G = add2(q8, q2), H = sub2(q2, q8), PP = add2(Px, Py), PM = sub2(Px, Py);
+  d[4] = add2(d[4], add2(PP, G));
+  d[6] = add2(d[6], sub2(G, PP));
+  d[5] = add2(d[5], sub2(H, PM));
+  d[7] = add2(d[7], add2(H, PM));
 }
 
 // macroscopic quantities only (no collision), for read-out kernels

@@ -14,6 +14,13 @@
 
 namespace lbm {
 
+// Interior cells of a uniform medium with 16-bit storage, where the step is bound by instruction
+// issue rather than by HBM, are collided two at a time with the packed FP32 pairs (collide_pair);
+// FP32 storage and per-cell media keep the scalar collision, whose lower register count holds
+// more loads in flight.
+template <int PREC, bool HET>
+constexpr bool kPacked = PREC != PREC_FP32 && !HET;
+
 template <int PREC, bool HET, bool THERMAL>
 __device__ void frame_step(const StepParams& P, const Frame& F, int k) {
   using S = Store<PREC>;
@@ -88,16 +95,17 @@ __device__ __forceinline__ void step_item(const StepParams& P, const Tiling& tl,
     k4 = __ldg(reinterpret_cast<const float4*>(P.K + r0 + xl));
   }
 
-  // pull streaming, Eq. 15: d_i(x) = d+_i(x - e_i)
+  // pull streaming, Eq. 15: d_i(x) = d+_i(x - e_i) (as stored, s d, for the pair collision)
+  constexpr bool R = kPacked<PREC, HET>;
   float d[8][C];
-  gather4<PREC, 1>(src + 0 * pl + r0, xl, P.pitch, lane, inv, d[0]);   // e1 = ( 1, 0)
-  gather4<PREC, 0>(src + 1 * pl + rm, xl, P.pitch, lane, inv, d[1]);   // e2 = ( 0, 1)
-  gather4<PREC, -1>(src + 2 * pl + r0, xl, P.pitch, lane, inv, d[2]);  // e3 = (-1, 0)
-  gather4<PREC, 0>(src + 3 * pl + rp, xl, P.pitch, lane, inv, d[3]);   // e4 = ( 0,-1)
-  gather4<PREC, 1>(src + 4 * pl + rm, xl, P.pitch, lane, inv, d[4]);   // e5 = ( 1, 1)
-  gather4<PREC, -1>(src + 5 * pl + rm, xl, P.pitch, lane, inv, d[5]);  // e6 = (-1, 1)
-  gather4<PREC, -1>(src + 6 * pl + rp, xl, P.pitch, lane, inv, d[6]);  // e7 = (-1,-1)
-  gather4<PREC, 1>(src + 7 * pl + rp, xl, P.pitch, lane, inv, d[7]);   // e8 = ( 1,-1)
+  gather4<PREC, 1, R>(src + 0 * pl + r0, xl, P.pitch, lane, inv, d[0]);   // e1 = ( 1, 0)
+  gather4<PREC, 0, R>(src + 1 * pl + rm, xl, P.pitch, lane, inv, d[1]);   // e2 = ( 0, 1)
+  gather4<PREC, -1, R>(src + 2 * pl + r0, xl, P.pitch, lane, inv, d[2]);  // e3 = (-1, 0)
+  gather4<PREC, 0, R>(src + 3 * pl + rp, xl, P.pitch, lane, inv, d[3]);   // e4 = ( 0,-1)
+  gather4<PREC, 1, R>(src + 4 * pl + rm, xl, P.pitch, lane, inv, d[4]);   // e5 = ( 1, 1)
+  gather4<PREC, -1, R>(src + 5 * pl + rm, xl, P.pitch, lane, inv, d[5]);  // e6 = (-1, 1)
+  gather4<PREC, -1, R>(src + 6 * pl + rp, xl, P.pitch, lane, inv, d[6]);  // e7 = (-1,-1)
+  gather4<PREC, 1, R>(src + 7 * pl + rp, xl, P.pitch, lane, inv, d[7]);   // e8 = ( 1,-1)
   float g[5][C];
   if (THERMAL) {
     const T* __restrict__ gsrc = static_cast<const T*>(P.gsrc);
@@ -112,32 +120,66 @@ __device__ __forceinline__ void step_item(const StepParams& P, const Tiling& tl,
   if (!has_group || wall_row || x0 == 0 || x0 + C >= P.nx) return;
 
   float check = 0.0f;
+  if constexpr (R) {
 #pragma unroll
-  for (int c = 0; c < C; ++c) {
-    float dc[8];
+    for (int h = 0; h < C / 2; ++h) {  // cells (x0 + 2h, x0 + 2h + 1) as one packed pair
+      const int c0 = 2 * h, c1 = 2 * h + 1;
+      float2 dp[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) dc[i] = d[i][c];
-    const Coef cf = HET ? coef_of(P, f4_get(ph4, c), f4_get(k4, c), P.sv ? __ldg(P.sv + r0 + x0 + c) : P.s_v) : coef_uniform(P);
-    float ay = P.ay;
-    if (THERMAL) ay += P.g_beta * (g[0][c] + g[1][c] + g[2][c] + g[3][c] + g[4][c]);  // a = g beta (T - T0) j
-    float ux, uy, phip;
-    collide_d2q8(dc, cf, P.ax, ay, P, ux, uy, phip);
-    check += fabsf(ux) + fabsf(uy);
+      for (int i = 0; i < 8; ++i) dp[i] = make_float2(d[i][c0], d[i][c1]);
+      float2 hy = f2(P.pc.u_hy);
+      if (THERMAL) {  // a_y = g beta (T - T0) j added to the body force (Boussinesq)
+        const float2 Td = make_float2(g[0][c0] + g[1][c0] + g[2][c0] + g[3][c0] + g[4][c0],
+                                      g[0][c1] + g[1][c1] + g[2][c1] + g[3][c1] + g[4][c1]);
+        hy = mul2(f2(P.phi_u), fma2(f2(0.5f * P.g_beta), Td, f2(P.pc.hay)));
+      }
+      float2 ux, uy;
+      collide_pair(dp, pair_coef_uniform(P.pc), f2(P.pc.u_hx), hy, P.pc, ux, uy);
+      check += (fabsf(ux.x) + fabsf(uy.x)) + (fabsf(ux.y) + fabsf(uy.y));
 #pragma unroll
-    for (int i = 0; i < 8; ++i) d[i][c] = dc[i];
-    if (THERMAL) {
-      float gc[5];
+      for (int i = 0; i < 8; ++i) S::store2r(dst + i * pl + r0 + x0 + c0, dp[i]);
+      if (THERMAL) {
+        float gc[5];
 #pragma unroll
-      for (int i = 0; i < 5; ++i) gc[i] = g[i][c];
-      collide_d2q5(gc, ux, uy, P);
+        for (int i = 0; i < 5; ++i) gc[i] = g[i][c0];
+        collide_d2q5(gc, ux.x, uy.x, P);
 #pragma unroll
-      for (int i = 0; i < 5; ++i) g[i][c] = gc[i];
+        for (int i = 0; i < 5; ++i) g[i][c0] = gc[i];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) gc[i] = g[i][c1];
+        collide_d2q5(gc, ux.y, uy.y, P);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) g[i][c1] = gc[i];
+      }
     }
+  } else {
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      float dc[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) dc[i] = d[i][c];
+      const Coef cf = HET ? coef_of(P, f4_get(ph4, c), f4_get(k4, c), P.sv ? __ldg(P.sv + r0 + x0 + c) : P.s_v) : coef_uniform(P);
+      float ay = P.ay;
+      if (THERMAL) ay += P.g_beta * (g[0][c] + g[1][c] + g[2][c] + g[3][c] + g[4][c]);  // a = g beta (T - T0) j
+      float ux, uy, phip;
+      collide_d2q8(dc, cf, P.ax, ay, P, ux, uy, phip);
+      check += fabsf(ux) + fabsf(uy);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) d[i][c] = dc[i];
+      if (THERMAL) {
+        float gc[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) gc[i] = g[i][c];
+        collide_d2q5(gc, ux, uy, P);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) g[i][c] = gc[i];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) S::store4(dst + i * pl + r0 + x0, d[i], P.scale);
   }
   if (!(check < 1e30f)) atomicOr(P.err, 1u);  // non-finite velocity in these cells
   const float sc = P.scale;
-#pragma unroll
-  for (int i = 0; i < 8; ++i) S::store4(dst + i * pl + r0 + x0, d[i], sc);
   if (THERMAL) {
     T* __restrict__ gdst = static_cast<T*>(P.gdst);
 #pragma unroll
@@ -145,11 +187,11 @@ __device__ __forceinline__ void step_item(const StepParams& P, const Tiling& tl,
   }
 }
 
-// One time step of one lattice: one CTA per work item.  Register caps keep 8 CTAs (32 warps) per
-// SM resident for the flow alone (64 registers, no spill) and 6 with the temperature populations
-// (80 registers; 5 for FP16 storage, whose conversions would spill at 80).
+// One time step of one lattice: one CTA per work item.  Register caps: 8 CTAs (32 warps) per SM
+// for the flow alone (64 registers, no spill), 7 for the packed collision of 16-bit storage (72,
+// a few words of spill), 6 and 5 with the temperature populations (80 and 96).
 template <int PREC, bool HET, bool THERMAL>
-__global__ void __launch_bounds__(kStepThreads, THERMAL ? (PREC == PREC_FP16 ? 5 : 6) : 8) k_step(const StepParams P, Tiling tl) {
+__global__ void __launch_bounds__(kStepThreads, THERMAL ? (PREC == PREC_FP32 ? 6 : 5) : (kPacked<PREC, HET> ? 7 : 8)) k_step(const StepParams P, Tiling tl) {
   step_item<PREC, HET, THERMAL, kStepThreads>(P, tl, blockIdx.x);
 }
 

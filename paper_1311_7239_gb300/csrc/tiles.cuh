@@ -12,22 +12,30 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kStepThreads = 128;
 constexpr int kCellsPerThread = 4;
 
-// out[c] = row[x0 + c - SH] for c = 0..3 (SH = +1: pull from x-1, SH = -1: from x+1, 0: aligned)
-template <int PREC, int SH>
+// out[c] = row[x0 + c - SH] for c = 0..3 (SH = +1: pull from x-1, SH = -1: from x+1, 0: aligned);
+// RAW: the stored values as they are (no storage scale applied).
+template <int PREC, int SH, bool RAW = false>
 __device__ __forceinline__ void gather4(const typename Store<PREC>::T* __restrict__ row, int xl, int pitch, int lane,
                                         float inv, float out[4]) {
   using S = Store<PREC>;
   float v[4];
-  S::load4(row + xl, v, inv);
+  if (RAW) S::load4r(row + xl, v);
+  else S::load4(row + xl, v, inv);
   if (SH == 0) {
     out[0] = v[0]; out[1] = v[1]; out[2] = v[2]; out[3] = v[3];
   } else if (SH == 1) {
     float left = __shfl_up_sync(kFull, v[3], 1);
-    if (lane == 0) left = S::dec(row[xl > 0 ? xl - 1 : 0], inv);
+    if (lane == 0) {
+      const typename S::T e = row[xl > 0 ? xl - 1 : 0];
+      left = RAW ? S::decr(e) : S::dec(e, inv);
+    }
     out[0] = left; out[1] = v[0]; out[2] = v[1]; out[3] = v[2];
   } else {
     float right = __shfl_down_sync(kFull, v[0], 1);
-    if (lane == 31) right = S::dec(row[xl + 4 < pitch ? xl + 4 : pitch - 1], inv);
+    if (lane == 31) {
+      const typename S::T e = row[xl + 4 < pitch ? xl + 4 : pitch - 1];
+      right = RAW ? S::decr(e) : S::dec(e, inv);
+    }
     out[0] = v[1]; out[1] = v[2]; out[2] = v[3]; out[3] = right;
   }
 }
