@@ -470,10 +470,10 @@ def run_case(args, local_rank):
         L, _, _ = lat.adjoint(64, "flux")
         lat.close()
         print(json.dumps({"case": "adjoint", "loss": L}))
-    elif args.case == "batch":  # 64 lattices of the ensemble, FP32, launch 64 x 8
+    elif args.case == "batch":  # 64 lattices of the ensemble, FP32, one 64-thread CTA per work item
         cfgs, media = workloads.ensemble(lbm, n=64, seed=42)
         b = workloads.build(lbm, cfgs, media)
-        b.set_launch(64, 8)
+        b.set_launch(64, 0)
         b.step(8)
         b.sync()
         print(json.dumps({"case": "batch", **b.info()}))
