@@ -311,7 +311,7 @@ def ensemble_form(lbm, steps, local_rank):
             e1.record(s)
             e1.synchronize()
         ms_b = e0.elapsed_time(e1)
-        each = max(2, steps // 16)
+        each = max(2, min(steps // 16, 640))
         e0.record(s)
         b.step_each(each)
         e1.record(s)
@@ -445,7 +445,7 @@ def run_gpu(args, rank, world, local_rank):
         line["forms"]["heterogeneous"] = heterogeneous_form(lbm, args.size, max(64, args.steps // 4), args.warmup, local_rank)
         line["forms"]["adjoint"] = adjoint_form(lbm, T=args.adjoint_steps)
         if not args.no_ensemble:
-            line["forms"]["ensemble"] = ensemble_form(lbm, max(64, args.steps // 16), local_rank)
+            line["forms"]["ensemble"] = ensemble_form(lbm, args.ensemble_steps, local_rank)
     acc = accuracy_record()
     if acc:
         line["accuracy"] = acc
@@ -549,6 +549,7 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the other storage precisions")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 512-lattice ensemble form")
     ap.add_argument("--adjoint-steps", type=int, default=4000, help="T of the adjoint form")
+    ap.add_argument("--ensemble-steps", type=int, default=10000, help="steps of the 512-lattice ensemble form")
     ap.add_argument("--case", default="", choices=["", "adjoint", "batch", "fp16", "thermal", "nusselt"],
                     help="run one small case of a kernel family (for profiler captures) and exit")
     ap.add_argument("--sweep", default="", help="comma-separated lattice sizes: print one line per size and precision")

@@ -1,3 +1,4 @@
+import json
 import os
 import sys
 
@@ -11,3 +12,21 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built liblbm.so")
     config.addinivalue_line("markers", "slow: long-running CPU check (minutes)")
+
+
+# Relative L2 errors against the FP64 oracle measured by the GPU tests; written as JSON to the path
+# in LBM_ACCURACY_OUT (if set) when the session ends.
+_ACCURACY = []
+
+
+@pytest.fixture(scope="session")
+def accuracy():
+    return _ACCURACY
+
+
+def pytest_sessionfinish(session, exitstatus):
+    out = os.environ.get("LBM_ACCURACY_OUT")
+    if out and _ACCURACY:
+        with open(out, "w") as fh:
+            json.dump({"source": "python -m pytest tests -m gpu (FP64 oracle vs liblbm.so on the same seeded inputs)",
+                       "cases": _ACCURACY}, fh, indent=1)

@@ -55,7 +55,7 @@ CASES = {
 
 
 @pytest.mark.parametrize("name", list(CASES))
-def test_adjoint_matches_oracle_adjoint(lbm, name):
+def test_adjoint_matches_oracle_adjoint(lbm, accuracy, name):
     case, T, kind, phip = CASES[name]
     rng = np.random.default_rng(7)
     target = None
@@ -65,11 +65,14 @@ def test_adjoint_matches_oracle_adjoint(lbm, name):
     assert abs(L - Lo) <= 1e-5 * abs(Lo) + 1e-9, (L, Lo)
     sk, se = np.abs(gko).max(), np.abs(geo).max()
     assert sk > 0 and se > 0
+    accuracy.append({"case": f"adjoint {name}, T {T}", "precision": "fp32 (fp64 gradients)", "rel_loss": abs(L - Lo) / abs(Lo),
+                     "max_rel_grad_logK": float(np.abs(gk - gko).max() / sk), "max_rel_grad_eps": float(np.abs(ge - geo).max() / se),
+                     "bound": 1e-4})
     assert np.abs(gk - gko).max() <= 1e-4 * sk, (np.abs(gk - gko).max(), sk)
     assert np.abs(ge - geo).max() <= 1e-4 * se, (np.abs(ge - geo).max(), se)
 
 
-def test_adjoint_matches_central_differences_at_64_cells(lbm):
+def test_adjoint_matches_central_differences_at_64_cells(lbm, accuracy):
     """Config-4-like crop: pressure-driven heterogeneous channel, outlet flux, 64 random cells."""
     case, T, kind, _ = CASES["pressure-channel-flux"]
     phip = case.p_rest()
@@ -86,6 +89,7 @@ def test_adjoint_matches_central_differences_at_64_cells(lbm):
             f = adj.step(f, fl2, lk, phi)
         return adj.loss_value(f, fl2, "flux")
 
+    worst = {"logK": 0.0, "phi": 0.0}
     for cell in cells:
         for which, h in (("logK", 1e-4), ("phi", 1e-5)):
             vals = []
@@ -98,7 +102,10 @@ def test_adjoint_matches_central_differences_at_64_cells(lbm):
                 vals.append(loss(phi, K))
             fd = (vals[0] - vals[1]) / (2 * h)
             g, sc = (gk[cell], sk) if which == "logK" else (ge[cell], se)
+            worst[which] = max(worst[which], abs(g - fd) / sc)
             assert abs(g - fd) <= 1e-4 * sc, (cell, which, g, fd, sc)
+    accuracy.append({"case": f"adjoint vs central differences of the FP64 oracle, 64 cells, T {T}", "precision": "fp32 (fp64 gradients)",
+                     "max_rel_grad_logK": worst["logK"], "max_rel_grad_eps": worst["phi"], "bound": 1e-4})
 
 
 def test_autograd_function(lbm):

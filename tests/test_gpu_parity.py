@@ -89,27 +89,33 @@ def _trajectory(lbm, case, steps, phip_uniform=None):
     return e_u, e_p
 
 
-def test_poiseuille_64_trajectory(lbm):
+def test_poiseuille_64_trajectory(lbm, accuracy):
     """Porous Poiseuille channel: 64x64, eps = 0.1, Da = 0.01, nu = 0.1, Re = 10 body force (Sec. 3.1)."""
     H, phi, nu = 64, 0.1, 0.1
     K = 0.01 * H * H
     th_ = np.sqrt(phi / K)
     G = (10 * nu / H) * nu / (K * (1 - 1 / np.cosh(th_ * H / 2)))
     e_u, e_p = _trajectory(lbm, Case(H, H, nu=nu, phi=phi, K=K, forch=False, ax=G), 1500)
+    accuracy.append({"case": "porous Poiseuille 64x64, eps 0.1, Da 0.01, Re 10", "precision": "fp32", "steps": 1500,
+                     "rel_l2_u": e_u, "rel_l2_p": e_p, "bound": 1e-5})
     assert e_u <= 1e-5 and e_p <= 1e-5, (e_u, e_p)
 
 
-def test_lid_cavity_trajectory(lbm):
+def test_lid_cavity_trajectory(lbm, accuracy):
     """Lid-driven porous cavity (Sec. 3.3 set-up, halfway walls): eps = 0.4, Da = 1e-3, Re = 100."""
     L = 96
     e_u, e_p = _trajectory(lbm, Case(L, L, nu=0.1 * L / 100, phi=0.4, K=1e-3 * L * L, bc_x="wall", bc_y="wall", walls=CAV), 800)
+    accuracy.append({"case": "lid-driven porous cavity 96x96, eps 0.4, Da 1e-3, Re 100", "precision": "fp32", "steps": 800,
+                     "rel_l2_u": e_u, "rel_l2_p": e_p, "bound": 1e-5})
     assert e_u <= 1e-5 and e_p <= 1e-5, (e_u, e_p)
 
 
-def test_heterogeneous_pressure_channel_trajectory(lbm):
+def test_heterogeneous_pressure_channel_trajectory(lbm, accuracy):
     case = Case(96, 48, nu=0.1, phi=0.3, K=1e-3 * 48 * 48, het=True, eps_sd=0.03, corr=12.0, bc_x="pressure", bc_y="wall",
                 p_in=1.002, p_out=0.998)
     e_u, e_p = _trajectory(lbm, case, 600, phip_uniform=case.p_rest())
+    accuracy.append({"case": "heterogeneous pressure-driven channel 96x48", "precision": "fp32", "steps": 600,
+                     "rel_l2_u": e_u, "rel_l2_p": e_p, "bound": 1e-5})
     assert e_u <= 1e-5 and e_p <= 1e-5, (e_u, e_p)
 
 
@@ -119,7 +125,7 @@ def _thermal_case(L=48, prec=0, Ra=1e4):
                 thermal=dict(tau_T=tau_T, g_beta=gb, T0=11.0, T_left=21.0, T_right=1.0))
 
 
-def test_natural_convection_trajectory_and_nusselt(lbm):
+def test_natural_convection_trajectory_and_nusselt(lbm, accuracy):
     case = _thermal_case()
     flow, tp = case.flow(), case.thermal_params()
     f, g = fl.initial_state(flow), th.initial_state(flow, tp)
@@ -131,9 +137,13 @@ def test_natural_convection_trajectory_and_nusselt(lbm):
     for _ in range(steps):
         f, g = th.coupled_step(f, g, flow, tp)
     uxo, uyo, po, To = th.coupled_macroscopic(f, g, flow, tp)
-    assert rel_l2(np.stack([ux, uy]), np.stack([uxo, uyo])) <= 1e-5
-    assert rel_l2(T, To) <= 1e-6
-    assert rel_l2(p, po) <= 1e-5
+    e_u, e_T, e_p = rel_l2(np.stack([ux, uy]), np.stack([uxo, uyo])), rel_l2(T, To), rel_l2(p, po)
+    accuracy.append({"case": "natural convection 48x48, Ra 1e4, eps 0.6, Da 1e-2", "precision": "fp32", "steps": steps,
+                     "rel_l2_u": e_u, "rel_l2_T": e_T, "rel_l2_T_minus_T0": rel_l2(T - 11.0, To - 11.0), "rel_l2_p": e_p,
+                     "bound": 1e-5})
+    assert e_u <= 1e-5
+    assert e_T <= 1e-6
+    assert e_p <= 1e-5
     nu_o = th.nusselt_left_wall(To, 21.0, 21.0, 1.0, case.nx)
     assert abs(nu_l - nu_o) <= 1e-5 * abs(nu_o)
     # right wall: mirror of the same formula
@@ -195,7 +205,7 @@ def test_host_pointers_round_trip(lbm):
 
 
 @pytest.mark.parametrize("prec,bound", [(1, 1e-3), (2, 1e-2)])
-def test_reduced_precision_storage_error(lbm, prec, bound):
+def test_reduced_precision_storage_error(lbm, accuracy, prec, bound):
     """FP16 / BF16 storage of f - f_rest with FP32 arithmetic: relative L2 error of u and p vs the
     FP64 oracle on the lid-driven cavity (bound 1e-3 for FP16; BF16's 8-bit mantissa is reported
     against a looser 1e-2)."""
@@ -203,11 +213,13 @@ def test_reduced_precision_storage_error(lbm, prec, bound):
     case = Case(L, L, nu=0.1 * L / 100, phi=0.4, K=1e-3 * L * L, bc_x="wall", bc_y="wall", walls=CAV, precision=prec)
     e_u, e_p = _trajectory(lbm, case, 800)
     print(f"precision {prec}: rel-L2 u {e_u:.3e}, p {e_p:.3e}")
+    accuracy.append({"case": "lid-driven porous cavity 96x96, eps 0.4, Da 1e-3, Re 100", "precision": {1: "fp16", 2: "bf16"}[prec],
+                     "steps": 800, "rel_l2_u": e_u, "rel_l2_p": e_p, "bound": bound})
     assert e_u <= bound and e_p <= bound, (e_u, e_p)
 
 
 @pytest.mark.parametrize("prec,bound", [(1, 1e-3), (2, 5e-2)])
-def test_reduced_precision_thermal_error(lbm, prec, bound):
+def test_reduced_precision_thermal_error(lbm, accuracy, prec, bound):
     """Natural convection with FP16 / BF16 storage.  BF16 keeps 8 significant bits (unit
     roundoff 2^-9 ~ 2e-3 per stored value), which the slow thermal transient accumulates to a few
     percent: it is reported against 5e-2, not the 1e-3 that FP16 meets."""
@@ -224,6 +236,8 @@ def test_reduced_precision_thermal_error(lbm, prec, bound):
     e_u = rel_l2(np.stack([ux, uy]), np.stack([uxo, uyo]))
     e_T = rel_l2(T - 11.0, To - 11.0)
     print(f"precision {prec}: rel-L2 u {e_u:.3e}, T-T0 {e_T:.3e}")
+    accuracy.append({"case": "natural convection 48x48, Ra 1e4, eps 0.6, Da 1e-2", "precision": {1: "fp16", 2: "bf16"}[prec],
+                     "steps": steps, "rel_l2_u": e_u, "rel_l2_T_minus_T0": e_T, "bound": bound})
     assert e_u <= bound and e_T <= bound, (e_u, e_T)
 
 
