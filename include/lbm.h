@@ -188,13 +188,20 @@ LBM_API int lbm_residual_noalloc(const float* ux, const float* uy, const float* 
  * contexts): runs the T steps -- the context ends at step T, as after lbm_step(ctx, T) -- and
  * returns the loss and its gradient with respect to the per-cell log K and eps (phi) fields,
  * including their effect on the initial equilibrium (Eq. 22).  Memory: checkpoints of the
- * post-collision state every ceil(sqrt(T)) steps plus one segment of ceil(sqrt(T)) states are
- * allocated for the call and freed before it returns; the forward work is about 2 T steps.
+ * post-collision state every ceil(sqrt(T)) steps, one segment of ceil(sqrt(T)) states, two FP32
+ * adjoint states and the gradient sums (FP32 partial sums over at most 64 steps, folded into FP64
+ * totals) form a workspace that stays allocated after the call, so that repeated calls (an
+ * optimisation loop) allocate nothing; it is counted by lbm_memory_bytes and freed by
+ * lbm_release_workspace or lbm_destroy.  The forward work is about 2 T steps.
  *   target_ux, target_uy: float32 [ny][nx] (misfit loss only; host or device).
  *   grad_logK, grad_eps: double [ny][nx] outputs (host or device; NULL skips); loss: double.
  * Waits for the stream. */
 LBM_API int lbm_adjoint(lbm_ctx* ctx, int T, int loss_kind, const float* target_ux, const float* target_uy, double* grad_logK,
                         double* grad_eps, double* loss);
+
+/* Frees the workspace that lbm_adjoint keeps between calls (no-op if there is none); the next
+ * lbm_adjoint allocates it again.  Waits for the stream.  Not in the paper: memory management. */
+LBM_API int lbm_release_workspace(lbm_ctx* ctx);
 
 /* Average Nusselt number of a wall with a prescribed temperature (side = LBM_LEFT or
  * LBM_RIGHT): Nu = (nx / (T_hot - T_cold)) * mean_y(-+ dT/dx at the wall), dT/dx from the

@@ -16,7 +16,8 @@
 // theta enters through phi (Eq. 3, 11, 16, 19, 20 and F_phi of Eq. 4) and K (Eq. 3, 19); with
 // c_lin = phi nu / K and c_nl = phi F_phi / sqrt(K) = 1.75 / sqrt(150 phi K):
 //   dc_lin/dl = -c_lin, dc_lin/dphi = c_lin / phi, dc_nl/dl = -c_nl / 2, dc_nl/dphi = -c_nl / (2 phi).
-// Gradients accumulate in FP64; the adjoint state is stored in FP32 planes [8][ny][pitch].
+// Per-step gradient terms are summed in FP32 over at most kAdjFold steps and then folded into FP64
+// totals (k_adj_fold); the adjoint state is stored in FP32 planes [8][ny][pitch].
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
 #include "tiles.cuh"
@@ -61,16 +62,15 @@ __device__ __forceinline__ VelBar velocity_vjp(float jx, float jy, const Coef& c
 }
 
 // theta-gradients from the adjoints of c_lin, c_nl, 1/phi and phi itself.
-__device__ __forceinline__ void theta_bar(const Coef& c, float clin_bar, float cnl_bar, float iphi_bar, float phi_bar, double& g_l,
-                                          double& g_phi) {
-  g_l += (double)(-c.c_lin * clin_bar - 0.5f * c.c_nl * cnl_bar);
-  g_phi += (double)(phi_bar - c.inv_phi * c.inv_phi * iphi_bar + c.c_lin * c.inv_phi * clin_bar -
-                    0.5f * c.c_nl * c.inv_phi * cnl_bar);
+__device__ __forceinline__ void theta_bar(const Coef& c, float clin_bar, float cnl_bar, float iphi_bar, float phi_bar, float& g_l,
+                                          float& g_phi) {
+  g_l += -c.c_lin * clin_bar - 0.5f * c.c_nl * cnl_bar;
+  g_phi += phi_bar - c.inv_phi * c.inv_phi * iphi_bar + c.c_lin * c.inv_phi * clin_bar - 0.5f * c.c_nl * c.inv_phi * cnl_bar;
 }
 
 // nu = J_C(z)^T mu and the theta-gradient (dC/dtheta)^T mu of one cell.
 __device__ void collide_vjp(const float z[8], const Coef& c, float ax, float ay, const StepParams& P, const float mu[8], float nu[8],
-                            double& g_l, double& g_phi) {
+                            float& g_l, float& g_phi) {
   const float rho0 = P.rho0;
   // forward quantities (as collide_d2q8)
   const float a13 = z[0] + z[2], a24 = z[1] + z[3];
@@ -181,8 +181,8 @@ __device__ __forceinline__ void gather_z(const StepParams& P, const void* buf, i
 struct AdjArgs {
   const float* nu_in;  // nu(t+1) after J_N^T (planes [8][ny][pitch])
   float* nu_out;       // nu(t)
-  double* g_l;         // dL/dlog K  [ny][pitch]
-  double* g_phi;       // dL/dphi    [ny][pitch]
+  float* g_l;          // dL/dlog K  [ny][pitch], FP32 partial sums (folded into FP64 by k_adj_fold)
+  float* g_phi;        // dL/dphi    [ny][pitch], likewise
 };
 
 // Seed: nu(T) = dL/dz(T) and the explicit theta-gradient of the loss; per-block loss partials.
@@ -214,7 +214,7 @@ __global__ void k_adj_seed(const StepParams P, AdjArgs A, int kind, const float*
       uby = ey;
     }
     float nu[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    double gl = 0.0, gp = 0.0;
+    float gl = 0.0f, gp = 0.0f;
     if (ubx != 0.0f || uby != 0.0f) {
       const VelBar vb = velocity_vjp(jx, jy, c, P.ax, P.ay, P.inv_rho0, ubx, uby, 0.0f);
 #pragma unroll
@@ -248,50 +248,50 @@ __global__ void k_adj_loss_total(const double* __restrict__ partial, int nblocks
   }
 }
 
-// J_N^T in place on nu: one thread per row and pressure column; when nx = 3 both columns share
-// their neighbour column, and one thread per row does both in turn.  z(nb) is gathered from
-// `buf`, the post-collision buffer whose gather is the state at which N was applied.
+// J_N^T in place on nu: eight lanes per row and pressure column, lane i holding population i
+// (sums over i are reductions within the lane group); when nx < 4 both columns share their
+// neighbour column, and one group per row does both in turn.  z(nb) is gathered from `buf`, the
+// post-collision buffer whose gather is the state at which N was applied.
+__device__ __forceinline__ float group8_sum(float v, unsigned mask) {
+  v += __shfl_xor_sync(mask, v, 1);
+  v += __shfl_xor_sync(mask, v, 2);
+  v += __shfl_xor_sync(mask, v, 4);
+  return v;
+}
+
 template <int PREC, bool HET>
-__global__ void k_adj_nee(const StepParams P, const void* buf, float* __restrict__ nu, double* __restrict__ g_l,
-                          double* __restrict__ g_phi) {
+__global__ void k_adj_nee(const StepParams P, const void* buf, float* __restrict__ nu, float* __restrict__ g_l,
+                          float* __restrict__ g_phi) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int grp = t >> 3, i = t & 7;
   const bool shared_nb = P.nx < 4;
-  const int y = shared_nb ? t : t >> 1;
-  if (y >= P.ny) return;
+  const int y = shared_nb ? grp : grp >> 1;
+  if (y >= P.ny) return;  // whole lane groups leave together
+  const unsigned gm = 0xffu << (threadIdx.x & 24);
   using T = typename Store<PREC>::T;
-  const int s0 = shared_nb ? 0 : (t & 1), s1 = shared_nb ? 2 : s0 + 1;
+  const float ex = (float)ex_of(i), ey = (float)ey_of(i), w = w_of(i);
+  const int s0 = shared_nb ? 0 : (grp & 1), s1 = shared_nb ? 2 : s0 + 1;
   for (int side = s0; side < s1; ++side) {
     const int xb = side ? P.nx - 1 : 0, xn = side ? P.nx - 2 : 1;
     const float pb = side ? P.p_out : P.p_in;
     const int64_t ob = (int64_t)y * P.pitch + xb, on = (int64_t)y * P.pitch + xn;
-    float nb_[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      nb_[i] = nu[i * P.plane + ob];
-      nu[i * P.plane + ob] = 0.0f;
-    }
-    float z[8];
-    pull_cell<PREC>(P, static_cast<const T*>(buf), xn, y, z);
+    const float nbi = nu[i * P.plane + ob];
+    nu[i * P.plane + ob] = 0.0f;
+    const float zi = pull_one<PREC>(P, static_cast<const T*>(buf), xn, y, i);
     const Coef cn = coef_at<HET>(P, xn, y);
     const Coef cb = coef_at<HET>(P, xb, y);
-    const float jx = (z[0] - z[2]) + (z[4] - z[5] - z[6] + z[7]);
-    const float jy = (z[1] - z[3]) + (z[4] + z[5] - z[6] - z[7]);
+    const float jx = group8_sum(ex * zi, gm), jy = group8_sum(ey * zi, gm);
     float ux, uy, umag;
     velocity_from_j(jx, jy, cn, P.ax, P.ay, P.inv_rho0, ux, uy, umag);
     const float usq = ux * ux + uy * uy;
     const float rho0 = P.rho0;
     // N_b,i = z_nb,i + 3 w_i (phi_b p_b - phi_n p_n) + rho0 w_i (4.5 (e_i.u)^2 - 1.5 |u|^2)(1/phi_b - 1/phi_n)
-    float W = 0.f, WA = 0.f, gux = 0.f, guy = 0.f;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const float wi = w_of(i) * nb_[i];
-      const float ex = (float)ex_of(i), ey = (float)ey_of(i);
-      const float eu = ex * ux + ey * uy;
-      W += wi;
-      WA += wi * (4.5f * eu * eu - 1.5f * usq);
-      gux += wi * (9.0f * eu * ex - 3.0f * ux);
-      guy += wi * (9.0f * eu * ey - 3.0f * uy);
-    }
+    const float wi = w * nbi;
+    const float eu = ex * ux + ey * uy;
+    const float W = group8_sum(wi, gm);
+    const float WA = group8_sum(wi * (4.5f * eu * eu - 1.5f * usq), gm);
+    const float gux = group8_sum(wi * (9.0f * eu * ex - 3.0f * ux), gm);
+    const float guy = group8_sum(wi * (9.0f * eu * ey - 3.0f * uy), gm);
     const float diff = cb.inv_phi - cn.inv_phi;
     float ubx = rho0 * diff * gux, uby = rho0 * diff * guy;
     const float Pn_b = -3.0f * W;  // adjoint of phi_n p_n
@@ -303,16 +303,15 @@ __global__ void k_adj_nee(const StepParams P, const void* buf, float* __restrict
     uby += -0.8f * rho0 * uy * cn.inv_phi * Pn_b;
     ipn_b += -0.4f * rho0 * usq * Pn_b;
     const VelBar vb = velocity_vjp(jx, jy, cn, P.ax, P.ay, P.inv_rho0, ubx, uby, 0.0f);
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-      nu[i * P.plane + on] += nb_[i] + mb1 + (float)ex_of(i) * vb.jx + (float)ey_of(i) * vb.jy;
-    const int64_t kb = ob, kn = on;
-    // boundary cell: phi_b p_b and 1/phi_b
-    g_phi[kb] += (double)(3.0f * pb * W - cb.inv_phi * cb.inv_phi * ipb_b);
-    double gl = 0.0, gp = 0.0;
-    theta_bar(cn, vb.clin, vb.cnl, ipn_b, vb.phi, gl, gp);
-    g_l[kn] += gl;
-    g_phi[kn] += gp;
+    nu[i * P.plane + on] += nbi + mb1 + ex * vb.jx + ey * vb.jy;
+    if (i == 0) {
+      // boundary cell: phi_b p_b and 1/phi_b
+      g_phi[ob] += 3.0f * pb * W - cb.inv_phi * cb.inv_phi * ipb_b;
+      float gl = 0.0f, gp = 0.0f;
+      theta_bar(cn, vb.clin, vb.cnl, ipn_b, vb.phi, gl, gp);
+      g_l[on] += gl;
+      g_phi[on] += gp;
+    }
   }
 }
 
@@ -336,7 +335,7 @@ __device__ void adj_cell(const StepParams& P, const void* buf, const AdjArgs& A,
   gather_z<PREC, HET>(P, buf, x, y, z);
   const Coef c = coef_at<HET>(P, x, y);
   float nu[8];
-  double gl = 0.0, gp = 0.0;
+  float gl = 0.0f, gp = 0.0f;
   collide_vjp(z, c, P.ax, P.ay, P, mu, nu, gl, gp);
   const int64_t o = (int64_t)y * P.pitch + x;
 #pragma unroll
@@ -345,25 +344,68 @@ __device__ void adj_cell(const StepParams& P, const void* buf, const AdjArgs& A,
   A.g_phi[o] += gp;
 }
 
-// Work item of the adjoint step (the forward kernel's tiling): frame items do whole frame groups
-// cell by cell; main items gather the forward state forwards and the adjoint state backwards
-// (mu_i(x) = nu~_i(x + e_i)) as aligned vectors with shuffled halos, and skip frame groups.
+// Work split of the adjoint step.  The frame is the forward kernel's (groups of four cells that
+// touch a wall row or the first/last column), done one cell per thread; the rest of the lattice is
+// split into pairs of cells, one pair per thread, which keeps half the forward kernel's live state
+// per thread (the reverse-mode collision holds the forward state, the adjoint state and their
+// partial adjoints) so that more warps stay resident.  Rows of P <= nt pairs are packed
+// rows_per_item = nt / P to a work item, longer rows take gx = ceil(P / nt) items.
+struct AdjTiling {
+  int frame_blocks, pairs, gx, rows_per_item, frame_x1;  // frame_x1: first x of the last frame group
+};
+
+__host__ __device__ inline AdjTiling adj_tiling_of(int nx, int ny, int bc_y, int nt) {
+  AdjTiling t;
+  const Frame F = frame_of(nx, ny, bc_y, kCellsPerThread);
+  t.frame_blocks = (int)(((int64_t)F.count * kCellsPerThread + nt - 1) / nt);
+  t.pairs = (nx + 1) / 2;
+  if (t.pairs <= nt) {
+    t.gx = 1;
+    t.rows_per_item = nt / t.pairs;
+  } else {
+    t.gx = (t.pairs + nt - 1) / nt;
+    t.rows_per_item = 1;
+  }
+  t.frame_x1 = (F.groups_per_row - 1) * kCellsPerThread;
+  return t;
+}
+
+inline int64_t adj_main_items(const AdjTiling& t, int ny) {
+  return t.rows_per_item > 1 ? (int64_t)((ny + t.rows_per_item - 1) / t.rows_per_item) : (int64_t)t.gx * ny;
+}
+
+// Row and first cell of the pair of thread `tid` in main item b; false for a thread with no pair
+// (it takes part in the loads and shuffles on a clamped row and stores nothing).
+__device__ __forceinline__ bool adj_pair(const AdjTiling& t, int ny, int nt, int b, int tid, int& x0, int& y) {
+  if (t.rows_per_item > 1) {
+    const int r = tid / t.pairs;
+    y = b * t.rows_per_item + r;
+    x0 = (tid - r * t.pairs) * 2;
+    const bool ok = r < t.rows_per_item && y < ny;
+    if (!ok) y = ny - 1;
+    return ok;
+  }
+  y = b / t.gx;
+  x0 = ((b - y * t.gx) * nt + tid) * 2;
+  return true;
+}
+
+// Work item of the adjoint step: frame items do the frame cell by cell; main items gather the
+// forward state forwards and the adjoint state backwards (mu_i(x) = nu~_i(x + e_i)) for a pair
+// of cells with shuffled halos, and skip the frame.
 template <int PREC, bool HET, int NT>
-__device__ __forceinline__ void adj_item(const StepParams& P, const void* buf, const AdjArgs& A, const Tiling& tl, int item) {
-  using S = Store<PREC>;
-  using T = typename S::T;
-  using SF = Store<PREC_FP32>;
-  constexpr int C = kCellsPerThread;
+__device__ __forceinline__ void adj_item(const StepParams& P, const void* buf, const AdjArgs& A, const AdjTiling& tl, int item) {
+  using T = typename Store<PREC>::T;
   if (item < tl.frame_blocks) {  // one frame cell per thread
-    const Frame F = frame_of(P.nx, P.ny, P.bc_y, C);
+    const Frame F = frame_of(P.nx, P.ny, P.bc_y, kCellsPerThread);
     int x, y;
     if (frame_cell(F, P.ny, item * NT + (int)threadIdx.x, x, y) && x < P.nx) adj_cell<PREC, HET>(P, buf, A, x, y);
     return;
   }
   int x0, y;
-  const bool has_group = main_group(tl, P.ny, NT, item - tl.frame_blocks, (int)threadIdx.x, x0, y);
+  const bool has_pair = adj_pair(tl, P.ny, NT, item - tl.frame_blocks, (int)threadIdx.x, x0, y);
   const int lane = threadIdx.x & 31;
-  const int xl = x0 < P.pitch - C ? x0 : P.pitch - C;
+  const int xl = x0 < P.pitch - 2 ? x0 : P.pitch - 2;
   int ym = y - 1, yp = y + 1;
   ym = ym < 0 ? P.ny - 1 : ym;
   yp = yp >= P.ny ? 0 : yp;
@@ -371,63 +413,73 @@ __device__ __forceinline__ void adj_item(const StepParams& P, const void* buf, c
   const int64_t rm = (int64_t)ym * P.pitch, r0 = (int64_t)y * P.pitch, rp = (int64_t)yp * P.pitch;
   const T* __restrict__ src = static_cast<const T*>(buf);
   const float inv = P.inv_scale;
+  // medium of the two cells, issued ahead of the state gathers
+  float2 ph2, k2;
+  if (HET) {
+    ph2 = __ldg(reinterpret_cast<const float2*>(P.phi + r0 + xl));
+    k2 = __ldg(reinterpret_cast<const float2*>(P.K + r0 + xl));
+  }
   // forward state z(t): the pull of Eq. 15
-  float z[8][C];
-  gather4<PREC, 1>(src + 0 * pl + r0, xl, P.pitch, lane, inv, z[0]);
-  gather4<PREC, 0>(src + 1 * pl + rm, xl, P.pitch, lane, inv, z[1]);
-  gather4<PREC, -1>(src + 2 * pl + r0, xl, P.pitch, lane, inv, z[2]);
-  gather4<PREC, 0>(src + 3 * pl + rp, xl, P.pitch, lane, inv, z[3]);
-  gather4<PREC, 1>(src + 4 * pl + rm, xl, P.pitch, lane, inv, z[4]);
-  gather4<PREC, -1>(src + 5 * pl + rm, xl, P.pitch, lane, inv, z[5]);
-  gather4<PREC, -1>(src + 6 * pl + rp, xl, P.pitch, lane, inv, z[6]);
-  gather4<PREC, 1>(src + 7 * pl + rp, xl, P.pitch, lane, inv, z[7]);
+  float z[8][2];
+  gather2<PREC, 1>(src + 0 * pl + r0, xl, P.pitch, lane, inv, z[0]);
+  gather2<PREC, 0>(src + 1 * pl + rm, xl, P.pitch, lane, inv, z[1]);
+  gather2<PREC, -1>(src + 2 * pl + r0, xl, P.pitch, lane, inv, z[2]);
+  gather2<PREC, 0>(src + 3 * pl + rp, xl, P.pitch, lane, inv, z[3]);
+  gather2<PREC, 1>(src + 4 * pl + rm, xl, P.pitch, lane, inv, z[4]);
+  gather2<PREC, -1>(src + 5 * pl + rm, xl, P.pitch, lane, inv, z[5]);
+  gather2<PREC, -1>(src + 6 * pl + rp, xl, P.pitch, lane, inv, z[6]);
+  gather2<PREC, 1>(src + 7 * pl + rp, xl, P.pitch, lane, inv, z[7]);
   // adjoint of the pull: mu_i(x) = nu~_i(x + e_i)
   const float* __restrict__ nu_in = A.nu_in;
-  float mu[8][C];
-  gather4<PREC_FP32, -1>(nu_in + 0 * pl + r0, xl, P.pitch, lane, 1.0f, mu[0]);  // e1 = ( 1, 0)
-  gather4<PREC_FP32, 0>(nu_in + 1 * pl + rp, xl, P.pitch, lane, 1.0f, mu[1]);   // e2 = ( 0, 1)
-  gather4<PREC_FP32, 1>(nu_in + 2 * pl + r0, xl, P.pitch, lane, 1.0f, mu[2]);   // e3 = (-1, 0)
-  gather4<PREC_FP32, 0>(nu_in + 3 * pl + rm, xl, P.pitch, lane, 1.0f, mu[3]);   // e4 = ( 0,-1)
-  gather4<PREC_FP32, -1>(nu_in + 4 * pl + rp, xl, P.pitch, lane, 1.0f, mu[4]);  // e5 = ( 1, 1)
-  gather4<PREC_FP32, 1>(nu_in + 5 * pl + rp, xl, P.pitch, lane, 1.0f, mu[5]);   // e6 = (-1, 1)
-  gather4<PREC_FP32, 1>(nu_in + 6 * pl + rm, xl, P.pitch, lane, 1.0f, mu[6]);   // e7 = (-1,-1)
-  gather4<PREC_FP32, -1>(nu_in + 7 * pl + rm, xl, P.pitch, lane, 1.0f, mu[7]);  // e8 = ( 1,-1)
+  float mu[8][2];
+  gather2<PREC_FP32, -1>(nu_in + 0 * pl + r0, xl, P.pitch, lane, 1.0f, mu[0]);  // e1 = ( 1, 0)
+  gather2<PREC_FP32, 0>(nu_in + 1 * pl + rp, xl, P.pitch, lane, 1.0f, mu[1]);   // e2 = ( 0, 1)
+  gather2<PREC_FP32, 1>(nu_in + 2 * pl + r0, xl, P.pitch, lane, 1.0f, mu[2]);   // e3 = (-1, 0)
+  gather2<PREC_FP32, 0>(nu_in + 3 * pl + rm, xl, P.pitch, lane, 1.0f, mu[3]);   // e4 = ( 0,-1)
+  gather2<PREC_FP32, -1>(nu_in + 4 * pl + rp, xl, P.pitch, lane, 1.0f, mu[4]);  // e5 = ( 1, 1)
+  gather2<PREC_FP32, 1>(nu_in + 5 * pl + rp, xl, P.pitch, lane, 1.0f, mu[5]);   // e6 = (-1, 1)
+  gather2<PREC_FP32, 1>(nu_in + 6 * pl + rm, xl, P.pitch, lane, 1.0f, mu[6]);   // e7 = (-1,-1)
+  gather2<PREC_FP32, -1>(nu_in + 7 * pl + rm, xl, P.pitch, lane, 1.0f, mu[7]);  // e8 = ( 1,-1)
   const bool wall_row = P.bc_y == BC_WALL && (y == 0 || y == P.ny - 1);
-  if (!has_group || wall_row || x0 == 0 || x0 + C >= P.nx) return;
-  double gl[C], gp[C];
+  if (!has_pair || wall_row || x0 < kCellsPerThread || x0 >= tl.frame_x1) return;
+  float gl[2], gp[2];
 #pragma unroll
-  for (int c = 0; c < C; ++c) {
+  for (int c = 0; c < 2; ++c) {
     float zc[8], mc[8], nc[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       zc[i] = z[i][c];
       mc[i] = mu[i][c];
     }
-    const Coef cf = coef_at<HET>(P, x0 + c, y);
-    gl[c] = 0.0;
-    gp[c] = 0.0;
+    const Coef cf = HET ? coef_of(P, c ? ph2.y : ph2.x, c ? k2.y : k2.x, P.sv ? __ldg(P.sv + r0 + x0 + c) : P.s_v) : coef_uniform(P);
+    gl[c] = 0.0f;
+    gp[c] = 0.0f;
     collide_vjp(zc, cf, P.ax, P.ay, P, mc, nc, gl[c], gp[c]);
 #pragma unroll
     for (int i = 0; i < 8; ++i) z[i][c] = nc[i];
   }
 #pragma unroll
-  for (int i = 0; i < 8; ++i) SF::store4(A.nu_out + i * pl + r0 + x0, z[i], 1.0f);
-  double2* g2l = reinterpret_cast<double2*>(A.g_l + r0 + x0);
-  double2* g2p = reinterpret_cast<double2*>(A.g_phi + r0 + x0);
-  double2 a0 = g2l[0], a1 = g2l[1], b0 = g2p[0], b1 = g2p[1];
-  a0.x += gl[0]; a0.y += gl[1]; a1.x += gl[2]; a1.y += gl[3];
-  b0.x += gp[0]; b0.y += gp[1]; b1.x += gp[2]; b1.y += gp[3];
-  g2l[0] = a0; g2l[1] = a1; g2p[0] = b0; g2p[1] = b1;
+  for (int i = 0; i < 8; ++i) *reinterpret_cast<float2*>(A.nu_out + i * pl + r0 + x0) = make_float2(z[i][0], z[i][1]);
+  float2* g2l = reinterpret_cast<float2*>(A.g_l + r0 + x0);
+  float2* g2p = reinterpret_cast<float2*>(A.g_phi + r0 + x0);
+  float2 a = *g2l, b = *g2p;
+  a.x += gl[0]; a.y += gl[1];
+  b.x += gp[0]; b.y += gp[1];
+  *g2l = a;
+  *g2p = b;
 }
 
+#ifndef LBM_ADJ_MIN_CTAS
+#define LBM_ADJ_MIN_CTAS 7
+#endif
 template <int PREC, bool HET>
-__global__ void __launch_bounds__(kStepThreads, 5) k_adj_step(const StepParams P, const void* buf, AdjArgs A, Tiling tl) {
+__global__ void __launch_bounds__(kStepThreads, LBM_ADJ_MIN_CTAS) k_adj_step(const StepParams P, const void* buf, AdjArgs A, AdjTiling tl) {
   adj_item<PREC, HET, kStepThreads>(P, buf, A, tl, blockIdx.x);
 }
 
 // Initial state: z(0) = f_eq(p0, u0; phi) (Eq. 22): dL/dphi += sum_i nu_i d f_eq,i / d phi.
 template <bool HET>
-__global__ void k_adj_init(const StepParams P, const float* __restrict__ nu, double* __restrict__ g_phi, float p0, float ux0, float uy0,
+__global__ void k_adj_init(const StepParams P, const float* __restrict__ nu, float* __restrict__ g_phi, float p0, float ux0, float uy0,
                            int phip_uniform) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y;
@@ -442,7 +494,19 @@ __global__ void k_adj_init(const StepParams P, const float* __restrict__ nu, dou
     const float d = w_of(i) * (pterm - P.rho0 * (4.5f * eu * eu - 1.5f * usq) * c.inv_phi * c.inv_phi);
     s += d * nu[i * P.plane + (int64_t)y * P.pitch + x];
   }
-  g_phi[(int64_t)y * P.pitch + x] += (double)s;
+  g_phi[(int64_t)y * P.pitch + x] += s;
+}
+
+// FP32 partial sums of the gradients into the FP64 totals, and the partial sums reset: run every
+// few dozen steps, so that each FP32 sum holds a bounded number of per-step terms.
+__global__ void k_adj_fold(float* __restrict__ l32, float* __restrict__ p32, double* __restrict__ l64, double* __restrict__ p64,
+                           int64_t n) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    l64[k] += (double)l32[k];
+    p64[k] += (double)p32[k];
+    l32[k] = 0.0f;
+    p32[k] = 0.0f;
+  }
 }
 
 // --------------------------------------------------------------------------------------------
@@ -455,7 +519,7 @@ __global__ void k_adj_init(const StepParams P, const float* __restrict__ nu, dou
     else { if (het) { CALL(PREC_BF16, true); } else { CALL(PREC_BF16, false); } } \
   } while (0)
 
-cudaError_t launch_adj_seed(const StepParams& P, int prec, bool het, float* nu_out, double* g_l, double* g_phi, int kind,
+cudaError_t launch_adj_seed(const StepParams& P, int prec, bool het, float* nu_out, float* g_l, float* g_phi, int kind,
                             const float* tux, const float* tuy, double* partial, int nblocks, double* loss_out, cudaStream_t s) {
   AdjArgs A{nullptr, nu_out, g_l, g_phi};
 #define CALL_SEED(PR, H) k_adj_seed<PR, H><<<nblocks, 256, 0, s>>>(P, A, kind, tux, tuy, partial)
@@ -465,34 +529,39 @@ cudaError_t launch_adj_seed(const StepParams& P, int prec, bool het, float* nu_o
   return cudaGetLastError();
 }
 
-cudaError_t launch_adj_nee(const StepParams& P, int prec, bool het, const void* buf, float* nu, double* g_l, double* g_phi,
+cudaError_t launch_adj_nee(const StepParams& P, int prec, bool het, const void* buf, float* nu, float* g_l, float* g_phi,
                            cudaStream_t s) {
-  const int threads = P.nx < 4 ? P.ny : 2 * P.ny;
-  const int blocks = (threads + 63) / 64;
-#define CALL_NEE(PR, H) k_adj_nee<PR, H><<<blocks, 64, 0, s>>>(P, buf, nu, g_l, g_phi)
+  const int threads = 8 * (P.nx < 4 ? P.ny : 2 * P.ny);
+  const int blocks = (threads + 127) / 128;
+#define CALL_NEE(PR, H) k_adj_nee<PR, H><<<blocks, 128, 0, s>>>(P, buf, nu, g_l, g_phi)
   LBM_ADJ_DISPATCH(prec, het, CALL_NEE);
 #undef CALL_NEE
   return cudaGetLastError();
 }
 
-cudaError_t launch_adj_step(const StepParams& P, int prec, bool het, const void* buf, const float* nu_in, float* nu_out, double* g_l,
-                            double* g_phi, cudaStream_t s) {
+cudaError_t launch_adj_step(const StepParams& P, int prec, bool het, const void* buf, const float* nu_in, float* nu_out, float* g_l,
+                            float* g_phi, cudaStream_t s) {
   AdjArgs A{nu_in, nu_out, g_l, g_phi};
-  const Tiling tl = tiling_of(P.nx, P.ny, P.bc_y, kStepThreads);
-  const unsigned blocks = (unsigned)((long long)tl.frame_blocks + main_items(tl, P.ny));
+  const AdjTiling tl = adj_tiling_of(P.nx, P.ny, P.bc_y, kStepThreads);
+  const unsigned blocks = (unsigned)((long long)tl.frame_blocks + adj_main_items(tl, P.ny));
 #define CALL_ADJ(PR, H) k_adj_step<PR, H><<<blocks, kStepThreads, 0, s>>>(P, buf, A, tl)
   LBM_ADJ_DISPATCH(prec, het, CALL_ADJ);
 #undef CALL_ADJ
   return cudaGetLastError();
 }
 
-cudaError_t launch_adj_init(const StepParams& P, bool het, const float* nu, double* g_phi, float p0, float ux0, float uy0,
+cudaError_t launch_adj_init(const StepParams& P, bool het, const float* nu, float* g_phi, float p0, float ux0, float uy0,
                             int phip_uniform, cudaStream_t s) {
   dim3 grid((P.nx + 127) / 128, P.ny);
   if (het)
     k_adj_init<true><<<grid, 128, 0, s>>>(P, nu, g_phi, p0, ux0, uy0, phip_uniform);
   else
     k_adj_init<false><<<grid, 128, 0, s>>>(P, nu, g_phi, p0, ux0, uy0, phip_uniform);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_fold(float* l32, float* p32, double* l64, double* p64, int64_t n, cudaStream_t s) {
+  k_adj_fold<<<1216, 256, 0, s>>>(l32, p32, l64, p64, n);
   return cudaGetLastError();
 }
 

@@ -132,6 +132,8 @@ struct lbm_ctx {
   float* phi = nullptr;
   float* K = nullptr;
   float* sv = nullptr;  // per-cell viscous rate (heterogeneous mode), when a viscosity-ratio field is set
+  std::vector<void*> ws;       // adjoint workspace, kept between lbm_adjoint calls (slots, see lbm_adjoint)
+  std::vector<size_t> ws_bytes;
   bool het = false;
   unsigned int* err = nullptr;   // device error word
   float* walls = nullptr;        // wall velocities [4][2] read by the kernels
@@ -346,6 +348,7 @@ void release(lbm_ctx* c) {
   cudaFree(c->probe);
   cudaFree(c->red);
   cudaFree(c->stage);
+  for (void* p : c->ws) cudaFree(p);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -731,18 +734,40 @@ int lbm_nusselt(lbm_ctx* c, int side, double* nu) {
 namespace {
 
 // Device buffers of one adjoint run, freed on every exit path.
-struct AdjointBuffers {
-  std::vector<void*> ptrs;
-  ~AdjointBuffers() {
-    for (void* p : ptrs) cudaFree(p);
+// Slot k of the adjoint workspace, `bytes` long: the buffer kept from an earlier call when its
+// size matches, else a new allocation.  Callers synchronise before the workspace changes hands.
+void* ws_slot(lbm_ctx* c, size_t k, size_t bytes, int* rc, const char* what) {
+  if (c->ws.size() <= k) {
+    c->ws.resize(k + 1, nullptr);
+    c->ws_bytes.resize(k + 1, 0);
   }
-  void* get(size_t bytes, cudaError_t* e) {
-    void* p = nullptr;
-    *e = cudaMalloc(&p, bytes);
-    if (*e == cudaSuccess) ptrs.push_back(p);
-    return p;
+  if (c->ws[k] && c->ws_bytes[k] == bytes) return c->ws[k];
+  if (c->ws[k]) {
+    cudaFree(c->ws[k]);
+    c->bytes -= c->ws_bytes[k];
+    c->ws[k] = nullptr;
+    c->ws_bytes[k] = 0;
   }
-};
+  void* p = nullptr;
+  if ((*rc = dev_alloc(c, &p, bytes, what)) != LBM_OK) return nullptr;
+  c->ws[k] = p;
+  c->ws_bytes[k] = bytes;
+  return p;
+}
+
+// Frees the workspace slots from `keep` on.
+void ws_trim(lbm_ctx* c, size_t keep) {
+  for (size_t k = keep; k < c->ws.size(); ++k) {
+    if (c->ws[k]) {
+      cudaFree(c->ws[k]);
+      c->bytes -= c->ws_bytes[k];
+    }
+  }
+  if (c->ws.size() > keep) {
+    c->ws.resize(keep);
+    c->ws_bytes.resize(keep);
+  }
+}
 
 int copy_out(lbm_ctx* c, void* user, const void* dev, size_t bytes, bool* waited) {
   if (!user) return LBM_OK;
@@ -782,30 +807,37 @@ int lbm_adjoint(lbm_ctx* c, int T, int loss_kind, const float* target_ux, const 
   int ck = 1;
   while ((int64_t)ck * ck < T) ++ck;  // checkpoint interval ceil(sqrt(T))
   const int nck = (T + ck - 1) / ck;
-  AdjointBuffers mem;
-  cudaError_t e = cudaSuccess;
+  // workspace slots (kept between calls): 0-1 adjoint state, 2-3 FP64 gradient totals, 4-5 FP32
+  // gradient partial sums, then nck checkpoints and ck segment states
+  LBM_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
+  int rc = LBM_OK;
   float* nu[2];
   for (int b = 0; b < 2; ++b)
-    if (!(nu[b] = static_cast<float*>(mem.get(nubytes, &e)))) return cuda_fail(e, "cudaMalloc(adjoint state)");
+    if (!(nu[b] = static_cast<float*>(ws_slot(c, b, nubytes, &rc, "cudaMalloc(adjoint state)")))) return rc;
   const size_t gbytes = (size_t)c->plane * sizeof(double);  // pitched [ny][pitch]
-  double* gl = static_cast<double*>(mem.get(gbytes, &e));
-  double* gp = gl ? static_cast<double*>(mem.get(gbytes, &e)) : nullptr;
-  if (!gp) return cuda_fail(e, "cudaMalloc(gradients)");
-  for (int b = 0; b < 2; ++b) LBM_CUDA(cudaMemsetAsync(nu[b], 0, nubytes, c->stream), "cudaMemset");
+  const size_t hbytes = (size_t)c->plane * sizeof(float);
+  double* gl = static_cast<double*>(ws_slot(c, 2, gbytes, &rc, "cudaMalloc(gradients)"));
+  double* gp = gl ? static_cast<double*>(ws_slot(c, 3, gbytes, &rc, "cudaMalloc(gradients)")) : nullptr;
+  float* hl = gp ? static_cast<float*>(ws_slot(c, 4, hbytes, &rc, "cudaMalloc(gradient partial sums)")) : nullptr;
+  float* hp = hl ? static_cast<float*>(ws_slot(c, 5, hbytes, &rc, "cudaMalloc(gradient partial sums)")) : nullptr;
+  if (!hp) return rc;
   std::vector<void*> ckpt(nck), seg(ck);
   for (int k = 0; k < nck; ++k)
-    if (!(ckpt[k] = mem.get(fbytes, &e))) return cuda_fail(e, "cudaMalloc(checkpoints)");
+    if (!(ckpt[k] = ws_slot(c, 6 + k, fbytes, &rc, "cudaMalloc(checkpoints)"))) return rc;
   for (int j = 0; j < ck; ++j)
-    if (!(seg[j] = mem.get(fbytes, &e))) return cuda_fail(e, "cudaMalloc(segment states)");
+    if (!(seg[j] = ws_slot(c, 6 + nck + j, fbytes, &rc, "cudaMalloc(segment states)"))) return rc;
+  ws_trim(c, 6 + nck + ck);
+  for (int b = 0; b < 2; ++b) LBM_CUDA(cudaMemsetAsync(nu[b], 0, nubytes, c->stream), "cudaMemset");
   const float *tux = nullptr, *tuy = nullptr;
   if (loss_kind == LBM_LOSS_VELOCITY_MISFIT) {
     const void* ptrs[2] = {target_ux, target_uy};
-    int rc;
     if (any_host(c, ptrs, 2) && (rc = ensure_stage(c, 2 * n * sizeof(float)))) return rc;
     if ((rc = input_ptr(c, target_ux, n, 0, &tux)) || (rc = input_ptr(c, target_uy, n, n, &tuy))) return rc;
   }
   LBM_CUDA(cudaMemsetAsync(gl, 0, gbytes, c->stream), "cudaMemset");
   LBM_CUDA(cudaMemsetAsync(gp, 0, gbytes, c->stream), "cudaMemset");
+  LBM_CUDA(cudaMemsetAsync(hl, 0, hbytes, c->stream), "cudaMemset");
+  LBM_CUDA(cudaMemsetAsync(hp, 0, hbytes, c->stream), "cudaMemset");
   const bool pressure = c->cfg.bc_x == LBM_PRESSURE;
   // forward sweep, keeping the buffer before every ck-th step
   for (int t = 0; t < T; ++t) {
@@ -819,9 +851,10 @@ int lbm_adjoint(lbm_ctx* c, int T, int loss_kind, const float* target_ux, const 
   StepParams P = params_at(c, c->cur);
   const int nb = residual_blocks((int)c->cfg.nx, (int)c->cfg.ny);
   double* loss_dev = c->red + 2 * kResidualMaxBlocks;
-  LBM_CUDA(launch_adj_seed(P, c->prec, c->het, nu[0], gl, gp, loss_kind, tux, tuy, c->red, nb, loss_dev, c->stream), "adjoint seed");
-  if (pressure) LBM_CUDA(launch_adj_nee(P, c->prec, c->het, c->f[c->cur], nu[0], gl, gp, c->stream), "adjoint pressure columns");
-  int cur_nu = 0;
+  LBM_CUDA(launch_adj_seed(P, c->prec, c->het, nu[0], hl, hp, loss_kind, tux, tuy, c->red, nb, loss_dev, c->stream), "adjoint seed");
+  if (pressure) LBM_CUDA(launch_adj_nee(P, c->prec, c->het, c->f[c->cur], nu[0], hl, hp, c->stream), "adjoint pressure columns");
+  int cur_nu = 0, unfolded = 1;
+  constexpr int kAdjFold = 64;  // at most this many per-step terms in an FP32 partial sum
   for (int k = nck - 1; k >= 0; --k) {
     const int t0 = k * ck, t1 = (t0 + ck < T) ? t0 + ck : T;
     LBM_CUDA(cudaMemcpyAsync(seg[0], ckpt[k], fbytes, cudaMemcpyDeviceToDevice, c->stream), "checkpoint restore");
@@ -833,20 +866,31 @@ int lbm_adjoint(lbm_ctx* c, int T, int loss_kind, const float* target_ux, const 
     }
     for (int t = t1 - 1; t >= t0; --t) {
       const void* buf = seg[t - t0];
-      LBM_CUDA(launch_adj_step(P, c->prec, c->het, buf, nu[cur_nu], nu[cur_nu ^ 1], gl, gp, c->stream), "adjoint step");
+      LBM_CUDA(launch_adj_step(P, c->prec, c->het, buf, nu[cur_nu], nu[cur_nu ^ 1], hl, hp, c->stream), "adjoint step");
       cur_nu ^= 1;
-      if (pressure) LBM_CUDA(launch_adj_nee(P, c->prec, c->het, buf, nu[cur_nu], gl, gp, c->stream), "adjoint pressure columns");
+      if (pressure) LBM_CUDA(launch_adj_nee(P, c->prec, c->het, buf, nu[cur_nu], hl, hp, c->stream), "adjoint pressure columns");
+      if (++unfolded == kAdjFold) {
+        LBM_CUDA(launch_adj_fold(hl, hp, gl, gp, c->plane, c->stream), "gradient fold");
+        unfolded = 0;
+      }
     }
   }
-  LBM_CUDA(launch_adj_init(P, c->het, nu[cur_nu], gp, (float)c->init_p0, (float)c->init_ux, (float)c->init_uy, c->init_phip, c->stream),
+  LBM_CUDA(launch_adj_init(P, c->het, nu[cur_nu], hp, (float)c->init_p0, (float)c->init_ux, (float)c->init_uy, c->init_phip, c->stream),
            "adjoint initial state");
+  LBM_CUDA(launch_adj_fold(hl, hp, gl, gp, c->plane, c->stream), "gradient fold");
   bool waited = false;
-  int rc;
   if ((rc = copy_out_rows(c, grad_logK, gl, &waited)) || (rc = copy_out_rows(c, grad_eps, gp, &waited)) ||
       (rc = copy_out(c, loss, loss_dev, sizeof(double), &waited)))
     return rc;
-  LBM_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");  // the temporaries are freed on return
+  LBM_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");  // the workspace may be reused or freed after return
   return check_error_word(c);
+}
+
+int lbm_release_workspace(lbm_ctx* c) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  LBM_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
+  ws_trim(c, 0);
+  return LBM_OK;
 }
 
 namespace {

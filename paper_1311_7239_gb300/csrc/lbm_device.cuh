@@ -84,6 +84,10 @@ template <> struct Store<PREC_FP32> {
   __device__ static __forceinline__ void load4r(const T* p, float o[4]) { load4(p, o, 1.0f); }
   __device__ static __forceinline__ void store4r(T* p, const float o[4]) { store4(p, o, 1.0f); }
   __device__ static __forceinline__ void store2r(T* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
+  __device__ static __forceinline__ void load2(const T* p, float o[2], float) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    o[0] = v.x; o[1] = v.y;
+  }
   __device__ static __forceinline__ float dec(T v, float) { return v; }
   __device__ static __forceinline__ T enc(float v, float) { return v; }
   __device__ static __forceinline__ void load4(const T* p, float o[4], float) {
@@ -112,6 +116,10 @@ template <> struct Store<PREC_FP16> {
     *reinterpret_cast<uint2*>(p) = raw;
   }
   __device__ static __forceinline__ void store2r(T* p, float2 v) { *reinterpret_cast<__half2*>(p) = __float22half2_rn(v); }
+  __device__ static __forceinline__ void load2(const T* p, float o[2], float inv) {
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(p));
+    o[0] = a.x * inv; o[1] = a.y * inv;
+  }
   __device__ static __forceinline__ float dec(T v, float inv) { return __half2float(v) * inv; }
   __device__ static __forceinline__ T enc(float v, float sc) { return __float2half_rn(v * sc); }
   __device__ static __forceinline__ void load4(const T* p, float o[4], float inv) {
@@ -136,6 +144,10 @@ template <> struct Store<PREC_BF16> {
   __device__ static __forceinline__ void load4r(const T* p, float o[4]) { load4(p, o, 1.0f); }
   __device__ static __forceinline__ void store4r(T* p, const float o[4]) { store4(p, o, 1.0f); }
   __device__ static __forceinline__ void store2r(T* p, float2 v) { *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(v); }
+  __device__ static __forceinline__ void load2(const T* p, float o[2], float) {
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+    o[0] = a.x; o[1] = a.y;
+  }
   __device__ static __forceinline__ float dec(T v, float) { return __bfloat162float(v); }
   __device__ static __forceinline__ T enc(float v, float) { return __float2bfloat16_rn(v); }
   __device__ static __forceinline__ void load4(const T* p, float o[4], float) {

@@ -36,13 +36,14 @@ cudaError_t launch_residual(const StepParams& P, int prec, bool het, bool therma
                             double* partial, int nblocks, double* out, cudaStream_t s);
 cudaError_t launch_nusselt(const StepParams& P, int prec, int side, double* out, cudaStream_t s);
 
-cudaError_t launch_adj_seed(const StepParams& P, int prec, bool het, float* nu_out, double* g_l, double* g_phi, int kind,
+cudaError_t launch_adj_seed(const StepParams& P, int prec, bool het, float* nu_out, float* g_l, float* g_phi, int kind,
                             const float* tux, const float* tuy, double* partial, int nblocks, double* loss_out, cudaStream_t s);
-cudaError_t launch_adj_nee(const StepParams& P, int prec, bool het, const void* buf, float* nu, double* g_l, double* g_phi,
+cudaError_t launch_adj_nee(const StepParams& P, int prec, bool het, const void* buf, float* nu, float* g_l, float* g_phi,
                            cudaStream_t s);
-cudaError_t launch_adj_step(const StepParams& P, int prec, bool het, const void* buf, const float* nu_in, float* nu_out, double* g_l,
-                            double* g_phi, cudaStream_t s);
-cudaError_t launch_adj_init(const StepParams& P, bool het, const float* nu, double* g_phi, float p0, float ux0, float uy0,
+cudaError_t launch_adj_step(const StepParams& P, int prec, bool het, const void* buf, const float* nu_in, float* nu_out, float* g_l,
+                            float* g_phi, cudaStream_t s);
+cudaError_t launch_adj_init(const StepParams& P, bool het, const float* nu, float* g_phi, float p0, float ux0, float uy0,
                             int phip_uniform, cudaStream_t s);
+cudaError_t launch_adj_fold(float* l32, float* p32, double* l64, double* p64, int64_t n, cudaStream_t s);
 
 }  // namespace lbm

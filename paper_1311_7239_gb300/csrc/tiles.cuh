@@ -40,6 +40,26 @@ __device__ __forceinline__ void gather4(const typename Store<PREC>::T* __restric
   }
 }
 
+// The same for a pair of cells: out[c] = row[x0 + c - SH], c = 0, 1 (x0 even, 2-element aligned).
+template <int PREC, int SH>
+__device__ __forceinline__ void gather2(const typename Store<PREC>::T* __restrict__ row, int xl, int pitch, int lane, float inv,
+                                        float out[2]) {
+  using S = Store<PREC>;
+  float v[2];
+  S::load2(row + xl, v, inv);
+  if (SH == 0) {
+    out[0] = v[0]; out[1] = v[1];
+  } else if (SH == 1) {
+    float left = __shfl_up_sync(kFull, v[1], 1);
+    if (lane == 0) left = S::dec(row[xl > 0 ? xl - 1 : 0], inv);
+    out[0] = left; out[1] = v[0];
+  } else {
+    float right = __shfl_down_sync(kFull, v[0], 1);
+    if (lane == 31) right = S::dec(row[xl + 2 < pitch ? xl + 2 : pitch - 1], inv);
+    out[0] = v[1]; out[1] = right;
+  }
+}
+
 // Frame of the lattice: the groups of C cells that contain a wall-row cell or a cell of the first
 // or last column (the last group of a row also holds the row padding).  Their cells are gathered
 // with every boundary rule (pull_one: halfway bounce-back with wall velocity, periodic wrap,

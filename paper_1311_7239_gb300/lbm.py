@@ -84,6 +84,7 @@ SIGNATURES = {
     "lbm_nusselt": (ctypes.c_int, [_c_ctx, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "lbm_adjoint": (ctypes.c_int, [_c_ctx, ctypes.c_int, ctypes.c_int, _f32p, _f32p, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p]),
+    "lbm_release_workspace": (ctypes.c_int, [_c_ctx]),
     "lbm_residual_noalloc": (ctypes.c_int, [_f32p, _f32p, _f32p, _f32p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "lbm_sync": (ctypes.c_int, [_c_ctx]),
     "lbm_save": (ctypes.c_int, [_c_ctx, ctypes.c_char_p]),
@@ -313,6 +314,10 @@ class Lattice:
         _check(lib().lbm_adjoint(self._h, int(T), kind, _ptr(tx), _ptr(ty), gk.data_ptr(), ge.data_ptr(), L.data_ptr()),
                "lbm_adjoint")
         return float(L.item()), gk, ge
+
+    def release_workspace(self):
+        """Free the adjoint workspace kept between adjoint calls."""
+        _check(lib().lbm_release_workspace(self._h), "lbm_release_workspace")
 
     def nusselt(self, side=LEFT):
         v = ctypes.c_double()

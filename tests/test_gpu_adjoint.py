@@ -51,6 +51,9 @@ CASES = {
     "lid-cavity-misfit": (Case(24, 20, nu=0.06, phi=0.5, K=4.0, het=True, eps_sd=0.05, corr=4.0, bc_x="wall", bc_y="wall",
                                walls={"top": (0.08, 0.0)}), 40, "misfit", False),
     "forced-channel-flux": (Case(20, 16, nu=0.08, phi=0.4, K=6.0, het=True, eps_sd=0.05, corr=4.0, ax=3e-4), 30, "flux", False),
+    # rows longer than one work item (150 cell pairs > 128 threads): the split-row tiling
+    "long-row-pressure-channel": (Case(300, 8, nu=0.1, phi=0.35, K=0.05 * 8 * 8, het=True, eps_sd=0.03, corr=8.0, bc_x="pressure",
+                                       bc_y="wall", p_in=1.001, p_out=0.999), 12, "flux", True),
 }
 
 
@@ -124,3 +127,28 @@ def test_autograd_function(lbm):
     assert abs(loss.item() - Lo) <= 1e-5 * abs(Lo)
     assert rel_l2(logk.grad.cpu().numpy(), 2 * gko) <= 1e-4
     assert rel_l2(e.grad.cpu().numpy(), 2 * geo) <= 1e-4
+
+
+def test_workspace_is_reused_and_released(lbm):
+    """Repeated adjoint calls (as in an optimisation loop) reuse the retained workspace and give
+    bitwise the same result; a call with another T resizes it; release frees it."""
+    case, T, kind, phip = CASES["pressure-channel-flux"]
+    p0 = case.p_rest()
+    with case.lattice(lbm) as lat:
+        base = lat.memory_bytes()
+        lat.init_equilibrium(p0, 0.0, 0.0, phi_p_uniform=True)
+        L1, gk1, ge1 = lat.adjoint(T, kind)
+        held = lat.memory_bytes()
+        assert held > base
+        lat.init_equilibrium(p0, 0.0, 0.0, phi_p_uniform=True)
+        L2, gk2, ge2 = lat.adjoint(T, kind)
+        assert lat.memory_bytes() == held
+        assert L1 == L2 and bool((gk1 == gk2).all()) and bool((ge1 == ge2).all())
+        lat.init_equilibrium(p0, 0.0, 0.0, phi_p_uniform=True)
+        L3, gk3, ge3 = lat.adjoint(2 * T + 7, kind)
+        Lo, gko, geo = adj.gradient(case.flow(), 2 * T + 7, kind, None, p0=p0, phi_p_uniform=True)
+        assert abs(L3 - Lo) <= 1e-5 * abs(Lo)
+        assert np.abs(gk3.cpu().numpy() - gko).max() <= 1e-4 * np.abs(gko).max()
+        assert np.abs(ge3.cpu().numpy() - geo).max() <= 1e-4 * np.abs(geo).max()
+        lat.release_workspace()
+        assert lat.memory_bytes() == base
