@@ -199,6 +199,11 @@ LBM_API int lbm_residual_noalloc(const float* ux, const float* uy, const float* 
 LBM_API int lbm_adjoint(lbm_ctx* ctx, int T, int loss_kind, const float* target_ux, const float* target_uy, double* grad_logK,
                         double* grad_eps, double* loss);
 
+/* lbm_adjoint under the name used in the method's interface description (same arguments, same
+ * behaviour): the adjoint of the stream-collide step applied over T steps. */
+LBM_API int lbm_adjoint_step(lbm_ctx* ctx, int T, int loss_kind, const float* target_ux, const float* target_uy,
+                             double* grad_logK, double* grad_eps, double* loss);
+
 /* Frees the workspace that lbm_adjoint keeps between calls (no-op if there is none); the next
  * lbm_adjoint allocates it again.  Waits for the stream.  Not in the paper: memory management. */
 LBM_API int lbm_release_workspace(lbm_ctx* ctx);

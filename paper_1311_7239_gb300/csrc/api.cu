@@ -886,6 +886,11 @@ int lbm_adjoint(lbm_ctx* c, int T, int loss_kind, const float* target_ux, const 
   return check_error_word(c);
 }
 
+int lbm_adjoint_step(lbm_ctx* c, int T, int loss_kind, const float* target_ux, const float* target_uy, double* grad_logK,
+                     double* grad_eps, double* loss) {
+  return lbm_adjoint(c, T, loss_kind, target_ux, target_uy, grad_logK, grad_eps, loss);
+}
+
 int lbm_release_workspace(lbm_ctx* c) {
   if (!c) return fail(LBM_EINVAL, "null context");
   LBM_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");

@@ -84,6 +84,8 @@ SIGNATURES = {
     "lbm_nusselt": (ctypes.c_int, [_c_ctx, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "lbm_adjoint": (ctypes.c_int, [_c_ctx, ctypes.c_int, ctypes.c_int, _f32p, _f32p, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p]),
+    "lbm_adjoint_step": (ctypes.c_int, [_c_ctx, ctypes.c_int, ctypes.c_int, _f32p, _f32p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
     "lbm_release_workspace": (ctypes.c_int, [_c_ctx]),
     "lbm_residual_noalloc": (ctypes.c_int, [_f32p, _f32p, _f32p, _f32p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
     "lbm_sync": (ctypes.c_int, [_c_ctx]),

@@ -152,3 +152,20 @@ def test_workspace_is_reused_and_released(lbm):
         assert np.abs(ge3.cpu().numpy() - geo).max() <= 1e-4 * np.abs(geo).max()
         lat.release_workspace()
         assert lat.memory_bytes() == base
+
+
+def test_adjoint_step_name_is_the_same_call(lbm):
+    """lbm_adjoint_step (the interface description's name) returns what lbm_adjoint returns."""
+    import torch
+
+    case, T, kind, phip = CASES["forced-channel-flux"]
+    with case.lattice(lbm) as lat:
+        lat.init_equilibrium(1.0, 0.0, 0.0)
+        L1, gk1, ge1 = lat.adjoint(T, kind)
+        lat.init_equilibrium(1.0, 0.0, 0.0)
+        gk2 = torch.zeros_like(gk1)
+        ge2 = torch.zeros_like(ge1)
+        L2 = torch.zeros(1, dtype=torch.float64, device="cuda")
+        rc = lbm.lib().lbm_adjoint_step(lat._h, T, lbm.LOSS_OUTLET_FLUX, None, None, gk2.data_ptr(), ge2.data_ptr(), L2.data_ptr())
+        assert rc == lbm.OK
+        assert L1 == float(L2.item()) and bool((gk1 == gk2).all()) and bool((ge1 == ge2).all())
