@@ -101,6 +101,12 @@ def test_bench_cavity_4096_fp16_sampled_cells(lbm):
     print(f"4096^2 FP16, {K_STEPS} steps: max |df| over 64 sampled cells = {worst:.2e}")
 
 
+def test_bench_cavity_4096_bf16_sampled_cells(lbm):
+    """BF16 deviation storage (unscaled, 8-bit significand): a unit of 2^-8 |d|, |d| <= 0.1."""
+    worst = _sampled_parity(lbm, 2, K_STEPS * 4e-4)
+    print(f"4096^2 BF16, {K_STEPS} steps: max |df| over 64 sampled cells = {worst:.2e}")
+
+
 def test_ensemble_512_in_bench_launch_form(lbm):
     """The 512-lattice ensemble of the benchmark, in the launch form its tuner picks (one CTA per
     work item): after 32 steps from the rest state, sampled cells of eight lattices (largest,

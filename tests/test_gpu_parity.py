@@ -218,6 +218,38 @@ def test_reduced_precision_storage_error(lbm, accuracy, prec, bound):
     assert e_u <= bound and e_p <= bound, (e_u, e_p)
 
 
+@pytest.mark.parametrize("prec,bound", [(1, 1e-3), (2, 2e-2)])
+def test_reduced_precision_long_rows(lbm, accuracy, prec, bound):
+    """16-bit storage with rows longer than one work item: a 600 x 64 lid-driven cavity (two
+    512-cell items per row, the second ragged) against the oracle.  BF16's 8-bit significand
+    gives ~1e-2 here (1.0e-2 at 600 x 64, 9.6e-3 at 500 x 64)."""
+    case = Case(600, 64, nu=0.1 * 64 / 100, phi=0.4, K=1e-3 * 64 * 64, bc_x="wall", bc_y="wall", walls=CAV, precision=prec)
+    e_u, e_p = _trajectory(lbm, case, 400)
+    print(f"precision {prec}, 600x64: rel-L2 u {e_u:.3e}, p {e_p:.3e}")
+    accuracy.append({"case": "lid-driven porous cavity 600x64, eps 0.4, Da 1e-3", "precision": {1: "fp16", 2: "bf16"}[prec],
+                     "steps": 400, "rel_l2_u": e_u, "rel_l2_p": e_p, "bound": bound})
+    assert e_u <= bound and e_p <= bound, (e_u, e_p)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_reduced_precision_one_step_long_rows(lbm, prec):
+    """One step with 16-bit storage from a random state against the oracle, cell by cell, on a
+    periodic 1100 x 7 channel with a moving top wall (three items per row, ragged), to the
+    storage's rounding, twice (the imported state and the result): FP16 2^-11 of |d| <= 0.1 at
+    scale 2^10, BF16 2^-8."""
+    case = Case(1100, 7, bc_x="periodic", bc_y="wall", walls={"top": (0.05, 0.0)}, ax=1e-4, precision=prec)
+    flow = case.flow()
+    f0 = random_state(flow, seed=3)
+    with case.lattice(lbm) as lat:
+        lat.set_populations(to_gpu(f0))
+        lat.step(1)
+        got = lat.get_populations().cpu().numpy()
+        lat.sync()
+    want = fl.step(f0, flow)  # the bound covers the rounding of the imported state and of the result
+    tol = 1e-4 if prec == 1 else 8e-4
+    assert np.abs(got - want).max() <= tol, np.abs(got - want).max()
+
+
 @pytest.mark.parametrize("prec,bound", [(1, 1e-3), (2, 5e-2)])
 def test_reduced_precision_thermal_error(lbm, accuracy, prec, bound):
     """Natural convection with FP16 / BF16 storage.  BF16 keeps 8 significant bits (unit
