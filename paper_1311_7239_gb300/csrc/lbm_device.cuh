@@ -116,6 +116,13 @@ template <> struct Store<PREC_FP16> {
     *reinterpret_cast<uint2*>(p) = raw;
   }
   __device__ static __forceinline__ void store2r(T* p, float2 v) { *reinterpret_cast<__half2*>(p) = __float22half2_rn(v); }
+  // a 32-bit word holding two stored values <-> the pair as float2 (no scale applied)
+  __device__ static __forceinline__ float2 w2f(uint32_t w) { return __half22float2(*reinterpret_cast<const __half2*>(&w)); }
+  __device__ static __forceinline__ uint32_t f2w(float2 v) {
+    const __half2 h = __float22half2_rn(v);
+    return *reinterpret_cast<const uint32_t*>(&h);
+  }
+  __device__ static __forceinline__ uint32_t bits(T v) { return *reinterpret_cast<const unsigned short*>(&v); }
   __device__ static __forceinline__ void load2(const T* p, float o[2], float inv) {
     const float2 a = __half22float2(*reinterpret_cast<const __half2*>(p));
     o[0] = a.x * inv; o[1] = a.y * inv;
@@ -144,6 +151,12 @@ template <> struct Store<PREC_BF16> {
   __device__ static __forceinline__ void load4r(const T* p, float o[4]) { load4(p, o, 1.0f); }
   __device__ static __forceinline__ void store4r(T* p, const float o[4]) { store4(p, o, 1.0f); }
   __device__ static __forceinline__ void store2r(T* p, float2 v) { *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(v); }
+  __device__ static __forceinline__ float2 w2f(uint32_t w) { return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w)); }
+  __device__ static __forceinline__ uint32_t f2w(float2 v) {
+    const __nv_bfloat162 h = __float22bfloat162_rn(v);
+    return *reinterpret_cast<const uint32_t*>(&h);
+  }
+  __device__ static __forceinline__ uint32_t bits(T v) { return *reinterpret_cast<const unsigned short*>(&v); }
   __device__ static __forceinline__ void load2(const T* p, float o[2], float) {
     const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
     o[0] = a.x; o[1] = a.y;

@@ -61,6 +61,54 @@ __device__ void frame_step(const StepParams& P, const Frame& F, int k) {
   }
 }
 
+// Main item of the packed collision without temperature: the populations stay in their stored
+// 16-bit form (two cells per 32-bit word) until each pair is collided, which halves the
+// registers that hold the gathered state.
+template <int PREC, int NT>
+__device__ __forceinline__ void step_item_words(const StepParams& P, const Tiling& tl, int item) {
+  using S = Store<PREC>;
+  using T = typename S::T;
+  constexpr int C = kCellsPerThread;
+  int x0, y;
+  const bool has_group = main_group(tl, P.ny, NT, item - tl.frame_blocks, (int)threadIdx.x, x0, y);
+  const T* __restrict__ src = static_cast<const T*>(P.src);
+  const int lane = threadIdx.x & 31;
+  const int xl = x0 < P.pitch - C ? x0 : P.pitch - C;
+  int ym = y - 1, yp = y + 1;
+  ym = ym < 0 ? P.ny - 1 : ym;
+  yp = yp >= P.ny ? 0 : yp;
+  const int64_t pl = P.plane;
+  const int64_t rm = (int64_t)ym * P.pitch, r0 = (int64_t)y * P.pitch, rp = (int64_t)yp * P.pitch;
+  // pull streaming, Eq. 15, as stored (s d): w[i] = pairs (c0, c1), (c2, c3) of population i
+  uint32_t w[8][2];
+  gather4w<PREC, 1>(src + 0 * pl + r0, xl, P.pitch, lane, w[0]);   // e1 = ( 1, 0)
+  gather4w<PREC, 0>(src + 1 * pl + rm, xl, P.pitch, lane, w[1]);   // e2 = ( 0, 1)
+  gather4w<PREC, -1>(src + 2 * pl + r0, xl, P.pitch, lane, w[2]);  // e3 = (-1, 0)
+  gather4w<PREC, 0>(src + 3 * pl + rp, xl, P.pitch, lane, w[3]);   // e4 = ( 0,-1)
+  gather4w<PREC, 1>(src + 4 * pl + rm, xl, P.pitch, lane, w[4]);   // e5 = ( 1, 1)
+  gather4w<PREC, -1>(src + 5 * pl + rm, xl, P.pitch, lane, w[5]);  // e6 = (-1, 1)
+  gather4w<PREC, -1>(src + 6 * pl + rp, xl, P.pitch, lane, w[6]);  // e7 = (-1,-1)
+  gather4w<PREC, 1>(src + 7 * pl + rp, xl, P.pitch, lane, w[7]);   // e8 = ( 1,-1)
+  const bool wall_row = P.bc_y == BC_WALL && (y == 0 || y == P.ny - 1);
+  if (!has_group || wall_row || x0 == 0 || x0 + C >= P.nx) return;
+  float check = 0.0f;
+#pragma unroll
+  for (int h = 0; h < C / 2; ++h) {
+    float2 dp[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) dp[i] = S::w2f(w[i][h]);
+    float2 ux, uy;
+    collide_pair(dp, pair_coef_uniform(P.pc), f2(P.pc.u_hx), f2(P.pc.u_hy), P.pc, ux, uy);
+    check += (fabsf(ux.x) + fabsf(uy.x)) + (fabsf(ux.y) + fabsf(uy.y));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) w[i][h] = S::f2w(dp[i]);
+  }
+  if (!(check < 1e30f)) atomicOr(P.err, 1u);  // non-finite velocity in these cells
+  T* __restrict__ dst = static_cast<T*>(P.dst);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) *reinterpret_cast<uint2*>(dst + i * pl + r0 + x0) = make_uint2(w[i][0], w[i][1]);
+}
+
 // Work item `item` of one lattice, for CTAs of NT threads: items [0, frame_blocks) do the frame,
 // the rest cover the lattice row by row, gx items per row, and store every group that is not a
 // frame group.  Every thread of the CTA calls this with the same item (warp shuffles inside).
@@ -72,6 +120,10 @@ __device__ __forceinline__ void step_item(const StepParams& P, const Tiling& tl,
   if (item < tl.frame_blocks) {
     const Frame F = frame_of(P.nx, P.ny, P.bc_y, C);
     frame_step<PREC, HET, THERMAL>(P, F, item * NT + (int)threadIdx.x);
+    return;
+  }
+  if constexpr (kPacked<PREC, HET> && !THERMAL) {
+    step_item_words<PREC, NT>(P, tl, item);
     return;
   }
   int x0, y;
@@ -187,11 +239,12 @@ __device__ __forceinline__ void step_item(const StepParams& P, const Tiling& tl,
   }
 }
 
-// One time step of one lattice: one CTA per work item.  Register caps: 8 CTAs (32 warps) per SM
-// for the flow alone (64 registers, no spill), 7 for the packed collision of 16-bit storage (72,
-// a few words of spill), 6 and 5 with the temperature populations (80 and 96).
+// One time step of one lattice: one CTA per work item.  Register caps (measured): 8 CTAs (32
+// warps) per SM for the flow alone (64 registers), also with FP16 storage; 7 with BF16 storage
+// (72: at 64 its conversions spill and it runs 8 % slower); 6 and 5 with the temperature
+// populations (80 and 96).
 template <int PREC, bool HET, bool THERMAL>
-__global__ void __launch_bounds__(kStepThreads, THERMAL ? (PREC == PREC_FP32 ? 6 : 5) : (kPacked<PREC, HET> ? 7 : 8)) k_step(const StepParams P, Tiling tl) {
+__global__ void __launch_bounds__(kStepThreads, THERMAL ? (PREC == PREC_FP32 ? 6 : 5) : (kPacked<PREC, HET> && PREC == PREC_BF16 ? 7 : 8)) k_step(const StepParams P, Tiling tl) {
   step_item<PREC, HET, THERMAL, kStepThreads>(P, tl, blockIdx.x);
 }
 

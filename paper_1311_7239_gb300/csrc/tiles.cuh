@@ -40,6 +40,29 @@ __device__ __forceinline__ void gather4(const typename Store<PREC>::T* __restric
   }
 }
 
+// 16-bit storage kept as stored: the four values of gather4 as two 32-bit words (cells 0-1 and
+// 2-3, first cell in the low half); the one-cell shifts are byte permutes of neighbouring words.
+template <int PREC, int SH>
+__device__ __forceinline__ void gather4w(const typename Store<PREC>::T* __restrict__ row, int xl, int pitch, int lane,
+                                         uint32_t out[2]) {
+  using S = Store<PREC>;
+  static_assert(sizeof(typename S::T) == 2, "16-bit storage");
+  const uint2 v = *reinterpret_cast<const uint2*>(row + xl);
+  if (SH == 0) {
+    out[0] = v.x; out[1] = v.y;
+  } else if (SH == 1) {  // cells x - 1: (left, c0), (c1, c2)
+    uint32_t lw = __shfl_up_sync(kFull, v.y, 1);  // its high half is the left neighbour's last cell
+    if (lane == 0) lw = S::bits(row[xl > 0 ? xl - 1 : 0]) << 16;
+    out[0] = __byte_perm(lw, v.x, 0x5432);
+    out[1] = __byte_perm(v.x, v.y, 0x5432);
+  } else {  // cells x + 1: (c1, c2), (c3, right)
+    uint32_t rw = __shfl_down_sync(kFull, v.x, 1);  // its low half is the right neighbour's first cell
+    if (lane == 31) rw = S::bits(row[xl + 4 < pitch ? xl + 4 : pitch - 1]);
+    out[0] = __byte_perm(v.x, v.y, 0x5432);
+    out[1] = __byte_perm(v.y, rw, 0x5432);
+  }
+}
+
 // The same for a pair of cells: out[c] = row[x0 + c - SH], c = 0, 1 (x0 even, 2-element aligned).
 template <int PREC, int SH>
 __device__ __forceinline__ void gather2(const typename Store<PREC>::T* __restrict__ row, int xl, int pitch, int lane, float inv,
