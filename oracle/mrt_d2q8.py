@@ -24,6 +24,11 @@ Readings of the paper used here (each one is listed with its reason in the design doc
   * Pressure inlet/outlet columns use non-equilibrium extrapolation (the scheme the paper cites
     for its boundaries, Sec. 3): f_b = f_eq(p_b, u_nb; phi_b) + f_nb - f_eq(p_nb, u_nb; phi_nb),
     with f_eq = M^-1 m_eq and nb the adjacent interior column, applied after streaming.
+  * The same extrapolation on wall nodes ('nee' sides, the paper's own wall treatment, Sec. 3):
+    the wall lies on the outermost nodes (channel height H = ny - 1), and a wall node takes
+    f_b = f_eq(p_nb, u_w; phi_b) + f_nb - f_eq(p_nb, u_nb; phi_nb), nb being the node one step
+    inward along the wall normal (the diagonal one at a corner where the other side is not
+    periodic), p extrapolated with zero normal gradient.  Bottom/top walls own the corners.
 """
 from __future__ import annotations
 
@@ -75,7 +80,8 @@ class Flow:
     rates: optional full diagonal of Lambda (Eq. 13); default (1, s_e, 1, s_q, 1, s_q, s_v, s_v)
            with s_v = 1/tau_v and upsilon_e = c_s^2 (tau_v - 1/2) (Eq. 21).
     forchheimer: F_phi from Ergun's relation (Eq. 4) if True, else F_phi = 0 (Brinkman limit).
-    bc_x: 'periodic' | 'wall' | 'pressure';  bc_y: 'periodic' | 'wall'.
+    bc_x: 'periodic' | 'wall' | 'pressure' | 'nee';  bc_y: 'periodic' | 'wall' | 'nee'
+          ('wall': halfway bounce-back; 'nee': wall nodes with non-equilibrium extrapolation).
     u_left/u_right/u_bottom/u_top: wall velocities (2,) of the four sides (moving lid = u_top).
     p_in/p_out: pressures of the x = 0 and x = nx-1 columns when bc_x == 'pressure'.
     """
@@ -277,8 +283,8 @@ def stream(f_plus, flow: Flow):
     """f_i(x + e_i, t+1) = f_i+(x, t) (Eq. 15); a link that leaves the fluid bounces back halfway:
     f_opp(i)(x, t+1) = f_i+(x, t) - 2 omega_i rho0 (e_i . u_w) / c_s^2.
 
-    'pressure' x-boundaries stream periodically here; ``pressure_columns`` then overwrites
-    columns 0 and nx-1.
+    'pressure' and 'nee' sides stream periodically here; ``pressure_columns`` and ``wall_nodes``
+    then overwrite their boundary nodes.
     """
     ny, nx = flow.ny, flow.nx
     ys, xs = np.mgrid[0:ny, 0:nx]
@@ -286,9 +292,9 @@ def stream(f_plus, flow: Flow):
     for i in range(8):
         tx = xs + E[i, 0]
         ty = ys + E[i, 1]
-        if flow.bc_x in ("periodic", "pressure"):
+        if flow.bc_x in ("periodic", "pressure", "nee"):
             tx = tx % nx
-        if flow.bc_y == "periodic":
+        if flow.bc_y in ("periodic", "nee"):
             ty = ty % ny
         inside = (tx >= 0) & (tx < nx) & (ty >= 0) & (ty < ny)
         out[i, ty[inside], tx[inside]] = f_plus[i, ys[inside], xs[inside]]
@@ -324,6 +330,56 @@ def pressure_columns(f, flow: Flow, phi=None, K=None):
     return out
 
 
+def wall_nodes(f, flow: Flow, phi=None, K=None):
+    """Non-equilibrium extrapolation on the wall nodes of 'nee' sides (Sec. 3's wall treatment).
+
+    f_b = f_eq(p_nb, u_w; phi_b) + [f_nb - f_eq(p_nb, u_nb; phi_nb)] with u_nb, p_nb from Eqs. 17-20
+    at nb, the node one step inward along the wall normal; bottom/top walls own the corners, whose
+    nb is the diagonal node when the x sides are not periodic.  Returns a new array.
+    """
+    phi = flow.phi if phi is None else phi
+    K = flow.K if K is None else K
+    ax, ay = _accel(flow, f[0])
+    ny, nx = flow.ny, flow.nx
+    nodes = []  # (y, x, yn, xn, u_w)
+    if flow.bc_x == "nee":
+        for y in range(ny):
+            if flow.bc_y == "nee" and y in (0, ny - 1):
+                continue
+            nodes.append((y, 0, y, 1, flow.u_left))
+            nodes.append((y, nx - 1, y, nx - 2, flow.u_right))
+    if flow.bc_y == "nee":
+        for x in range(nx):
+            xn = x
+            if flow.bc_x != "periodic" and x in (0, nx - 1):
+                xn = 1 if x == 0 else nx - 2
+            nodes.append((0, x, 1, xn, flow.u_bottom))
+            nodes.append((ny - 1, x, ny - 2, xn, flow.u_top))
+    out = f.astype(np.result_type(f, phi, K), copy=True)
+    if not nodes:
+        return out
+    yb, xb, yn, xn = (np.array([n[k] for n in nodes]) for k in range(4))
+    uw = np.array([n[4] for n in nodes], dtype=np.float64)
+    fn = f[:, yn, xn]
+    ux, uy = velocity(fn, phi[yn, xn], K[yn, xn], flow.nu, flow.rho0, flow.forchheimer, ax[yn, xn], ay[yn, xn])
+    pn = pressure(fn, ux, uy, phi[yn, xn], flow.rho0)
+    out[:, yb, xb] = (
+        equilibrium(pn, uw[:, 0], uw[:, 1], phi[yb, xb], flow.rho0)
+        + fn
+        - equilibrium(pn, ux, uy, phi[yn, xn], flow.rho0)
+    )
+    return out
+
+
+def boundary_nodes(f, flow: Flow):
+    """The extrapolated boundary nodes after streaming: pressure columns, then wall nodes."""
+    if flow.bc_x == "pressure":
+        f = pressure_columns(f, flow)
+    if "nee" in (flow.bc_x, flow.bc_y):
+        f = wall_nodes(f, flow)
+    return f
+
+
 # ---------------------------------------------------------------------------------------------
 # Time stepping
 # ---------------------------------------------------------------------------------------------
@@ -336,17 +392,14 @@ def initial_state(flow: Flow, p0=1.0, u0=(0.0, 0.0)):
     uy = np.full((flow.ny, flow.nx), float(u0[1]))
     p = np.broadcast_to(np.asarray(p0, dtype=np.float64), (flow.ny, flow.nx))
     f = equilibrium(p, ux, uy, flow.phi, flow.rho0)
-    # the initial state, like every later one, satisfies the pressure-column rule
-    return pressure_columns(f, flow) if flow.bc_x == "pressure" else f
+    # the initial state, like every later one, satisfies the boundary-node rules
+    return boundary_nodes(f, flow)
 
 
 def step(f, flow: Flow):
-    """One time step of Eq. 6: collide (Eq. 14) then stream (Eq. 15), then pressure columns."""
+    """One time step of Eq. 6: collide (Eq. 14) then stream (Eq. 15), then the boundary nodes."""
     f_plus = collide(f, flow)[0]
-    out = stream(f_plus, flow)
-    if flow.bc_x == "pressure":
-        out = pressure_columns(out, flow)
-    return out
+    return boundary_nodes(stream(f_plus, flow), flow)
 
 
 def run(f, flow: Flow, steps: int):

@@ -10,7 +10,7 @@ from oracle import mrt_d2q8 as fl
 from oracle import thermal_d2q5 as th
 from paper_1311_7239_gb300 import synth
 
-_BC = {"periodic": 0, "wall": 1, "pressure": 2}
+_BC = {"periodic": 0, "wall": 1, "pressure": 2, "nee": 3}
 
 
 @dataclass
@@ -101,6 +101,6 @@ def random_state(flow: fl.Flow, seed: int, amp: float = 0.02, u_amp: float = 0.0
     uy = u_amp * rng.standard_normal((flow.ny, flow.nx))
     f = fl.equilibrium(p, ux, uy, flow.phi) + amp * 0.1 * rng.standard_normal((8, flow.ny, flow.nx))
     f = f.astype(np.float32).astype(np.float64)
-    if flow.bc_x == "pressure":
-        f = fl.pressure_columns(f, flow).astype(np.float32).astype(np.float64)
+    if flow.bc_x == "pressure" or "nee" in (flow.bc_x, flow.bc_y):
+        f = fl.boundary_nodes(f, flow).astype(np.float32).astype(np.float64)
     return f

@@ -20,6 +20,8 @@ FLOW_PINS = [
         "wall", "wall", {"bottom": (0.0, 0.01), "top": (0.1, 0.0), "left": (0.0, 0.02), "right": (0.0, -0.03)}),
     pins.test_free_fluid_poiseuille_is_exact_parabola_at_magic_rates,
     pins.test_porous_couette_sinh_profile_pins_moving_wall,
+    pins.test_nee_walls_porous_couette_moving_node,
+    pins.test_nee_wall_node_is_equilibrium_at_wall_velocity_for_equilibrium_neighbour,
 ]
 THERMAL_PINS = [
     tpins.test_collision_keeps_T_and_relaxes_flux_to_uT,
@@ -94,10 +96,21 @@ def _mut_opposite(monkeypatch):
     monkeypatch.setattr(fl, "OPP", opp)
 
 
+def _mut_nee_neighbour_velocity(monkeypatch):
+    """Wall nodes that ignore the walls' velocities (a moving lid treated as fixed)."""
+    orig_nodes = fl.wall_nodes
+
+    def wrong_nodes(f, flow, phi=None, K=None):
+        import dataclasses
+        return orig_nodes(f, dataclasses.replace(flow, u_top=(0.0, 0.0), u_bottom=(0.0, 0.0)), phi, K)
+
+    monkeypatch.setattr(fl, "wall_nodes", wrong_nodes)
+
+
 @pytest.mark.parametrize(
     "mutation",
     [_mut_forcing_sign, _mut_l0, _mut_minv_transposed, _mut_bb_weights, _mut_pressure_s0, _mut_meq_gamma, _mut_drag_phi,
-     _mut_opposite],
+     _mut_opposite, _mut_nee_neighbour_velocity],
 )
 def test_flow_pins_catch_planted_mistake(monkeypatch, mutation):
     mutation(monkeypatch)

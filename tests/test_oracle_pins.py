@@ -328,3 +328,61 @@ def test_partially_porous_couette_with_viscosity_ratio(J):
     y = np.arange(H) + 0.5
     exact = np.where(y < H / 2, d0 * np.sinh(th * y) / np.sinh(th * H / 2), d0 + s * (y - H / 2))
     assert np.abs(ux - exact).max() < 1.5e-2 * u0, np.abs(ux - exact).max() / u0
+
+
+# ---------------------------------------------------------------------------------------------
+# Wall nodes with non-equilibrium extrapolation (the paper's own wall treatment, Sec. 3): walls on
+# the outermost nodes, channel height H = ny - 1.  The scheme is second-order accurate, so the
+# error against the closed forms of Eq. 23 falls ~4x when the grid is refined 2x.
+# ---------------------------------------------------------------------------------------------
+def _nee_poiseuille_error(N, phi=0.1, nu=0.3):
+    H = N - 1
+    K = 0.01 * H * H
+    th = np.sqrt(phi / K)
+    u0 = nu / H  # Re = 1
+    G = u0 * nu / (K * (1 - 1 / np.cosh(th * H / 2)))  # Eq. 24 solved for a_x
+    flow = _uniform_flow(2, N, phi, K, nu, forchheimer=False, accel=np.array([G, 0.0]), bc_y="nee")
+    f = _steady(flow, fl.initial_state(flow), 40000, tol=1e-12)
+    ux = fl.macroscopic(f, flow)[0][:, 0]
+    exact = _brinkman_poiseuille(np.arange(N, dtype=np.float64), H, G, phi, K, nu)
+    return np.abs(ux - exact).max() / exact.max()
+
+
+def test_nee_walls_porous_poiseuille_second_order():
+    e17, e33 = _nee_poiseuille_error(17), _nee_poiseuille_error(33)
+    assert e33 < 7e-3, e33
+    assert e17 / e33 > 3.3, (e17, e33)
+
+
+def test_nee_walls_porous_couette_moving_node():
+    """Top wall node moving at u0, a = 0, F_phi = 0: u = u0 sinh(th y) / sinh(th H) with y the
+    distance from the bottom wall node; the moving node itself carries u0."""
+    N, phi, nu, u0 = 25, 0.1, 0.25, 0.01
+    H = N - 1
+    K = 0.01 * H * H
+    th = np.sqrt(phi / K)
+    flow = _uniform_flow(2, N, phi, K, nu, forchheimer=False, bc_y="nee", u_top=(u0, 0.0))
+    f = _steady(flow, fl.initial_state(flow), 40000, tol=1e-12)
+    ux, uy = fl.macroscopic(f, flow)[:2]
+    exact = u0 * np.sinh(th * np.arange(N)) / np.sinh(th * H)
+    assert np.abs(ux[:, 0] - exact).max() < 5e-3 * u0
+    assert abs(ux[-1, 0] - u0) < 1e-3 * u0
+    assert np.abs(uy).max() < 1e-4 * u0  # extrapolated walls do not conserve mass exactly
+
+
+def test_nee_wall_node_is_equilibrium_at_wall_velocity_for_equilibrium_neighbour():
+    """If the inner neighbour is at equilibrium, the extrapolated wall node is the equilibrium at
+    the neighbour's pressure and the wall's velocity (the non-equilibrium part vanishes).  K -> inf
+    and F_phi = 0, so that Eqs. 18-20 recover the neighbour's (p, u) exactly."""
+    flow = _uniform_flow(5, 4, 0.6, 1e30, 0.1, forchheimer=False, bc_x="nee", bc_y="nee", u_top=(0.07, 0.0),
+                         u_left=(0.0, 0.02))
+    p = 1.0 + 0.02 * rng.standard_normal((4, 5))
+    ux, uy = 0.03 * rng.standard_normal((2, 4, 5))
+    f = fl.equilibrium(p, ux, uy, flow.phi)
+    g = fl.wall_nodes(f, flow)
+    # top node (x = 2, y = 3) from (2, 2); left node (0, 1) from (1, 1); corner (0, 3) from (1, 2)
+    for (y, x), (yn, xn), uw in (((3, 2), (2, 2), (0.07, 0.0)), ((1, 0), (1, 1), (0.0, 0.02)), ((3, 0), (2, 1), (0.07, 0.0))):
+        want = fl.equilibrium(p[yn, xn], uw[0], uw[1], 0.6)
+        assert np.allclose(g[:, y, x], want, atol=1e-13), (y, x)
+    # interior untouched
+    assert np.array_equal(g[:, 1:3, 1:4], f[:, 1:3, 1:4])
