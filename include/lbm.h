@@ -55,6 +55,10 @@ extern "C" {
 #define LBM_PERIODIC 0u
 #define LBM_WALL 1u     /* halfway bounce-back, optionally moving (u_wall) */
 #define LBM_PRESSURE 2u /* x sides only: pressure columns by non-equilibrium extrapolation */
+#define LBM_NEE 3u      /* walls on the outermost nodes, treated by non-equilibrium extrapolation (the
+                         * paper's scheme, Sec. 3): f_b = f_eq(p_nb, u_w) + f_nb - f_eq(p_nb, u_nb), nb
+                         * the node inward along the normal; walls at distance nx - 1 / ny - 1;
+                         * isothermal flow only, not differentiable by lbm_adjoint, needs nx, ny >= 3 */
 
 /* wall indices of u_wall / T_wall */
 #define LBM_LEFT 0
@@ -72,7 +76,7 @@ typedef struct lbm_config {
   uint32_t abi_version; /* = LBM_ABI_VERSION */
   uint32_t nx, ny;      /* lattice size, 2..65535 each */
   uint32_t precision;   /* LBM_FP32 | LBM_FP16_DEV | LBM_BF16_DEV */
-  uint32_t bc_x, bc_y;  /* LBM_PERIODIC | LBM_WALL (| LBM_PRESSURE for bc_x) */
+  uint32_t bc_x, bc_y;  /* LBM_PERIODIC | LBM_WALL | LBM_NEE (| LBM_PRESSURE for bc_x) */
   int32_t forchheimer;  /* 1: F_phi = 1.75 / sqrt(150 phi^3) (Eq. 4); 0: F_phi = 0 (Brinkman) */
   int32_t thermal;      /* 1: couple the D2Q5 temperature equation (Appendix B, Sec. 3.4) */
   double nu, J, rho0, s_e, s_q;

@@ -301,7 +301,10 @@ int validate_config(const lbm_config* c) {
   if (c->abi_version != LBM_ABI_VERSION) return fail(LBM_EABI, "abi_version %u, library %u", c->abi_version, LBM_ABI_VERSION);
   if (c->nx < 2 || c->ny < 2 || c->nx > 65535 || c->ny > 65535) return fail(LBM_EINVAL, "nx, ny must be in [2, 65535]");
   if (c->precision > LBM_BF16_DEV) return fail(LBM_EINVAL, "unknown precision %u", c->precision);
-  if (c->bc_x > LBM_PRESSURE || c->bc_y > LBM_WALL) return fail(LBM_EINVAL, "unknown boundary kind");
+  if (c->bc_x > LBM_NEE || c->bc_y > LBM_NEE || c->bc_y == LBM_PRESSURE) return fail(LBM_EINVAL, "unknown boundary kind");
+  const bool nee = c->bc_x == LBM_NEE || c->bc_y == LBM_NEE;
+  if (nee && (c->nx < 3 || c->ny < 3)) return fail(LBM_EINVAL, "extrapolated wall nodes need nx, ny >= 3");
+  if (nee && c->thermal) return fail(LBM_EINVAL, "extrapolated wall nodes are for the isothermal flow only");
   if (c->bc_x == LBM_PRESSURE && c->nx < 3) return fail(LBM_EINVAL, "pressure columns need nx >= 3");
   if (!(c->nu > 0) || !(c->J > 0) || !(c->rho0 > 0)) return fail(LBM_EINVAL, "nu, J, rho0 must be positive");
   if (!(c->s_e > 0 && c->s_e < 2) || !(c->s_q > 0 && c->s_q < 2)) return fail(LBM_EINVAL, "s_e, s_q must be in (0, 2)");
@@ -799,6 +802,8 @@ int lbm_adjoint(lbm_ctx* c, int T, int loss_kind, const float* target_ux, const 
   if (loss_kind != LBM_LOSS_OUTLET_FLUX && loss_kind != LBM_LOSS_VELOCITY_MISFIT) return fail(LBM_EINVAL, "unknown loss kind");
   if (loss_kind == LBM_LOSS_VELOCITY_MISFIT && (!target_ux || !target_uy)) return fail(LBM_EINVAL, "misfit loss needs a target");
   if (thermal_of(c)) return fail(LBM_ESTATE, "the adjoint covers the isothermal flow step only");
+  if (c->cfg.bc_x == LBM_NEE || c->cfg.bc_y == LBM_NEE)
+    return fail(LBM_ESTATE, "the adjoint covers halfway walls, periodic sides and pressure columns, not extrapolated wall nodes");
   if (c->steps != 0 || c->history != 0)
     return fail(LBM_ESTATE, "lbm_adjoint differentiates from the initial state: call lbm_init_equilibrium first");
   const int64_t n = (int64_t)c->cfg.nx * c->cfg.ny;

@@ -209,11 +209,7 @@ template <int PREC, bool HET, bool THERMAL>
 __device__ __forceinline__ void gather_state(const StepParams& P, const void* src_v, const void* gsrc_v, int x, int y, float d[8],
                                              float gd[5], float& ay_out) {
   using T = typename Store<PREC>::T;
-  const T* src = static_cast<const T*>(src_v);
-  if (P.bc_x == BC_PRESSURE && (x == 0 || x == P.nx - 1))
-    pressure_column<PREC, HET>(P, src, x, y, d);
-  else
-    pull_cell<PREC>(P, src, x, y, d);
+  gather_cell<PREC, HET>(P, static_cast<const T*>(src_v), x, y, d);
   ay_out = P.ay;
   if (THERMAL) {
     pull_cell_g<PREC>(P, static_cast<const T*>(gsrc_v), x, y, gd);

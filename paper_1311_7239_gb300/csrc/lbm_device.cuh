@@ -21,7 +21,7 @@
 namespace lbm {
 
 enum : int { PREC_FP32 = 0, PREC_FP16 = 1, PREC_BF16 = 2 };
-enum : int { BC_PERIODIC = 0, BC_WALL = 1, BC_PRESSURE = 2 };
+enum : int { BC_PERIODIC = 0, BC_WALL = 1, BC_PRESSURE = 2, BC_NEE = 3 };
 
 // Constants of the two-cell collision (collide_pair), derived on the host from the configuration.
 // Moments there are taken of the stored (scaled) deviations s d, so every constant that turns a
@@ -525,6 +525,57 @@ __device__ __forceinline__ void pressure_column(const StepParams& P, const typen
   feq_dev_d2q8(mn.phip_dev, mn.ux, mn.uy, cn.inv_phi, P.rho0, en);
 #pragma unroll
   for (int i = 0; i < 8; ++i) d[i] = eb[i] + dn[i] - en[i];
+}
+
+// Wall node of a side with non-equilibrium extrapolation (BC_NEE, the paper's wall treatment of
+// Sec. 3): true for (x, y) on such a wall, with nb = (xn, yn) one step inward along the wall
+// normal and w the wall (0 left, 1 right, 2 bottom, 3 top).  Bottom/top walls own the corners,
+// whose nb is the diagonal node when the x sides are not periodic.
+__device__ __forceinline__ bool nee_node(const StepParams& P, int x, int y, int& xn, int& yn, int& w) {
+  if (P.bc_y == BC_NEE && (y == 0 || y == P.ny - 1)) {
+    yn = y == 0 ? 1 : P.ny - 2;
+    w = y == 0 ? 2 : 3;
+    xn = (P.bc_x != BC_PERIODIC && (x == 0 || x == P.nx - 1)) ? (x == 0 ? 1 : P.nx - 2) : x;
+    return true;
+  }
+  if (P.bc_x == BC_NEE && (x == 0 || x == P.nx - 1)) {
+    xn = x == 0 ? 1 : P.nx - 2;
+    yn = y;
+    w = x == 0 ? 0 : 1;
+    return true;
+  }
+  return false;
+}
+
+// d of a wall node: f_eq(p_nb, u_w; phi_b) + f_nb - f_eq(p_nb, u_nb; phi_nb) (pressure extrapolated
+// with zero normal gradient), in deviations.
+template <int PREC, bool HET>
+__device__ __forceinline__ void wall_node(const StepParams& P, const typename Store<PREC>::T* src, int x, int y, int xn, int yn,
+                                          int w, float d[8]) {
+  float dn[8];
+  pull_cell<PREC>(P, src, xn, yn, dn);
+  const Coef cn = coef_at<HET>(P, xn, yn);
+  const Coef cb = coef_at<HET>(P, x, y);
+  const Macro mn = macro_d2q8(dn, cn, P.ax, P.ay, P.rho0);
+  const float pn = (mn.phip_dev + P.p_rest) * cn.inv_phi;
+  float eb[8], en[8];
+  feq_dev_d2q8(cb.phi * pn - P.p_rest, __ldg(P.uw + 2 * w), __ldg(P.uw + 2 * w + 1), cb.inv_phi, P.rho0, eb);
+  feq_dev_d2q8(mn.phip_dev, mn.ux, mn.uy, cn.inv_phi, P.rho0, en);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) d[i] = eb[i] + dn[i] - en[i];
+}
+
+// Pre-collision state of any cell: the pull of Eq. 15 with its wall rules, or the extrapolated
+// state of a wall node or pressure column.
+template <int PREC, bool HET>
+__device__ __forceinline__ void gather_cell(const StepParams& P, const typename Store<PREC>::T* src, int x, int y, float d[8]) {
+  int xn, yn, w;
+  if (nee_node(P, x, y, xn, yn, w))
+    wall_node<PREC, HET>(P, src, x, y, xn, yn, w, d);
+  else if (P.bc_x == BC_PRESSURE && (x == 0 || x == P.nx - 1))
+    pressure_column<PREC, HET>(P, src, x, y, d);
+  else
+    pull_cell<PREC>(P, src, x, y, d);
 }
 
 }  // namespace lbm

@@ -32,11 +32,7 @@ __device__ void frame_step(const StepParams& P, const Frame& F, int k) {
   T* gdst = static_cast<T*>(P.gdst);
   float dc[8], gc[5];
   if (x < P.nx) {
-    const T* src = static_cast<const T*>(P.src);
-    if (P.bc_x == BC_PRESSURE && (x == 0 || x == P.nx - 1))
-      pressure_column<PREC, HET>(P, src, x, y, dc);
-    else
-      pull_cell<PREC>(P, src, x, y, dc);
+    gather_cell<PREC, HET>(P, static_cast<const T*>(P.src), x, y, dc);
     float ay = P.ay;
     if (THERMAL) {
       pull_cell_g<PREC>(P, static_cast<const T*>(P.gsrc), x, y, gc);
@@ -89,7 +85,7 @@ __device__ __forceinline__ void step_item_words(const StepParams& P, const Tilin
   gather4w<PREC, -1>(src + 5 * pl + rm, xl, P.pitch, lane, w[5]);  // e6 = (-1, 1)
   gather4w<PREC, -1>(src + 6 * pl + rp, xl, P.pitch, lane, w[6]);  // e7 = (-1,-1)
   gather4w<PREC, 1>(src + 7 * pl + rp, xl, P.pitch, lane, w[7]);   // e8 = ( 1,-1)
-  const bool wall_row = P.bc_y == BC_WALL && (y == 0 || y == P.ny - 1);
+  const bool wall_row = (P.bc_y == BC_WALL || P.bc_y == BC_NEE) && (y == 0 || y == P.ny - 1);
   if (!has_group || wall_row || x0 == 0 || x0 + C >= P.nx) return;
   float check = 0.0f;
 #pragma unroll
@@ -168,7 +164,7 @@ __device__ __forceinline__ void step_item(const StepParams& P, const Tiling& tl,
     gather4<PREC, 0>(gsrc + 4 * pl + rp, xl, P.pitch, lane, inv, g[4]);
   }
   // (after the shuffles) frame groups and groups past the row are not stored here
-  const bool wall_row = P.bc_y == BC_WALL && (y == 0 || y == P.ny - 1);
+  const bool wall_row = (P.bc_y == BC_WALL || P.bc_y == BC_NEE) && (y == 0 || y == P.ny - 1);
   if (!has_group || wall_row || x0 == 0 || x0 + C >= P.nx) return;
 
   float check = 0.0f;

@@ -98,7 +98,7 @@ __host__ __device__ inline Frame frame_of(int nx, int ny, int bc_y, int C) {
   Frame f;
   f.groups_per_row = (nx + C - 1) / C;
   f.cols = f.groups_per_row == 1 ? 1 : 2;
-  f.wall_rows = bc_y == BC_WALL ? 1 : 0;
+  f.wall_rows = (bc_y == BC_WALL || bc_y == BC_NEE) ? 1 : 0;
   f.count = (f.wall_rows ? 2 * f.groups_per_row : 0) + f.cols * (ny - (f.wall_rows ? 2 : 0));
   return f;
 }

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(PKG, "liblbm.so")
 
 ABI_VERSION = 1
 FP32, FP16_DEV, BF16_DEV = 0, 1, 2
-PERIODIC, WALL, PRESSURE = 0, 1, 2
+PERIODIC, WALL, PRESSURE, NEE = 0, 1, 2, 3
 LEFT, RIGHT, BOTTOM, TOP = 0, 1, 2, 3
 CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy
 LOSS_OUTLET_FLUX, LOSS_VELOCITY_MISFIT = 0, 1
