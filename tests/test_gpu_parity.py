@@ -38,6 +38,14 @@ ONE_STEP_CASES = {
     "tiny-2x3": Case(2, 3, bc_x="periodic", bc_y="wall", walls=CAV),
     "tiny-3x2-walls": Case(3, 2, bc_x="wall", bc_y="wall", walls=CAV),
     "brinkman-no-forch": Case(64, 8, forch=False, phi=0.1, K=40.96, ax=1e-5),
+    # wall nodes with non-equilibrium extrapolation (LBM_NEE)
+    "nee-cavity-moving-walls-het": Case(37, 21, bc_x="nee", bc_y="nee", het=True,
+                                        walls={"top": (0.1, 0.0), "bottom": (0.0, 0.01), "left": (0.0, 0.02), "right": (0.0, -0.03)}),
+    "nee-channel-lid": Case(33, 17, bc_x="periodic", bc_y="nee", walls={"top": (0.05, 0.0)}, ax=1e-4),
+    "nee-walls-pressure-het": Case(41, 13, bc_x="pressure", bc_y="nee", het=True, p_in=1.01, p_out=0.99),
+    "nee-x-halfway-y": Case(20, 9, bc_x="nee", bc_y="wall", walls={"left": (0.0, 0.05), "top": (0.03, 0.0)}),
+    "nee-ragged-3-tiles": Case(1100, 6, bc_x="nee", bc_y="nee", walls=CAV, phi=0.7, K=5.0),
+    "nee-tiny-3x3": Case(3, 3, bc_x="nee", bc_y="nee", walls=CAV),
 }
 
 
@@ -231,13 +239,14 @@ def test_reduced_precision_long_rows(lbm, accuracy, prec, bound):
     assert e_u <= bound and e_p <= bound, (e_u, e_p)
 
 
+@pytest.mark.parametrize("bc", ["periodic", "nee"])
 @pytest.mark.parametrize("prec", [1, 2])
-def test_reduced_precision_one_step_long_rows(lbm, prec):
+def test_reduced_precision_one_step_long_rows(lbm, prec, bc):
     """One step with 16-bit storage from a random state against the oracle, cell by cell, on a
     periodic 1100 x 7 channel with a moving top wall (three items per row, ragged), to the
     storage's rounding, twice (the imported state and the result): FP16 2^-11 of |d| <= 0.1 at
     scale 2^10, BF16 2^-8."""
-    case = Case(1100, 7, bc_x="periodic", bc_y="wall", walls={"top": (0.05, 0.0)}, ax=1e-4, precision=prec)
+    case = Case(1100, 7, bc_x=bc, bc_y="wall" if bc == "periodic" else "nee", walls={"top": (0.05, 0.0)}, ax=1e-4, precision=prec)
     flow = case.flow()
     f0 = random_state(flow, seed=3)
     with case.lattice(lbm) as lat:
@@ -325,3 +334,57 @@ def test_viscosity_ratio_field_one_step_and_trajectory(lbm):
     uxo, uyo, po = fl.macroscopic(f, flow)
     assert rel_l2(np.stack([ux, uy]), np.stack([uxo, uyo])) <= 1e-5
     assert rel_l2(p, po) <= 1e-5
+
+
+def test_nee_lid_cavity_trajectory(lbm, accuracy):
+    """The paper's lid-driven porous cavity (Sec. 3.3: eps = 0.1, Re = 10, nu = 0.256 on 128 x 128,
+    Da = 1e-2) with its own wall treatment, extrapolated wall nodes on the four sides (H = 127)."""
+    L, nu = 128, 0.256
+    u0 = 10 * nu / (L - 1)
+    case = Case(L, L, nu=nu, phi=0.1, K=1e-2 * (L - 1) ** 2, bc_x="nee", bc_y="nee", walls={"top": (u0, 0.0)})
+    e_u, e_p = _trajectory(lbm, case, 600)
+    accuracy.append({"case": "lid-driven porous cavity 128x128 with extrapolated wall nodes, eps 0.1, Da 1e-2, Re 10",
+                     "precision": "fp32", "steps": 600, "rel_l2_u": e_u, "rel_l2_p": e_p, "bound": 1e-5})
+    assert e_u <= 1e-5 and e_p <= 1e-5, (e_u, e_p)
+
+
+def test_nee_poiseuille_steady_state_matches_eq24(lbm):
+    """Porous Poiseuille between wall nodes (H = ny - 1) run to steady state on the GPU against the
+    profile behind Eq. 24 (second-order scheme: 1.5e-3 at ny = 65 in the oracle)."""
+    N, phi, nu = 65, 0.1, 0.3
+    H = N - 1
+    K = 0.01 * H * H
+    th_ = np.sqrt(phi / K)
+    u0 = nu / H
+    G = u0 * nu / (K * (1 - 1 / np.cosh(th_ * H / 2)))
+    cfg = lbm.default_config(nx=8, ny=N, bc_x=lbm.PERIODIC, bc_y=lbm.NEE, nu=nu, phi=phi, K=K, forchheimer=0, ax=G, p_rest=phi)
+    lat = lbm.Lattice(cfg)
+    try:
+        for _ in range(400):
+            lat.step(100)
+            if lat.residual() < 1e-11:
+                break
+        ux = lat.macros()[1].cpu().numpy()[:, 0].astype(np.float64)
+    finally:
+        lat.close()
+    y = np.arange(N, dtype=np.float64)
+    exact = G * K / nu * (1 - np.cosh(th_ * (y - H / 2)) / np.cosh(th_ * H / 2))
+    err = np.abs(ux - exact).max() / exact.max()
+    assert err < 2e-3, err
+
+
+def test_nee_rejections(lbm):
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.Lattice(lbm.default_config(nx=8, ny=2, bc_y=lbm.NEE))
+    assert e.value.code == lbm.EINVAL
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.Lattice(lbm.default_config(nx=8, ny=8, bc_x=lbm.WALL, bc_y=lbm.NEE, thermal=1, tau_T=1.0))
+    assert e.value.code == lbm.EINVAL
+    lat = lbm.Lattice(lbm.default_config(nx=8, ny=8, bc_y=lbm.NEE))
+    try:
+        lat.init_equilibrium(1.0, 0.0, 0.0)
+        with pytest.raises(lbm.LbmError) as e:
+            lat.adjoint(4, "flux")
+        assert e.value.code == lbm.ESTATE
+    finally:
+        lat.close()
