@@ -330,6 +330,28 @@ def pressure_columns(f, flow: Flow, phi=None, K=None):
     return out
 
 
+def wall_node_list(flow: Flow):
+    """Wall nodes of the 'nee' sides as index arrays (y, x, y_nb, x_nb, side), side 0..3 =
+    left, right, bottom, top; bottom/top walls own the corners, whose nb is the diagonal node
+    when the x sides are not periodic."""
+    ny, nx = flow.ny, flow.nx
+    nodes = []
+    if flow.bc_x == "nee":
+        for y in range(ny):
+            if flow.bc_y == "nee" and y in (0, ny - 1):
+                continue
+            nodes.append((y, 0, y, 1, 0))
+            nodes.append((y, nx - 1, y, nx - 2, 1))
+    if flow.bc_y == "nee":
+        for x in range(nx):
+            xn = x
+            if flow.bc_x != "periodic" and x in (0, nx - 1):
+                xn = 1 if x == 0 else nx - 2
+            nodes.append((0, x, 1, xn, 2))
+            nodes.append((ny - 1, x, ny - 2, xn, 3))
+    return tuple(np.array([n[k] for n in nodes], dtype=np.int64) for k in range(5))
+
+
 def wall_nodes(f, flow: Flow, phi=None, K=None):
     """Non-equilibrium extrapolation on the wall nodes of 'nee' sides (Sec. 3's wall treatment).
 
@@ -340,26 +362,11 @@ def wall_nodes(f, flow: Flow, phi=None, K=None):
     phi = flow.phi if phi is None else phi
     K = flow.K if K is None else K
     ax, ay = _accel(flow, f[0])
-    ny, nx = flow.ny, flow.nx
-    nodes = []  # (y, x, yn, xn, u_w)
-    if flow.bc_x == "nee":
-        for y in range(ny):
-            if flow.bc_y == "nee" and y in (0, ny - 1):
-                continue
-            nodes.append((y, 0, y, 1, flow.u_left))
-            nodes.append((y, nx - 1, y, nx - 2, flow.u_right))
-    if flow.bc_y == "nee":
-        for x in range(nx):
-            xn = x
-            if flow.bc_x != "periodic" and x in (0, nx - 1):
-                xn = 1 if x == 0 else nx - 2
-            nodes.append((0, x, 1, xn, flow.u_bottom))
-            nodes.append((ny - 1, x, ny - 2, xn, flow.u_top))
     out = f.astype(np.result_type(f, phi, K), copy=True)
-    if not nodes:
+    yb, xb, yn, xn, side = wall_node_list(flow)
+    if yb.size == 0:
         return out
-    yb, xb, yn, xn = (np.array([n[k] for n in nodes]) for k in range(4))
-    uw = np.array([n[4] for n in nodes], dtype=np.float64)
+    uw = np.array([flow.u_left, flow.u_right, flow.u_bottom, flow.u_top], dtype=np.float64)[side]
     fn = f[:, yn, xn]
     ux, uy = velocity(fn, phi[yn, xn], K[yn, xn], flow.nu, flow.rho0, flow.forchheimer, ax[yn, xn], ay[yn, xn])
     pn = pressure(fn, ux, uy, phi[yn, xn], flow.rho0)

@@ -11,11 +11,14 @@ Coupled step (readings listed in the design doc): from the pre-collision f(t), g(t):
     both streams (Eq. 15 / Eq. B.2).
 Thermal walls: a wall with a prescribed temperature T_w uses anti-bounce-back,
 g_opp(i)(x, t+1) = -g_i+(x, t) + 2 w_i T_w, where w_i T is the u = 0 equilibrium of Eq. B.6
-(w_i = 1/5 at varpi = 0); an adiabatic wall uses plain bounce-back.
+(w_i = 1/5 at varpi = 0); an adiabatic wall uses plain bounce-back.  On the wall nodes of 'nee'
+sides (the paper's extrapolation, Sec. 3) g_b = g_eq(T_b, u_w) + g_nb - g_eq(T_nb, u_nb), with
+T_b = T_w for a prescribed temperature and T_b = T_nb (zero normal gradient) for an adiabatic
+wall, and u_nb the flow velocity at nb with the buoyancy of T_nb.
 """
 from __future__ import annotations
 
-from dataclasses import dataclass
+from dataclasses import dataclass, replace
 
 import numpy as np
 
@@ -101,9 +104,9 @@ def stream(g_plus, flow: fl.Flow, th: Thermal):
     for i in range(1, 5):
         tx = xs + E5[i, 0]
         ty = ys + E5[i, 1]
-        if flow.bc_x == "periodic":
+        if flow.bc_x in ("periodic", "nee"):  # 'nee' wall nodes are overwritten by wall_nodes
             tx = tx % nx
-        if flow.bc_y == "periodic":
+        if flow.bc_y in ("periodic", "nee"):
             ty = ty % ny
         inside = (tx >= 0) & (tx < nx) & (ty >= 0) & (ty < ny)
         out[i, ty[inside], tx[inside]] = g_plus[i, ys[inside], xs[inside]]
@@ -123,22 +126,55 @@ def stream(g_plus, flow: fl.Flow, th: Thermal):
     return out
 
 
-def initial_state(flow: fl.Flow, th: Thermal, T_init=None):
-    """g at equilibrium (Eq. B.6) with u = 0 and T = T_init (default T0)."""
+def equilibrium(T, ux, uy, th: Thermal):
+    """g_eq = N^-1 n_eq (Eq. B.6)."""
+    return np.einsum("ik,k...->i...", N_INV, equilibrium_moments(T, ux, uy, th))
+
+
+def _buoyant(flow: fl.Flow, th: Thermal, T):
+    """The flow problem with a = a0 + g beta (T - T0) j as a field (Sec. 3.4)."""
+    ax0, ay0 = fl._accel(flow, T)
+    return replace(flow, accel=np.stack([ax0 + 0.0 * T, ay0 + th.g_beta * (T - th.T0)]))
+
+
+def boundary_nodes(f, g, flow: fl.Flow, th: Thermal):
+    """Wall nodes of 'nee' sides for both equations after streaming (flow: fl.wall_nodes with the
+    buoyancy of the streamed temperature; temperature: see the module docstring)."""
+    if "nee" not in (flow.bc_x, flow.bc_y):
+        return fl.boundary_nodes(f, flow), g
+    bflow = _buoyant(flow, th, temperature(g))
+    yb, xb, yn, xn, side = fl.wall_node_list(bflow)
+    fn, gn = f[:, yn, xn], g[:, yn, xn]
+    ax, ay = fl._accel(bflow, f[0])
+    ux, uy = fl.velocity(fn, flow.phi[yn, xn], flow.K[yn, xn], flow.nu, flow.rho0, flow.forchheimer, ax[yn, xn], ay[yn, xn])
+    Tn = temperature(gn)
+    Tw = [th.T_left, th.T_right, th.T_bottom, th.T_top]
+    Tb = np.array([Tn[k] if Tw[side[k]] is None else Tw[side[k]] for k in range(side.size)])
+    uw = np.array([flow.u_left, flow.u_right, flow.u_bottom, flow.u_top], dtype=np.float64)[side]
+    g_out = g.copy()
+    g_out[:, yb, xb] = equilibrium(Tb, uw[:, 0], uw[:, 1], th) + gn - equilibrium(Tn, ux, uy, th)
+    return fl.boundary_nodes(f, bflow), g_out
+
+
+def initial_state(flow: fl.Flow, th: Thermal, T_init=None, f=None):
+    """g at equilibrium (Eq. B.6) with u = 0 and T = T_init (default T0); with 'nee' sides its wall
+    nodes follow the extrapolation from the flow state f (default: the flow's initial state)."""
     T = np.full((flow.ny, flow.nx), th.T0 if T_init is None else float(T_init))
     z = np.zeros_like(T)
-    return np.einsum("ik,k...->i...", N_INV, equilibrium_moments(T, z, z, th))
+    g = equilibrium(T, z, z, th)
+    if "nee" in (flow.bc_x, flow.bc_y):
+        g = boundary_nodes(fl.initial_state(flow) if f is None else f, g, flow, th)[1]
+    return g
 
 
 def coupled_step(f, g, flow: fl.Flow, th: Thermal):
     """One step of the flow (Eq. 6) and temperature (Eq. B.2) equations with buoyancy."""
     T = temperature(g)
-    ax0, ay0 = fl._accel(flow, T)
-    ax = ax0 + 0.0 * T
-    ay = ay0 + th.g_beta * (T - th.T0)
+    bflow = _buoyant(flow, th, T)
+    ax, ay = fl._accel(bflow, T)
     f_plus, ux, uy, _ = fl.collide(f, flow, ax=ax, ay=ay)
     g_plus = collide(g, ux, uy, th)
-    return fl.stream(f_plus, flow), stream(g_plus, flow, th)
+    return boundary_nodes(fl.stream(f_plus, flow), stream(g_plus, flow, th), flow, th)
 
 
 def coupled_macroscopic(f, g, flow: fl.Flow, th: Thermal):
@@ -166,6 +202,17 @@ def nusselt_left_wall(T, T_wall, T_hot, T_cold, width):
         c[k] = (-(others[0]) - (others[1])) / denom
     dTdx = c[0] * T_wall + c[1] * T[:, 0] + c[2] * T[:, 1]
     return float(-np.mean(dTdx) * width / (T_hot - T_cold))
+
+
+def nusselt_wall_nodes(T, side, T_hot, T_cold):
+    """Average Nusselt number of the x = 0 (side 0) or x = nx-1 (side 1) wall when the walls lie
+    on the outermost nodes: Nu = (L / dT) * mean_y(-+ dT/dx at the wall node), L = nx - 1, with the
+    second-order one-sided difference dT/dx ~ (-3 T_0 + 4 T_1 - T_2) / 2 (mirrored for side 1)."""
+    Tn = T if side == 0 else T[:, ::-1]
+    dTds = (-3.0 * Tn[:, 0] + 4.0 * Tn[:, 1] - Tn[:, 2]) / 2.0
+    L = T.shape[1] - 1
+    # s runs into the fluid: -dT/dx = -dT/ds at the left wall, +dT/ds at the right one
+    return float((-1.0 if side == 0 else 1.0) * np.mean(dTds) * L / (T_hot - T_cold))
 
 
 def parameters_from_Ra(L, Ra, Pr, Ma, J=1.0, sigma=1.0, gamma=1.0, varpi=0.0, dT=20.0):

@@ -113,3 +113,40 @@ def test_buoyancy_drives_no_flow_in_stably_stratified_rest_state():
     y = np.arange(ny) + 0.5
     assert np.allclose(T[:, 0], 1.0 + 20.0 * y / ny, atol=1e-8)
     assert np.abs(ux).max() < 1e-12 and np.abs(uy).max() < 1e-10
+
+
+def test_conduction_between_extrapolated_wall_nodes_is_linear_and_nu_is_one():
+    """Isothermal wall nodes ('nee' x sides, the paper's extrapolation) at T_h and T_c, no flow
+    (g beta = 0): the steady temperature is linear between the wall nodes (H = nx - 1) and both
+    walls' Nusselt numbers are 1."""
+    L = 17
+    nu, tau_v, tau_T, gb = th.parameters_from_Ra(L - 1, 1e3, 1.0, 0.1)
+    flow = fl.Flow(nx=L, ny=6, phi=np.full((6, L), 0.6), K=np.full((6, L), 1e-2 * (L - 1) ** 2), nu=nu, bc_x="nee",
+                   bc_y="periodic")
+    tp = th.Thermal(tau_T=tau_T, g_beta=0.0, T0=11.0, T_left=21.0, T_right=1.0)
+    f = fl.initial_state(flow)
+    g = th.initial_state(flow, tp, f=f)
+    for _ in range(6000):
+        f, g = th.coupled_step(f, g, flow, tp)
+    T = th.coupled_macroscopic(f, g, flow, tp)[3]
+    lin = 21.0 - 20.0 * np.arange(L) / (L - 1)
+    assert np.abs(T - lin).max() < 1e-9
+    assert abs(th.nusselt_wall_nodes(T, 0, 21.0, 1.0) - 1.0) < 1e-9
+    assert abs(th.nusselt_wall_nodes(T, 1, 21.0, 1.0) - 1.0) < 1e-9
+
+
+def test_adiabatic_extrapolated_wall_node_copies_the_neighbour_temperature():
+    """An adiabatic 'nee' wall node takes T_b = T_nb exactly (g_eq(T_nb, u_w) + g_nb - g_eq(T_nb, u_nb)
+    sums to T_nb); an isothermal one takes T_w."""
+    nx, ny = 6, 5
+    flow = fl.Flow(nx=nx, ny=ny, phi=np.full((ny, nx), 0.6), K=np.full((ny, nx), 4.0), nu=0.1, bc_x="nee", bc_y="nee",
+                   u_top=(0.05, 0.0))
+    tp = th.Thermal(tau_T=0.8, g_beta=1e-4, T0=11.0, T_left=21.0, T_right=1.0)
+    rng = np.random.default_rng(4)
+    f = fl.equilibrium(1.0 + 0.01 * rng.standard_normal((ny, nx)), *(0.02 * rng.standard_normal((2, ny, nx))), flow.phi)
+    g = th.equilibrium(11.0 + rng.standard_normal((ny, nx)), *(0.02 * rng.standard_normal((2, ny, nx))), tp)
+    g2 = th.boundary_nodes(f, g, flow, tp)[1]
+    T, T2 = th.temperature(g), th.temperature(g2)
+    assert np.allclose(T2[0, 1:-1], T[1, 1:-1]) and np.allclose(T2[-1, 1:-1], T[-2, 1:-1])  # adiabatic bottom/top
+    assert np.allclose(T2[0, 0], T[1, 1]) and np.allclose(T2[-1, -1], T[-2, -2])  # corners: y walls, diagonal nb
+    assert np.allclose(T2[1:-1, 0], 21.0) and np.allclose(T2[1:-1, -1], 1.0)  # isothermal sides
