@@ -57,8 +57,9 @@ extern "C" {
 #define LBM_PRESSURE 2u /* x sides only: pressure columns by non-equilibrium extrapolation */
 #define LBM_NEE 3u      /* walls on the outermost nodes, treated by non-equilibrium extrapolation (the
                          * paper's scheme, Sec. 3): f_b = f_eq(p_nb, u_w) + f_nb - f_eq(p_nb, u_nb), nb
-                         * the node inward along the normal; walls at distance nx - 1 / ny - 1;
-                         * isothermal flow only, not differentiable by lbm_adjoint, needs nx, ny >= 3 */
+                         * the node inward along the normal; walls at distance nx - 1 / ny - 1; a
+                         * temperature wall node takes g_eq(T_w or T_nb, u_w) + g_nb - g_eq(T_nb, u_nb);
+                         * not differentiable by lbm_adjoint; needs nx, ny >= 3 */
 
 /* wall indices of u_wall / T_wall */
 #define LBM_LEFT 0
@@ -213,8 +214,10 @@ LBM_API int lbm_adjoint_step(lbm_ctx* ctx, int T, int loss_kind, const float* ta
 LBM_API int lbm_release_workspace(lbm_ctx* ctx);
 
 /* Average Nusselt number of a wall with a prescribed temperature (side = LBM_LEFT or
- * LBM_RIGHT): Nu = (nx / (T_hot - T_cold)) * mean_y(-+ dT/dx at the wall), dT/dx from the
- * parabola through the wall value and the two nearest cells; the sum is FP64.  Waits. */
+ * LBM_RIGHT): Nu = (L / (T_hot - T_cold)) * mean_y(-+ dT/dx at the wall).  Halfway walls
+ * (LBM_WALL): L = nx, dT/dx from the parabola through the wall value and the two nearest cells;
+ * wall nodes (LBM_NEE): L = nx - 1, dT/dx = (-3 T_0 + 4 T_1 - T_2) / 2, over the rows 1..ny-2
+ * when the bottom/top walls are wall nodes too (they own the corners).  FP64 sum.  Waits. */
 LBM_API int lbm_nusselt(lbm_ctx* ctx, int side, double* nu);
 
 /* ---------------------------------------------------------------------------------------------

@@ -204,10 +204,13 @@ def nusselt_left_wall(T, T_wall, T_hot, T_cold, width):
     return float(-np.mean(dTdx) * width / (T_hot - T_cold))
 
 
-def nusselt_wall_nodes(T, side, T_hot, T_cold):
+def nusselt_wall_nodes(T, side, T_hot, T_cold, corners_on_y_walls=True):
     """Average Nusselt number of the x = 0 (side 0) or x = nx-1 (side 1) wall when the walls lie
     on the outermost nodes: Nu = (L / dT) * mean_y(-+ dT/dx at the wall node), L = nx - 1, with the
-    second-order one-sided difference dT/dx ~ (-3 T_0 + 4 T_1 - T_2) / 2 (mirrored for side 1)."""
+    second-order one-sided difference dT/dx ~ (-3 T_0 + 4 T_1 - T_2) / 2 (mirrored for side 1).
+    When the bottom/top walls are wall nodes too they own the corner nodes, whose rows are left out."""
+    if corners_on_y_walls:
+        T = T[1:-1]
     Tn = T if side == 0 else T[:, ::-1]
     dTds = (-3.0 * Tn[:, 0] + 4.0 * Tn[:, 1] - Tn[:, 2]) / 2.0
     L = T.shape[1] - 1

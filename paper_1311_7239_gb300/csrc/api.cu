@@ -304,7 +304,6 @@ int validate_config(const lbm_config* c) {
   if (c->bc_x > LBM_NEE || c->bc_y > LBM_NEE || c->bc_y == LBM_PRESSURE) return fail(LBM_EINVAL, "unknown boundary kind");
   const bool nee = c->bc_x == LBM_NEE || c->bc_y == LBM_NEE;
   if (nee && (c->nx < 3 || c->ny < 3)) return fail(LBM_EINVAL, "extrapolated wall nodes need nx, ny >= 3");
-  if (nee && c->thermal) return fail(LBM_EINVAL, "extrapolated wall nodes are for the isothermal flow only");
   if (c->bc_x == LBM_PRESSURE && c->nx < 3) return fail(LBM_EINVAL, "pressure columns need nx >= 3");
   if (!(c->nu > 0) || !(c->J > 0) || !(c->rho0 > 0)) return fail(LBM_EINVAL, "nu, J, rho0 must be positive");
   if (!(c->s_e > 0 && c->s_e < 2) || !(c->s_q > 0 && c->s_q < 2)) return fail(LBM_EINVAL, "s_e, s_q must be in (0, 2)");
@@ -719,7 +718,7 @@ int lbm_nusselt(lbm_ctx* c, int side, double* nu) {
   if (!c || !nu) return fail(LBM_EINVAL, "null argument");
   if (!thermal_of(c)) return fail(LBM_ESTATE, "context has no temperature field");
   if (side != LBM_LEFT && side != LBM_RIGHT) return fail(LBM_EINVAL, "side must be LBM_LEFT or LBM_RIGHT");
-  if (c->cfg.bc_x != LBM_WALL || isnan(c->cfg.T_wall[LBM_LEFT]) || isnan(c->cfg.T_wall[LBM_RIGHT]))
+  if ((c->cfg.bc_x != LBM_WALL && c->cfg.bc_x != LBM_NEE) || isnan(c->cfg.T_wall[LBM_LEFT]) || isnan(c->cfg.T_wall[LBM_RIGHT]))
     return fail(LBM_ESTATE, "the Nusselt number needs isothermal left and right walls");
   const double dT = c->cfg.T_wall[LBM_LEFT] - c->cfg.T_wall[LBM_RIGHT];
   if (dT == 0) return fail(LBM_EINVAL, "equal wall temperatures");
@@ -729,8 +728,10 @@ int lbm_nusselt(lbm_ctx* c, int side, double* nu) {
   double s = 0;
   LBM_CUDA(cudaMemcpyAsync(&s, out, sizeof(s), cudaMemcpyDeviceToHost, c->stream), "read of Nusselt sum");
   LBM_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
-  const double mean = s / (double)c->cfg.ny;
-  *nu = (side == LBM_LEFT ? -1.0 : 1.0) * (double)c->cfg.nx / dT * mean;
+  const int rows = (int)c->cfg.ny - (c->cfg.bc_x == LBM_NEE && c->cfg.bc_y == LBM_NEE ? 2 : 0);
+  const double mean = s / (double)rows;
+  const double width = c->cfg.bc_x == LBM_NEE ? (double)c->cfg.nx - 1.0 : (double)c->cfg.nx;  // wall-to-wall distance
+  *nu = (side == LBM_LEFT ? -1.0 : 1.0) * width / dT * mean;
   return check_error_word(c);
 }
 

@@ -106,18 +106,6 @@ __global__ void k_init_flow(const StepParams P, float p0, float ux0, float uy0, 
   }
 }
 
-// thermal equilibrium (Eq. B.6) deviation from T0/5
-__device__ __forceinline__ void geq_dev(const StepParams& P, float T, float ux, float uy, float out[5]) {
-  const float a = 0.2f * T - 0.2f * P.T0;
-  const float b = 0.05f * P.varpi * T;
-  const float hx = 0.5f * ux * T * P.inv_sigma, hy = 0.5f * uy * T * P.inv_sigma;
-  out[0] = a - 4.0f * b;
-  out[1] = a + hx + b;
-  out[2] = a + hy + b;
-  out[3] = a - hx + b;
-  out[4] = a - hy + b;
-}
-
 // Inverse of the temperature gather for one slot, given the pre-collision deviations z of the
 // target cell (inside) or of the own cell (wall).
 __device__ __forceinline__ float g_slot(const StepParams& P, int x, int y, int j, const float* z_own, const float* z_tgt,
@@ -209,11 +197,12 @@ template <int PREC, bool HET, bool THERMAL>
 __device__ __forceinline__ void gather_state(const StepParams& P, const void* src_v, const void* gsrc_v, int x, int y, float d[8],
                                              float gd[5], float& ay_out) {
   using T = typename Store<PREC>::T;
-  gather_cell<PREC, HET>(P, static_cast<const T*>(src_v), x, y, d);
   ay_out = P.ay;
   if (THERMAL) {
-    pull_cell_g<PREC>(P, static_cast<const T*>(gsrc_v), x, y, gd);
+    gather_cell_thermal<PREC, HET>(P, static_cast<const T*>(src_v), static_cast<const T*>(gsrc_v), x, y, d, gd);
     ay_out += P.g_beta * (gd[0] + gd[1] + gd[2] + gd[3] + gd[4]);
+  } else {
+    gather_cell<PREC, HET>(P, static_cast<const T*>(src_v), x, y, d);
   }
 }
 
@@ -335,6 +324,18 @@ __global__ void k_nusselt(const StepParams P, int side, double* __restrict__ out
   double s = 0.0, unused = 0.0;
   const int xa = side == 0 ? 0 : P.nx - 1;
   const int xb = side == 0 ? 1 : P.nx - 2;
+  if (P.bc_x == BC_NEE) {  // walls on the nodes x = 0, nx-1: dT/ds = (-3 T_0 + 4 T_1 - T_2) / 2
+    const int xc = side == 0 ? 2 : P.nx - 3;
+    const int y0 = P.bc_y == BC_NEE ? 1 : 0;  // corner rows belong to extrapolated bottom/top walls
+    for (int y = y0 + (int)threadIdx.x; y < P.ny - y0; y += blockDim.x) {
+      const double Ta = temperature_at<PREC>(P, g, xa, y), Tb = temperature_at<PREC>(P, g, xb, y);
+      const double Tc = temperature_at<PREC>(P, g, xc, y);
+      s += (-3.0 * Ta + 4.0 * Tb - Tc) / 2.0;
+    }
+    block_sum2(s, unused);
+    if (threadIdx.x == 0) out[0] = s;
+    return;
+  }
   for (int y = threadIdx.x; y < P.ny; y += blockDim.x) {
     float ga[5], gb[5];
     pull_cell_g<PREC>(P, g, xa, y, ga);

@@ -548,18 +548,24 @@ __device__ __forceinline__ bool nee_node(const StepParams& P, int x, int y, int&
 }
 
 // d of a wall node: f_eq(p_nb, u_w; phi_b) + f_nb - f_eq(p_nb, u_nb; phi_nb) (pressure extrapolated
-// with zero normal gradient), in deviations.
+// with zero normal gradient), in deviations; ay_nb is a_y at nb (with its buoyancy in a thermal
+// context), u_nb is returned.
 template <int PREC, bool HET>
 __device__ __forceinline__ void wall_node(const StepParams& P, const typename Store<PREC>::T* src, int x, int y, int xn, int yn,
-                                          int w, float d[8]) {
+                                          int w, float ay_nb, float d[8], float& ux_nb, float& uy_nb) {
   float dn[8];
   pull_cell<PREC>(P, src, xn, yn, dn);
   const Coef cn = coef_at<HET>(P, xn, yn);
   const Coef cb = coef_at<HET>(P, x, y);
-  const Macro mn = macro_d2q8(dn, cn, P.ax, P.ay, P.rho0);
-  const float pn = (mn.phip_dev + P.p_rest) * cn.inv_phi;
+  const Macro mn = macro_d2q8(dn, cn, P.ax, ay_nb, P.rho0);
+  ux_nb = mn.ux;
+  uy_nb = mn.uy;
+  // phi_b p_nb - p_rest = phi_nb p_nb - p_rest + (phi_b / phi_nb - 1) phi_nb p_nb, kept in deviations
+  // (exact for phi_b = phi_nb; forming p_nb itself would add p_rest to a small deviation)
+  const float dr = (cb.phi - cn.phi) * cn.inv_phi;
+  const float phip_b = mn.phip_dev + dr * (mn.phip_dev + P.p_rest);
   float eb[8], en[8];
-  feq_dev_d2q8(cb.phi * pn - P.p_rest, __ldg(P.uw + 2 * w), __ldg(P.uw + 2 * w + 1), cb.inv_phi, P.rho0, eb);
+  feq_dev_d2q8(phip_b, __ldg(P.uw + 2 * w), __ldg(P.uw + 2 * w + 1), cb.inv_phi, P.rho0, eb);
   feq_dev_d2q8(mn.phip_dev, mn.ux, mn.uy, cn.inv_phi, P.rho0, en);
 #pragma unroll
   for (int i = 0; i < 8; ++i) d[i] = eb[i] + dn[i] - en[i];
@@ -570,12 +576,63 @@ __device__ __forceinline__ void wall_node(const StepParams& P, const typename St
 template <int PREC, bool HET>
 __device__ __forceinline__ void gather_cell(const StepParams& P, const typename Store<PREC>::T* src, int x, int y, float d[8]) {
   int xn, yn, w;
+  float uxn, uyn;
   if (nee_node(P, x, y, xn, yn, w))
-    wall_node<PREC, HET>(P, src, x, y, xn, yn, w, d);
+    wall_node<PREC, HET>(P, src, x, y, xn, yn, w, P.ay, d, uxn, uyn);
   else if (P.bc_x == BC_PRESSURE && (x == 0 || x == P.nx - 1))
     pressure_column<PREC, HET>(P, src, x, y, d);
   else
     pull_cell<PREC>(P, src, x, y, d);
+}
+
+// thermal equilibrium (Eq. B.6) deviation from T0/5
+__device__ __forceinline__ void geq_dev(const StepParams& P, float T, float ux, float uy, float out[5]) {
+  const float a = 0.2f * T - 0.2f * P.T0;
+  const float b = 0.05f * P.varpi * T;
+  const float hx = 0.5f * ux * T * P.inv_sigma, hy = 0.5f * uy * T * P.inv_sigma;
+  out[0] = a - 4.0f * b;
+  out[1] = a + hx + b;
+  out[2] = a + hy + b;
+  out[3] = a - hx + b;
+  out[4] = a - hy + b;
+}
+
+// Pre-collision temperature of a cell: on a wall node of an extrapolated side the wall temperature
+// (isothermal wall) or that of its inner neighbour (adiabatic wall), which is what the node's
+// extrapolated populations sum to.
+template <int PREC>
+__device__ __forceinline__ double temperature_at(const StepParams& P, const typename Store<PREC>::T* gsrc, int x, int y) {
+  int xn = x, yn = y, w = 0;
+  if (nee_node(P, x, y, xn, yn, w) && P.Tdir[w]) return (double)P.Tw[w];
+  float g[5];
+  pull_cell_g<PREC>(P, gsrc, xn, yn, g);
+  return (double)P.T0 + ((double)g[0] + g[1] + g[2] + g[3] + g[4]);
+}
+
+// Pre-collision flow (d) and temperature (g, deviations from T0/5) state of a cell of a thermal
+// context.  On a wall node of an extrapolated side, g = g_eq(T_b, u_w) + g_nb - g_eq(T_nb, u_nb)
+// with T_b the wall temperature (isothermal wall) or T_nb (adiabatic wall), and the flow part
+// uses the velocity of nb with the buoyancy of T_nb.
+template <int PREC, bool HET>
+__device__ __forceinline__ void gather_cell_thermal(const StepParams& P, const typename Store<PREC>::T* src,
+                                                    const typename Store<PREC>::T* gsrc, int x, int y, float d[8], float g[5]) {
+  int xn, yn, w;
+  if (nee_node(P, x, y, xn, yn, w)) {
+    float gn[5];
+    pull_cell_g<PREC>(P, gsrc, xn, yn, gn);
+    const float Tn = gn[0] + gn[1] + gn[2] + gn[3] + gn[4];  // T_nb - T0
+    float uxn, uyn;
+    wall_node<PREC, HET>(P, src, x, y, xn, yn, w, P.ay + P.g_beta * Tn, d, uxn, uyn);
+    const float Tb = P.Tdir[w] ? P.Tw[w] - P.T0 : Tn;
+    float eb[5], en[5];
+    geq_dev(P, P.T0 + Tb, __ldg(P.uw + 2 * w), __ldg(P.uw + 2 * w + 1), eb);
+    geq_dev(P, P.T0 + Tn, uxn, uyn, en);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) g[i] = eb[i] + gn[i] - en[i];
+  } else {
+    gather_cell<PREC, HET>(P, src, x, y, d);
+    pull_cell_g<PREC>(P, gsrc, x, y, g);
+  }
 }
 
 }  // namespace lbm

@@ -32,11 +32,12 @@ __device__ void frame_step(const StepParams& P, const Frame& F, int k) {
   T* gdst = static_cast<T*>(P.gdst);
   float dc[8], gc[5];
   if (x < P.nx) {
-    gather_cell<PREC, HET>(P, static_cast<const T*>(P.src), x, y, dc);
     float ay = P.ay;
     if (THERMAL) {
-      pull_cell_g<PREC>(P, static_cast<const T*>(P.gsrc), x, y, gc);
+      gather_cell_thermal<PREC, HET>(P, static_cast<const T*>(P.src), static_cast<const T*>(P.gsrc), x, y, dc, gc);
       ay += P.g_beta * (gc[0] + gc[1] + gc[2] + gc[3] + gc[4]);
+    } else {
+      gather_cell<PREC, HET>(P, static_cast<const T*>(P.src), x, y, dc);
     }
     const Coef cf = coef_at<HET>(P, x, y);
     float ux, uy, phip;

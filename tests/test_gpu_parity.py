@@ -377,9 +377,6 @@ def test_nee_rejections(lbm):
     with pytest.raises(lbm.LbmError) as e:
         lbm.Lattice(lbm.default_config(nx=8, ny=2, bc_y=lbm.NEE))
     assert e.value.code == lbm.EINVAL
-    with pytest.raises(lbm.LbmError) as e:
-        lbm.Lattice(lbm.default_config(nx=8, ny=8, bc_x=lbm.WALL, bc_y=lbm.NEE, thermal=1, tau_T=1.0))
-    assert e.value.code == lbm.EINVAL
     lat = lbm.Lattice(lbm.default_config(nx=8, ny=8, bc_y=lbm.NEE))
     try:
         lat.init_equilibrium(1.0, 0.0, 0.0)
@@ -388,3 +385,63 @@ def test_nee_rejections(lbm):
         assert e.value.code == lbm.ESTATE
     finally:
         lat.close()
+
+
+def _thermal_nee_case(L=48, prec=0, Ra=1e4):
+    nu, tau_v, tau_T, gb = th.parameters_from_Ra(L - 1, Ra, 1.0, 0.1)
+    return Case(L, L, nu=nu, phi=0.6, K=1e-2 * (L - 1) ** 2, bc_x="nee", bc_y="nee", precision=prec,
+                thermal=dict(tau_T=tau_T, g_beta=gb, T0=11.0, T_left=21.0, T_right=1.0))
+
+
+@pytest.mark.parametrize("prec,bound", [(0, 1e-5), (1, 1e-3)])
+def test_natural_convection_wall_nodes_trajectory_and_nusselt(lbm, accuracy, prec, bound):
+    """Natural convection with the paper's wall treatment for both equations (extrapolated wall
+    nodes, isothermal sides, adiabatic top and bottom) against the coupled oracle step, and the
+    wall-node Nusselt numbers of both sides."""
+    case = _thermal_nee_case(prec=prec)
+    flow, tp = case.flow(), case.thermal_params()
+    f = fl.initial_state(flow)
+    g = th.initial_state(flow, tp, f=f)
+    steps = 600
+    with case.lattice(lbm) as lat:
+        lat.step(steps)
+        p, ux, uy, T = [t.cpu().numpy() for t in lat.macros()]
+        nu_l, nu_r = lat.nusselt(0), lat.nusselt(1)
+    for _ in range(steps):
+        f, g = th.coupled_step(f, g, flow, tp)
+    uxo, uyo, po, To = th.coupled_macroscopic(f, g, flow, tp)
+    e_u = rel_l2(np.stack([ux, uy]), np.stack([uxo, uyo]))
+    e_T = rel_l2(T - 11.0, To - 11.0)
+    accuracy.append({"case": "natural convection 48x48 with extrapolated wall nodes, Ra 1e4, eps 0.6, Da 1e-2",
+                     "precision": {0: "fp32", 1: "fp16"}[prec], "steps": steps, "rel_l2_u": e_u, "rel_l2_T_minus_T0": e_T,
+                     "bound": bound})
+    assert e_u <= bound and e_T <= bound, (e_u, e_T)
+    nl, nr = th.nusselt_wall_nodes(To, 0, 21.0, 1.0), th.nusselt_wall_nodes(To, 1, 21.0, 1.0)
+    assert abs(nu_l - nl) <= 20 * bound * abs(nl) and abs(nu_r - nr) <= 20 * bound * abs(nr), (nu_l, nl, nu_r, nr)
+
+
+@pytest.mark.parametrize("bc", ["wall", "nee"])
+def test_thermal_one_step_matches_oracle_elementwise(lbm, bc):
+    """One coupled step (flow + temperature, buoyancy) from a random state, cell by cell, with
+    halfway walls or extrapolated wall nodes on all sides (isothermal sides, adiabatic top and
+    bottom, moving lid)."""
+    case = Case(23, 17, nu=0.05, phi=0.6, K=3.0, bc_x=bc, bc_y=bc, walls={"top": (0.04, 0.0)},
+                thermal=dict(tau_T=0.8, g_beta=2e-4, T0=11.0, T_left=21.0, T_right=1.0))
+    flow, tp = case.flow(), case.thermal_params()
+    rng = np.random.default_rng(21)
+    f0 = random_state(flow, seed=9)
+    T = 11.0 + 5.0 * rng.standard_normal((flow.ny, flow.nx))
+    g0 = th.equilibrium(T, *(0.03 * rng.standard_normal((2, flow.ny, flow.nx))), tp) + 0.01 * rng.standard_normal((5, flow.ny, flow.nx))
+    if bc == "nee":
+        f0, g0 = th.boundary_nodes(f0, g0, flow, tp)
+    f0 = f0.astype(np.float32).astype(np.float64)
+    g0 = g0.astype(np.float32).astype(np.float64)
+    with case.lattice(lbm) as lat:
+        lat.set_populations(to_gpu(f0), to_gpu(g0))
+        lat.step(1)
+        f1, g1 = [t.cpu().numpy() for t in lat.get_populations()]
+        lat.sync()
+    fo, go = th.coupled_step(f0, g0, flow, tp)
+    ef, eg = np.abs(f1 - fo), np.abs(g1 - go)
+    assert ef.max() <= 4e-6, (ef.max(), np.unravel_index(ef.argmax(), ef.shape))
+    assert eg.max() <= 4e-5, (eg.max(), np.unravel_index(eg.argmax(), eg.shape))

@@ -131,8 +131,8 @@ def test_conduction_between_extrapolated_wall_nodes_is_linear_and_nu_is_one():
     T = th.coupled_macroscopic(f, g, flow, tp)[3]
     lin = 21.0 - 20.0 * np.arange(L) / (L - 1)
     assert np.abs(T - lin).max() < 1e-9
-    assert abs(th.nusselt_wall_nodes(T, 0, 21.0, 1.0) - 1.0) < 1e-9
-    assert abs(th.nusselt_wall_nodes(T, 1, 21.0, 1.0) - 1.0) < 1e-9
+    assert abs(th.nusselt_wall_nodes(T, 0, 21.0, 1.0, corners_on_y_walls=False) - 1.0) < 1e-9
+    assert abs(th.nusselt_wall_nodes(T, 1, 21.0, 1.0, corners_on_y_walls=False) - 1.0) < 1e-9
 
 
 def test_adiabatic_extrapolated_wall_node_copies_the_neighbour_temperature():
