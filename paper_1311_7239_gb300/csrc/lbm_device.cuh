@@ -151,7 +151,8 @@ template <> struct Store<PREC_BF16> {
   __device__ static __forceinline__ void load4r(const T* p, float o[4]) { load4(p, o, 1.0f); }
   __device__ static __forceinline__ void store4r(T* p, const float o[4]) { store4(p, o, 1.0f); }
   __device__ static __forceinline__ void store2r(T* p, float2 v) { *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(v); }
-  __device__ static __forceinline__ float2 w2f(uint32_t w) { return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w)); }
+  // a BF16 value is the high half of its FP32 value
+  __device__ static __forceinline__ float2 w2f(uint32_t w) { return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u)); }
   __device__ static __forceinline__ uint32_t f2w(float2 v) {
     const __nv_bfloat162 h = __float22bfloat162_rn(v);
     return *reinterpret_cast<const uint32_t*>(&h);

@@ -237,11 +237,10 @@ __device__ __forceinline__ void step_item(const StepParams& P, const Tiling& tl,
 }
 
 // One time step of one lattice: one CTA per work item.  Register caps (measured): 8 CTAs (32
-// warps) per SM for the flow alone (64 registers), also with FP16 storage; 7 with BF16 storage
-// (72: at 64 its conversions spill and it runs 8 % slower); 6 and 5 with the temperature
-// populations (80 and 96).
+// warps) per SM for the flow alone (64 registers), with every storage precision; 6 and 5 with
+// the temperature populations (80 and 96).
 template <int PREC, bool HET, bool THERMAL>
-__global__ void __launch_bounds__(kStepThreads, THERMAL ? (PREC == PREC_FP32 ? 6 : 5) : (kPacked<PREC, HET> && PREC == PREC_BF16 ? 7 : 8)) k_step(const StepParams P, Tiling tl) {
+__global__ void __launch_bounds__(kStepThreads, THERMAL ? (PREC == PREC_FP32 ? 6 : 5) : 8) k_step(const StepParams P, Tiling tl) {
   step_item<PREC, HET, THERMAL, kStepThreads>(P, tl, blockIdx.x);
 }
 
