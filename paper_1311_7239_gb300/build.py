@@ -16,6 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "liblbm.so")
+DEBUG_LIB = os.path.join(PKG, "liblbm_debug.so")  # -DLBM_DEBUG: kernel index checks (load with LBM_LIBRARY)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
@@ -32,18 +33,23 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def build(verbose: bool = False, extra=()) -> str:
-    """Compile and link liblbm.so; returns its path.  Rebuilds only when a source is newer."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, extra=(), debug: bool = False) -> str:
+    """Compile and link liblbm.so (liblbm_debug.so with debug=True: the kernels' index checks);
+    returns its path.  Rebuilds only when a source is newer."""
+    lib_path = DEBUG_LIB if debug else LIB
+    bdir = os.path.join(BUILD, "debug") if debug else BUILD
+    if debug:
+        extra = ("-DLBM_DEBUG", *extra)
+    os.makedirs(bdir, exist_ok=True)
     nvcc = _nvcc()
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "lbm.h")]
     newest = max(os.path.getmtime(p) for p in deps)
-    if os.path.exists(LIB) and os.path.getmtime(LIB) >= newest and not extra:
-        return LIB
+    if os.path.exists(lib_path) and os.path.getmtime(lib_path) >= newest and not (set(extra) - {"-DLBM_DEBUG"}):
+        return lib_path
     objs = []
     cmds = []
     for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         cmds.append([nvcc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj])
 
@@ -56,11 +62,11 @@ def build(verbose: bool = False, extra=()) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=min(8, len(cmds))) as ex:
         list(ex.map(run, cmds))
-    tmp = LIB + ".tmp"
+    tmp = lib_path + ".tmp"
     run([nvcc, *ARCH, "-shared", "-Xlinker", "--no-undefined", "-o", tmp, *objs, "-lcudart"])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv))
+    print(build(verbose="-v" in sys.argv, debug="--debug" in sys.argv))

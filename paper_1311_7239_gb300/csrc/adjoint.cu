@@ -399,13 +399,16 @@ __device__ __forceinline__ void adj_item(const StepParams& P, const void* buf, c
   if (item < tl.frame_blocks) {  // one frame cell per thread
     const Frame F = frame_of(P.nx, P.ny, P.bc_y, kCellsPerThread);
     int x, y;
-    if (frame_cell(F, P.ny, item * NT + (int)threadIdx.x, x, y) && x < P.nx) adj_cell<PREC, HET>(P, buf, A, x, y);
+    if (frame_cell(F, P.ny, item * NT + (int)threadIdx.x, x, y) && x < P.nx && dbg_check(P, y >= 0 && y < P.ny))
+      adj_cell<PREC, HET>(P, buf, A, x, y);
     return;
   }
   int x0, y;
   const bool has_pair = adj_pair(tl, P.ny, NT, item - tl.frame_blocks, (int)threadIdx.x, x0, y);
   const int lane = threadIdx.x & 31;
-  const int xl = x0 < P.pitch - 2 ? x0 : P.pitch - 2;
+  int xl = x0 < P.pitch - 2 ? x0 : P.pitch - 2;
+  const bool idx_ok = dbg_check(P, y >= 0 && y < P.ny && xl >= 0);
+  if (!idx_ok) y = xl = 0;  // (debug builds) keep the loads and shuffles inside the buffers
   int ym = y - 1, yp = y + 1;
   ym = ym < 0 ? P.ny - 1 : ym;
   yp = yp >= P.ny ? 0 : yp;
@@ -441,7 +444,7 @@ __device__ __forceinline__ void adj_item(const StepParams& P, const void* buf, c
   gather2<PREC_FP32, 1>(nu_in + 6 * pl + rm, xl, P.pitch, lane, 1.0f, mu[6]);   // e7 = (-1,-1)
   gather2<PREC_FP32, -1>(nu_in + 7 * pl + rm, xl, P.pitch, lane, 1.0f, mu[7]);  // e8 = ( 1,-1)
   const bool wall_row = P.bc_y == BC_WALL && (y == 0 || y == P.ny - 1);
-  if (!has_pair || wall_row || x0 < kCellsPerThread || x0 >= tl.frame_x1) return;
+  if (!has_pair || !idx_ok || wall_row || x0 < kCellsPerThread || x0 >= tl.frame_x1) return;
   float gl[2], gp[2];
 #pragma unroll
   for (int c = 0; c < 2; ++c) {

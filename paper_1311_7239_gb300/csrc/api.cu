@@ -286,6 +286,7 @@ int check_error_word(lbm_ctx* c) {
   unsigned int h = 0;
   LBM_CUDA(cudaMemcpyAsync(&h, c->err, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "read of error word");
   LBM_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
+  if (h & 4u) return fail(LBM_ECUDA, "a kernel index left its buffer (debug build check)");
   if (h & 1u) return fail(LBM_EUNSTABLE, "a step produced a non-finite velocity (after %lld steps)", (long long)c->steps);
   return LBM_OK;
 }

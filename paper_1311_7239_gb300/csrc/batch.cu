@@ -510,6 +510,7 @@ int lbm_batch_sync(lbm_batch* b) {
   LBM_BCUDA(cudaGetLastError(), "pending launch error");
   LBM_BCUDA(cudaMemcpyAsync(&h, b->err, sizeof(h), cudaMemcpyDeviceToHost, b->stream), "read of error word");
   LBM_BCUDA(cudaStreamSynchronize(b->stream), "stream synchronize");
+  if (h & 4u) return fail_msg(LBM_ECUDA, "a kernel index left its buffer (debug build check)");
   if (h & 1u) return fail_msg(LBM_EUNSTABLE, "a lattice of the batch produced a non-finite velocity");
   return LBM_OK;
 }

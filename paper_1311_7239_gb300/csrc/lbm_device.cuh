@@ -66,6 +66,20 @@ struct StepParams {
   PairConst pc;
 };
 
+// Debug builds (-DLBM_DEBUG) check the index invariants of the kernels: a violation sets bit 2 of
+// the error word, which the next synchronising call reports, and the access is skipped or clamped.
+// Release builds compile the checks away.
+__device__ __forceinline__ bool dbg_check(const StepParams& P, bool ok) {
+#ifdef LBM_DEBUG
+  if (!ok) atomicOr(P.err, 4u);
+  return ok;
+#else
+  (void)P;
+  (void)ok;
+  return true;
+#endif
+}
+
 // D2Q8 velocities of Eq. 7 and the weights w_i listed after Eq. 20 (w_1..4 = 1/9, w_5..8 = 1/36).
 __device__ __forceinline__ int ex_of(int i) { return (i == 0 || i == 4 || i == 7) ? 1 : ((i == 2 || i == 5 || i == 6) ? -1 : 0); }
 __device__ __forceinline__ int ey_of(int i) { return (i == 1 || i == 4 || i == 5) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0); }
@@ -470,6 +484,7 @@ __device__ __forceinline__ int wall_of(int sx, int sy, int ny) {
 template <int PREC>
 __device__ __forceinline__ float pull_one(const StepParams& P, const typename Store<PREC>::T* src, int x, int y, int i) {
   using S = Store<PREC>;
+  if (!dbg_check(P, x >= 0 && x < P.pitch && y >= 0 && y < P.ny)) return 0.0f;
   int sx = x - ex_of(i), sy = y - ey_of(i);
   if (P.bc_x != BC_WALL) sx = (sx + P.nx) % P.nx;
   if (P.bc_y != BC_WALL) sy = (sy + P.ny) % P.ny;
@@ -492,6 +507,7 @@ __device__ __forceinline__ void pull_cell(const StepParams& P, const typename St
 template <int PREC>
 __device__ __forceinline__ float pull_one_g(const StepParams& P, const typename Store<PREC>::T* src, int x, int y, int i) {
   using S = Store<PREC>;
+  if (!dbg_check(P, x >= 0 && x < P.pitch && y >= 0 && y < P.ny)) return 0.0f;
   if (i == 0) return S::dec(src[(int64_t)y * P.pitch + x], P.inv_scale);
   int sx = x - ex5(i), sy = y - ey5(i);
   if (P.bc_x != BC_WALL) sx = (sx + P.nx) % P.nx;

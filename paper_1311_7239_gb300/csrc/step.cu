@@ -27,6 +27,7 @@ __device__ void frame_step(const StepParams& P, const Frame& F, int k) {
   using T = typename S::T;
   int x, y;
   if (!frame_cell(F, P.ny, k, x, y)) return;
+  if (!dbg_check(P, x >= 0 && x < P.pitch && y >= 0 && y < P.ny)) return;
   const int64_t o = (int64_t)y * P.pitch + x;
   T* dst = static_cast<T*>(P.dst);
   T* gdst = static_cast<T*>(P.gdst);
@@ -70,7 +71,9 @@ __device__ __forceinline__ void step_item_words(const StepParams& P, const Tilin
   const bool has_group = main_group(tl, P.ny, NT, item - tl.frame_blocks, (int)threadIdx.x, x0, y);
   const T* __restrict__ src = static_cast<const T*>(P.src);
   const int lane = threadIdx.x & 31;
-  const int xl = x0 < P.pitch - C ? x0 : P.pitch - C;
+  int xl = x0 < P.pitch - C ? x0 : P.pitch - C;
+  const bool idx_ok = dbg_check(P, y >= 0 && y < P.ny && xl >= 0);
+  if (!idx_ok) y = xl = 0;  // (debug builds) keep the loads and shuffles inside the buffers
   int ym = y - 1, yp = y + 1;
   ym = ym < 0 ? P.ny - 1 : ym;
   yp = yp >= P.ny ? 0 : yp;
@@ -87,7 +90,7 @@ __device__ __forceinline__ void step_item_words(const StepParams& P, const Tilin
   gather4w<PREC, -1>(src + 6 * pl + rp, xl, P.pitch, lane, w[6]);  // e7 = (-1,-1)
   gather4w<PREC, 1>(src + 7 * pl + rp, xl, P.pitch, lane, w[7]);   // e8 = ( 1,-1)
   const bool wall_row = (P.bc_y == BC_WALL || P.bc_y == BC_NEE) && (y == 0 || y == P.ny - 1);
-  if (!has_group || wall_row || x0 == 0 || x0 + C >= P.nx) return;
+  if (!has_group || !idx_ok || wall_row || x0 == 0 || x0 + C >= P.nx) return;
   float check = 0.0f;
 #pragma unroll
   for (int h = 0; h < C / 2; ++h) {
@@ -128,7 +131,9 @@ __device__ __forceinline__ void step_item(const StepParams& P, const Tiling& tl,
   const T* __restrict__ src = static_cast<const T*>(P.src);
   T* __restrict__ dst = static_cast<T*>(P.dst);
   const int lane = threadIdx.x & 31;
-  const int xl = x0 < P.pitch - C ? x0 : P.pitch - C;  // loads stay inside the row
+  int xl = x0 < P.pitch - C ? x0 : P.pitch - C;  // loads stay inside the row
+  const bool idx_ok = dbg_check(P, y >= 0 && y < P.ny && xl >= 0);
+  if (!idx_ok) y = xl = 0;  // (debug builds) keep the loads and shuffles inside the buffers
   // source rows of e_y = +1 and -1 (periodic wrap; wall rows belong to the frame)
   int ym = y - 1, yp = y + 1;
   ym = ym < 0 ? P.ny - 1 : ym;
@@ -166,7 +171,7 @@ __device__ __forceinline__ void step_item(const StepParams& P, const Tiling& tl,
   }
   // (after the shuffles) frame groups and groups past the row are not stored here
   const bool wall_row = (P.bc_y == BC_WALL || P.bc_y == BC_NEE) && (y == 0 || y == P.ny - 1);
-  if (!has_group || wall_row || x0 == 0 || x0 + C >= P.nx) return;
+  if (!has_group || !idx_ok || wall_row || x0 == 0 || x0 + C >= P.nx) return;
 
   float check = 0.0f;
   if constexpr (R) {

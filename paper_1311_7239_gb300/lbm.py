@@ -12,7 +12,8 @@ import math
 import os
 
 PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(PKG, "liblbm.so")
+# LBM_LIBRARY selects another build of the library (e.g. liblbm_debug.so, with kernel index checks)
+LIB_PATH = os.environ.get("LBM_LIBRARY") or os.path.join(PKG, "liblbm.so")
 
 ABI_VERSION = 1
 FP32, FP16_DEV, BF16_DEV = 0, 1, 2
