@@ -290,6 +290,15 @@ class Lattice:
         _check(lib().lbm_macros(self._h, _ptr(p, True), _ptr(ux, True), _ptr(uy, True), _ptr(T, True)), "lbm_macros")
         return (p, ux, uy, T) if want_T else (p, ux, uy)
 
+    def write_fields(self, path):
+        """Write p, ux, uy (and T) of the current state to a NumPy .npz file (float32 [ny, nx] arrays,
+        row 0 at the bottom), with the step count."""
+        import numpy as np
+
+        fields = self.macros()
+        names = ("p", "ux", "uy", "T")[: len(fields)]
+        np.savez(path, step=np.int64(self.step_count()), **{k: v.cpu().numpy() for k, v in zip(names, fields)})
+
     def get_populations(self, f=None, g=None):
         f = self._new(8, self.ny, self.nx) if f is None else f
         if self.thermal and g is None:

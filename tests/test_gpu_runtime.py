@@ -83,3 +83,38 @@ def test_injected_allocation_failure_is_enomem(lbm, k):
                        timeout=300)
     assert r.returncode == 0, r.stderr
     assert "code -2" in r.stdout and "second ok" in r.stdout
+
+
+def test_write_fields_round_trip(lbm, tmp_path):
+    import numpy as np
+
+    cfg = lbm.default_config(nx=20, ny=12, bc_x=lbm.WALL, bc_y=lbm.WALL, u_wall=[(0, 0), (0, 0), (0, 0), (0.05, 0)])
+    with lbm.Lattice(cfg) as lat:
+        lat.step(17)
+        p, ux, uy = [t.cpu().numpy() for t in lat.macros()]
+        lat.write_fields(tmp_path / "fields.npz")
+    z = np.load(tmp_path / "fields.npz")
+    assert int(z["step"]) == 17
+    assert np.array_equal(z["p"], p) and np.array_equal(z["ux"], ux) and np.array_equal(z["uy"], uy)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_bench_cavity_stays_bounded_for_50k_steps(lbm, prec):
+    """The 4096^2 benchmark cavity (eps 0.4, Da 1e-3, Re 100, lid 0.1) for the 50k steps of its
+    configuration: no non-finite velocity, speeds below the lid's, a small per-step change (the
+    flow is still spinning up: its viscous time L^2 / nu is 4M steps)."""
+    L = 4096
+    cfg = lbm.default_config(nx=L, ny=L, bc_x=lbm.WALL, bc_y=lbm.WALL, nu=0.1 * L / 100, phi=0.4, K=1e-3 * L * L,
+                             u_wall=[(0, 0), (0, 0), (0, 0), (0.1, 0)], precision=prec, p_rest=0.4, dev_scale_log2=10)
+    with lbm.Lattice(cfg) as lat:
+        lat.step(9999)
+        lat.step(1)
+        r1 = lat.residual()
+        lat.step(39999)
+        lat.step(1)
+        r2 = lat.residual()
+        _, ux, uy = lat.macros()
+        umax = float((ux * ux + uy * uy).sqrt().max())
+        lat.sync()
+        assert lat.step_count() == 50000
+    assert umax <= 0.1 and 0 < r1 < 1e-2 and 0 < r2 < 1e-2, (umax, r1, r2)
