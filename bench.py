@@ -181,21 +181,21 @@ def run_reference(args, rank, world):
     return 0
 
 
-def make_lattice(lbm, L, prec, stream):
+def make_lattice(lbm, L, prec, stream, streaming=0):
     prm = cavity_params(L)
     cfg = lbm.default_config(nx=L, ny=L, bc_x=lbm.WALL, bc_y=lbm.WALL, nu=prm["nu"], phi=prm["phi"], K=prm["K"],
                              u_wall=[(0, 0), (0, 0), (0, 0), (prm["lid"], 0)], precision=PREC[prec], p_rest=prm["phi"],
-                             dev_scale_log2=10)
+                             dev_scale_log2=10, streaming=streaming)
     cfg.stream = stream.cuda_stream
     return lbm.Lattice(cfg)
 
 
-def timed_steps(lbm, L, prec, steps, warmup, local_rank, dist=None):
+def timed_steps(lbm, L, prec, steps, warmup, local_rank, dist=None, streaming=0):
     """(ms for `steps` steps, clock summary, lattice) with CUDA events on the lattice's stream."""
     import torch
 
     stream = torch.cuda.Stream()
-    lat = make_lattice(lbm, L, prec, stream)
+    lat = make_lattice(lbm, L, prec, stream, streaming)
     lat.step(warmup)
     lat.sync()
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -219,6 +219,29 @@ def accuracy_record():
             return json.load(fh)
     except Exception:
         return None
+
+
+def inplace_form(lbm, L, steps, warmup, local_rank):
+    """The benchmark cavity with in-place streaming (one population buffer): same bytes per update
+    as the A-B form, half the population memory."""
+    import torch
+
+    out = {}
+    peak, _ = peaks()
+    for prec in ("fp32", "fp16"):
+        ms, clk, lat = timed_steps(lbm, L, prec, steps, warmup, local_rank, streaming=1)
+        mem = lat.memory_bytes()
+        lat.close()
+        torch.cuda.empty_cache()
+        stream = torch.cuda.Stream()
+        ab = make_lattice(lbm, L, prec, stream)
+        mem_ab = ab.memory_bytes()
+        ab.close()
+        bw = BYTES_PER_LU[prec] * L * L * steps / (ms * 1e-3) / 1e9
+        out[prec] = {"value": L * L * steps / (ms * 1e-3) / 1e6, "unit": "MLUPS", "achieved_gbs": bw, "roofline_frac": bw / peak,
+                     "algorithmic_bytes_per_lu": BYTES_PER_LU[prec], "steps": steps, "device_bytes": mem,
+                     "device_bytes_ab": mem_ab, "clocks": clk}
+    return {"workload": f"lid-driven porous cavity {L}x{L}, eps=0.4, Da=1e-3, Re=100, lid=0.1, in-place streaming", **out}
 
 
 def thermal_form(lbm, L, steps, warmup, local_rank):
@@ -388,7 +411,8 @@ def run_gpu(args, rank, world, local_rank):
     L = args.size
     prm = cavity_params(L)
     prec = args.precision
-    ms, clocks, lat = timed_steps(lbm, L, prec, args.steps, args.warmup, local_rank, dist)
+    streaming = 1 if args.streaming == "inplace" else 0
+    ms, clocks, lat = timed_steps(lbm, L, prec, args.steps, args.warmup, local_rank, dist, streaming)
     if dist:
         ms = max_over_ranks(ms, dist, "cuda")
         dist.barrier()
@@ -428,21 +452,21 @@ def run_gpu(args, rank, world, local_rank):
         return 0
     bpl = BYTES_PER_LU[prec]
     achieved = bpl * cells / (ms * 1e-3 / args.steps) / 1e9
-    kernel_key = f"k_step_{prec}_uniform_{L}"
+    kernel_key = f"k_step_{prec}_uniform_{L}" if not streaming else f"k_step_ip_{prec}_uniform_{L}"
     traffic = traffic_for(kernel_key)
     line = {
         "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "fp16": "f32 (f16 storage)", "bf16": "f32 (bf16 storage)"}[prec], "data": "synthetic",
         "config": {"workload": f"lid-driven porous cavity {L}x{L}, eps=0.4, Da=1e-3, Re=100, lid=0.1, "
-                               f"{prec} deviation storage, A-B pull streaming",
+                               f"{prec} deviation storage, {'in-place' if streaming else 'A-B pull'} streaming",
                    "nx": L, "ny": L, "precision": prec,
-                   "l2": f"inputs larger than L2 (2 population buffers of {bpl // 2 * cells / 1e6:.0f} MB)",
+                   "l2": f"inputs larger than L2 ({1 if streaming else 2} population buffer(s) of {bpl // 2 * cells / 1e6:.0f} MB)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs", "kernel": "k_step",
+                     "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs", "kernel": "k_step_ip" if streaming else "k_step",
                      "algorithmic_bytes_per_lu": bpl},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps + (1 if streaming else 0),  # in-place: + the u(t-1) record before the last step
         "e2e": {"value": e2e_mlups, "unit": "MLUPS", "h2d_bytes_per_step": int(walls.numel() * 4),
                 "d2h_bytes_per_step": int(probe.numel() * 4), "steps": e2e_steps,
                 "call": "lbm_set_walls(host) + lbm_step(1) + lbm_probe(host) per step"},
@@ -452,6 +476,7 @@ def run_gpu(args, rank, world, local_rank):
         line["forms"] = forms
         line["forms"]["thermal"] = thermal_form(lbm, 2048, max(64, args.steps // 4), args.warmup, local_rank)
         line["forms"]["heterogeneous"] = heterogeneous_form(lbm, args.size, max(64, args.steps // 4), args.warmup, local_rank)
+        line["forms"]["inplace"] = inplace_form(lbm, args.size, max(64, args.steps // 4), args.warmup, local_rank)
         line["forms"]["adjoint"] = adjoint_form(lbm, T=args.adjoint_steps)
         if not args.no_ensemble:
             line["forms"]["ensemble"] = ensemble_form(lbm, args.ensemble_steps, local_rank)
@@ -507,10 +532,11 @@ def run_case(args, local_rank):
         print(json.dumps({"case": "nusselt", "L": L, "precision": args.precision, "steps": steps, "Nu_left": nl, "Nu_right": nr,
                           "table1_present": 3.451, "rel_diff": abs(nl - 3.451) / 3.451, "seconds": time.perf_counter() - t0,
                           "history": hist[-5:]}))
-    elif args.case in ("fp16", "thermal"):  # 2048^2 cavity FP16 storage / natural convection FP32
-        stream = torch.cuda.Stream()
-        if args.case == "fp16":
-            cfg = make_lattice(lbm, 2048, "fp16", stream).cfg
+    elif args.case in ("fp16", "thermal", "inplace"):  # 2048^2 cavity FP16 storage / natural convection FP32 /
+        stream = torch.cuda.Stream()                     # cavity with in-place streaming (--precision)
+        if args.case in ("fp16", "inplace"):
+            cfg = make_lattice(lbm, 2048, "fp16" if args.case == "fp16" else args.precision, stream,
+                               1 if args.case == "inplace" else 0).cfg
         else:
             cfg = workloads.natural_convection(lbm, L=2048)
             cfg.stream = stream.cuda_stream
@@ -534,12 +560,14 @@ def run_sweep(args, local_rank):
         for prec in PREC:
             steps = max(64, int(args.steps * (4096 / L) ** 2))
             steps = min(steps, 64000) // 32 * 32
-            ms, clk, lat = timed_steps(lbm, L, prec, steps, args.warmup, local_rank)
+            ms, clk, lat = timed_steps(lbm, L, prec, steps, args.warmup, local_rank,
+                                       streaming=1 if args.streaming == "inplace" else 0)
             lat.close()
             cells = L * L
             bw = BYTES_PER_LU[prec] * cells * steps / (ms * 1e-3) / 1e9
             l2 = 2 * BYTES_PER_LU[prec] // 2 * cells / 1e6
-            print(json.dumps({"size": L, "precision": prec, "steps": steps, "MLUPS": cells * steps / (ms * 1e-3) / 1e6,
+            print(json.dumps({"size": L, "precision": prec, "streaming": args.streaming, "steps": steps,
+                              "MLUPS": cells * steps / (ms * 1e-3) / 1e6,
                               "achieved_gbs": bw, "roofline_frac": bw / peak, "peak_source": peak_kind,
                               "state_MB": l2, "l2_resident": l2 < 129.0, "clocks": clk}), flush=True)
             torch.cuda.empty_cache()
@@ -554,13 +582,15 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="fp32", choices=list(PREC))
     ap.add_argument("--size", type=int, default=4096)
+    ap.add_argument("--streaming", default="ab", choices=["ab", "inplace"],
+                    help="population streaming of the main line and the sweep (A-B buffers or in-place)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the timed CPU oracle baseline")
     ap.add_argument("--no-forms", action="store_true", help="skip the other storage precisions")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 512-lattice ensemble form")
     ap.add_argument("--adjoint-steps", type=int, default=4000, help="T of the adjoint form")
     ap.add_argument("--ensemble-steps", type=int, default=10000, help="steps of the 512-lattice ensemble form")
     ap.add_argument("--adjoint-nx", type=int, default=1024, help="channel length of --case adjoint (height nx / 2)")
-    ap.add_argument("--case", default="", choices=["", "adjoint", "batch", "fp16", "thermal", "nusselt"],
+    ap.add_argument("--case", default="", choices=["", "adjoint", "batch", "fp16", "thermal", "nusselt", "inplace"],
                     help="run one small case of a kernel family (for profiler captures) and exit")
     ap.add_argument("--sweep", default="", help="comma-separated lattice sizes: print one line per size and precision")
     args = ap.parse_args()

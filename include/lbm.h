@@ -28,7 +28,7 @@
 extern "C" {
 #endif
 
-#define LBM_ABI_VERSION 1u
+#define LBM_ABI_VERSION 2u
 
 #if defined(__GNUC__)
 #define LBM_API __attribute__((visibility("default")))
@@ -60,6 +60,17 @@ extern "C" {
                          * the node inward along the normal; walls at distance nx - 1 / ny - 1; a
                          * temperature wall node takes g_eq(T_w or T_nb, u_w) + g_nb - g_eq(T_nb, u_nb);
                          * not differentiable by lbm_adjoint; needs nx, ny >= 3 */
+
+/* population streaming (lbm_config.streaming) */
+#define LBM_STREAM_AB 0u      /* two population buffers: the step pulls from one into the other */
+#define LBM_STREAM_INPLACE 1u /* one buffer, updated in place ("esoteric pull": every cell writes back into the
+                               * slots it read, each slot receiving the opposite population; populations
+                               * leaving through a wall are parked in one ghost row below and above and one
+                               * ghost column right of the lattice).  Same arithmetic and results as
+                               * LBM_STREAM_AB with half the population memory.  Sides: LBM_PERIODIC and
+                               * LBM_WALL only (the extrapolated sides read a neighbour's state while it is
+                               * being overwritten); not for lbm_adjoint or batches.  lbm_step records u
+                               * before the last step of each call (8 B per cell) for lbm_residual. */
 
 /* wall indices of u_wall / T_wall */
 #define LBM_LEFT 0
@@ -95,6 +106,8 @@ typedef struct lbm_config {
   double g_beta, T0;    /* buoyancy a = g_beta (T - T0) j (Sec. 3.4); T0 is also the stored reference */
   double T_wall[4];     /* wall temperature (anti-bounce-back), NaN = adiabatic (bounce-back) */
   void* stream;         /* cudaStream_t to use, or NULL */
+  uint32_t streaming;   /* LBM_STREAM_AB (default) | LBM_STREAM_INPLACE */
+  uint32_t reserved0;   /* must be 0 */
 } lbm_config;
 
 typedef struct lbm_ctx lbm_ctx;
@@ -108,7 +121,8 @@ LBM_API void lbm_config_defaults(lbm_config* cfg);
 LBM_API uint32_t lbm_config_size(void);
 
 /* Create a context on the current CUDA device: allocates two population buffers (A-B
- * streaming), the medium fields and, if thermal, two temperature buffers.  The state is
+ * streaming; one with LBM_STREAM_INPLACE), the medium fields and, if thermal, the temperature
+ * buffers in the same number.  The state is
  * initialised as by lbm_init_equilibrium(ctx, 1, 0, 0, 0).  EABI / EINVAL / ENOMEM / ECUDA. */
 LBM_API int lbm_create(const lbm_config* cfg, lbm_ctx** out);
 

@@ -128,7 +128,9 @@ struct lbm_ctx {
   int64_t plane = 0;
   void* f[2] = {nullptr, nullptr};
   void* g[2] = {nullptr, nullptr};
-  int cur = 0;
+  int cur = 0;                   // A-B: buffer of the current state; in-place: parity of the next step
+  bool inplace = false;          // one buffer (f[0], g[0]) with rows -1..ny; see ip_off
+  float* uprev = nullptr;        // in-place: u before the last step of the last lbm_step call, [2][ny][nx]
   float* phi = nullptr;
   float* K = nullptr;
   float* sv = nullptr;  // per-cell viscous rate (heterogeneous mode), when a viscosity-ratio field is set
@@ -269,12 +271,21 @@ bool any_host(const lbm_ctx* c, const void* const* ptrs, int n) {
   return false;
 }
 
+// row 0 of an in-place buffer (row -1 is the first row of the allocation)
+void* ip_row0(const lbm_ctx* c, void* buf) { return buf ? static_cast<char*>(buf) + (size_t)c->pitch * c->elem : nullptr; }
+
 StepParams params_for(const lbm_ctx* c, bool forward_dst = true) {
   StepParams P = c->base;
-  P.src = c->f[c->cur];
-  P.dst = c->f[c->cur ^ 1];
-  P.gsrc = c->g[c->cur];
-  P.gdst = c->g[c->cur ^ 1];
+  if (c->inplace) {
+    P.src = P.dst = ip_row0(c, c->f[0]);
+    P.gsrc = P.gdst = ip_row0(c, c->g[0]);
+    P.parity = c->cur;
+  } else {
+    P.src = c->f[c->cur];
+    P.dst = c->f[c->cur ^ 1];
+    P.gsrc = c->g[c->cur];
+    P.gdst = c->g[c->cur ^ 1];
+  }
   P.phi = c->het ? c->phi : nullptr;
   P.K = c->het ? c->K : nullptr;
   P.sv = c->het ? c->sv : nullptr;
@@ -311,6 +322,9 @@ int validate_config(const lbm_config* c) {
   if (!(c->phi > 0 && c->phi <= 1) || !(c->K > 0)) return fail(LBM_EINVAL, "uniform phi must be in (0, 1], K > 0");
   if (!isfinite(c->ax) || !isfinite(c->ay) || !isfinite(c->p_rest)) return fail(LBM_EINVAL, "non-finite a or p_rest");
   if (c->dev_scale_log2 < -30 || c->dev_scale_log2 > 30) return fail(LBM_EINVAL, "dev_scale_log2 out of [-30, 30]");
+  if (c->streaming > LBM_STREAM_INPLACE || c->reserved0 != 0) return fail(LBM_EINVAL, "unknown streaming mode %u", c->streaming);
+  if (c->streaming == LBM_STREAM_INPLACE && (c->bc_x > LBM_WALL || c->bc_y > LBM_WALL))
+    return fail(LBM_EINVAL, "in-place streaming supports periodic and halfway-wall sides only");
   if (c->thermal) {
     if (!(c->tau_T > 0.5) || !(c->sigma > 0)) return fail(LBM_EINVAL, "tau_T must exceed 1/2 and sigma be positive");
     if (!(c->zeta3 > 0 && c->zeta3 < 2) || !(c->zeta4 > 0 && c->zeta4 < 2)) return fail(LBM_EINVAL, "zeta3, zeta4 in (0, 2)");
@@ -325,6 +339,7 @@ void fill_base(lbm_ctx* c) {
   params_from_config(c->cfg, c->prec, c->pitch, c->plane, c->base);
   c->base.uw = c->walls;
   c->base.err = c->err;
+  c->base.inplace = c->inplace ? 1 : 0;
 }
 
 void drop_graphs(lbm_ctx* c) {
@@ -346,6 +361,7 @@ void release(lbm_ctx* c) {
   cudaFree(c->phi);
   cudaFree(c->K);
   cudaFree(c->sv);
+  cudaFree(c->uprev);
   cudaFree(c->err);
   cudaFree(c->walls);
   cudaFree(c->probe);
@@ -402,8 +418,15 @@ int lbm_create(const lbm_config* cfg, lbm_ctx** out) {
   }
   c->prec = (int)cfg->precision;
   c->elem = c->prec == PREC_FP32 ? 4 : 2;
-  c->pitch = (int)((cfg->nx + 127) / 128 * 128);
-  c->plane = (int64_t)c->pitch * cfg->ny;
+  // in-place: a ghost column right of the lattice and ghost rows below and above it
+  c->inplace = cfg->streaming == LBM_STREAM_INPLACE;
+  c->pitch = (int)((cfg->nx + (c->inplace ? 1 : 0) + 127) / 128 * 128);
+  c->plane = (int64_t)c->pitch * (cfg->ny + (c->inplace ? 2 : 0));
+  const int nbuf = c->inplace ? 1 : 2;
+  if (c->inplace && 8 * (uint64_t)c->plane > (1ull << 32)) {  // the in-place step indexes a buffer with 32-bit offsets
+    delete c;
+    return fail(LBM_EINVAL, "in-place streaming needs 8 (ny + 2) pitch <= 2^32 elements (pitch = nx + 1 rounded up to 128)");
+  }
   if (cfg->stream) {
     c->stream = static_cast<cudaStream_t>(cfg->stream);
   } else {
@@ -416,10 +439,12 @@ int lbm_create(const lbm_config* cfg, lbm_ctx** out) {
   }
   const size_t fbytes = 8 * (size_t)c->plane * c->elem;
   const size_t gbytes = 5 * (size_t)c->plane * c->elem;
-  for (int b = 0; b < 2 && rc == LBM_OK; ++b) {
+  for (int b = 0; b < nbuf && rc == LBM_OK; ++b) {
     rc = dev_alloc(c, &c->f[b], fbytes, "cudaMalloc(populations)");
     if (rc == LBM_OK && cfg->thermal) rc = dev_alloc(c, &c->g[b], gbytes, "cudaMalloc(temperature populations)");
   }
+  if (rc == LBM_OK && c->inplace)
+    rc = dev_alloc(c, reinterpret_cast<void**>(&c->uprev), 2 * (size_t)cfg->nx * cfg->ny * sizeof(float), "cudaMalloc(previous velocity)");
   if (rc == LBM_OK) rc = dev_alloc(c, reinterpret_cast<void**>(&c->err), sizeof(unsigned int), "cudaMalloc(error word)");
   if (rc == LBM_OK)
     rc = dev_alloc(c, reinterpret_cast<void**>(&c->red), (2 * kResidualMaxBlocks + 2) * sizeof(double), "cudaMalloc(reduction)");
@@ -436,7 +461,7 @@ int lbm_create(const lbm_config* cfg, lbm_ctx** out) {
     if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemset");
   }
   if (rc == LBM_OK) {
-    for (int b = 0; b < 2 && rc == LBM_OK; ++b) {
+    for (int b = 0; b < nbuf && rc == LBM_OK; ++b) {
       e = cudaMemsetAsync(c->f[b], 0, fbytes, c->stream);
       if (e == cudaSuccess && c->g[b]) e = cudaMemsetAsync(c->g[b], 0, gbytes, c->stream);
       if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemset");
@@ -544,10 +569,16 @@ int lbm_init_equilibrium(lbm_ctx* c, double p0, double ux0, double uy0, int phi_
   if (!c) return fail(LBM_EINVAL, "null context");
   if (!isfinite(p0) || !isfinite(ux0) || !isfinite(uy0)) return fail(LBM_EINVAL, "non-finite initial state");
   StepParams P = params_for(c);
-  P.dst = c->f[c->cur];
-  LBM_CUDA(launch_init(P, c->prec, c->het, thermal_of(c), (float)p0, (float)ux0, (float)uy0, phi_p_uniform ? 1 : 0, 0.0f, true,
-                       false, c->stream),
-           "init kernel");
+  if (c->inplace) {
+    LBM_CUDA(launch_put_inplace(P, c->prec, c->het, nullptr, nullptr, true, false, (float)p0, (float)ux0, (float)uy0,
+                                phi_p_uniform ? 1 : 0, 0.0f, c->stream),
+             "init kernel");
+  } else {
+    P.dst = c->f[c->cur];
+    LBM_CUDA(launch_init(P, c->prec, c->het, thermal_of(c), (float)p0, (float)ux0, (float)uy0, phi_p_uniform ? 1 : 0, 0.0f, true,
+                         false, c->stream),
+             "init kernel");
+  }
   c->steps = 0;
   c->history = 0;
   c->init_p0 = p0;
@@ -562,8 +593,13 @@ int lbm_init_temperature(lbm_ctx* c, double T_init) {
   if (!thermal_of(c)) return fail(LBM_ESTATE, "context has no temperature field");
   if (!isfinite(T_init)) return fail(LBM_EINVAL, "non-finite temperature");
   StepParams P = params_for(c);
-  P.gdst = c->g[c->cur];
-  LBM_CUDA(launch_init(P, c->prec, c->het, true, 0.0f, 0.0f, 0.0f, 0, (float)T_init, false, true, c->stream), "init kernel");
+  if (c->inplace) {
+    LBM_CUDA(launch_put_inplace(P, c->prec, c->het, nullptr, nullptr, false, true, 0.0f, 0.0f, 0.0f, 0, (float)T_init, c->stream),
+             "init kernel");
+  } else {
+    P.gdst = c->g[c->cur];
+    LBM_CUDA(launch_init(P, c->prec, c->het, true, 0.0f, 0.0f, 0.0f, 0, (float)T_init, false, true, c->stream), "init kernel");
+  }
   c->steps = 0;
   c->history = 0;
   return LBM_OK;
@@ -573,11 +609,21 @@ namespace {
 
 StepParams params_at(const lbm_ctx* c, int cur) {
   StepParams P = params_for(c);
-  P.src = c->f[cur];
-  P.dst = c->f[cur ^ 1];
-  P.gsrc = c->g[cur];
-  P.gdst = c->g[cur ^ 1];
+  if (c->inplace) {
+    P.parity = cur;
+  } else {
+    P.src = c->f[cur];
+    P.dst = c->f[cur ^ 1];
+    P.gsrc = c->g[cur];
+    P.gdst = c->g[cur ^ 1];
+  }
   return P;
+}
+
+// one step from buffer (A-B) or parity (in-place) `cur`
+cudaError_t launch_step_at(const lbm_ctx* c, int cur, cudaStream_t s) {
+  const StepParams P = params_at(c, cur);
+  return c->inplace ? launch_step_inplace(P, c->prec, c->het, thermal_of(c), s) : launch_step(P, c->prec, c->het, thermal_of(c), s);
 }
 
 // Instantiate the graph of kGraphSteps steps that starts from buffer `cur`.
@@ -586,7 +632,7 @@ int capture_graph(lbm_ctx* c, int cur) {
   LBM_CUDA(cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
   cudaError_t launch_err = cudaSuccess;
   for (int k = 0; k < kGraphSteps && launch_err == cudaSuccess; ++k)
-    launch_err = launch_step(params_at(c, cur ^ (k & 1)), c->prec, c->het, thermal_of(c), c->capture_stream);
+    launch_err = launch_step_at(c, cur ^ (k & 1), c->capture_stream);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(c->capture_stream, &g);
   if (launch_err != cudaSuccess || e != cudaSuccess) {
@@ -604,9 +650,9 @@ int capture_graph(lbm_ctx* c, int cur) {
 
 }  // namespace
 
-int lbm_step(lbm_ctx* c, int n) {
-  if (!c) return fail(LBM_EINVAL, "null context");
-  if (n < 0) return fail(LBM_EINVAL, "negative step count");
+namespace {
+
+int run_steps(lbm_ctx* c, int n) {
   while (n >= kGraphSteps) {  // replay a captured graph of kGraphSteps steps
     if (!c->graph[c->cur]) {
       int rc = capture_graph(c, c->cur);
@@ -618,12 +664,27 @@ int lbm_step(lbm_ctx* c, int n) {
     n -= kGraphSteps;
   }
   for (int k = 0; k < n; ++k) {
-    LBM_CUDA(launch_step(params_at(c, c->cur), c->prec, c->het, thermal_of(c), c->stream), "step kernel");
+    LBM_CUDA(launch_step_at(c, c->cur, c->stream), "step kernel");
     c->cur ^= 1;
     ++c->steps;
     ++c->history;
   }
   return LBM_OK;
+}
+
+}  // namespace
+
+int lbm_step(lbm_ctx* c, int n) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  if (n < 0) return fail(LBM_EINVAL, "negative step count");
+  if (!c->inplace || n == 0) return run_steps(c, n);
+  // in-place: u(t-1) of the residual is recorded before the last step (its state is overwritten)
+  int rc = run_steps(c, n - 1);
+  if (rc) return rc;
+  const size_t nn = (size_t)c->cfg.nx * c->cfg.ny;
+  LBM_CUDA(launch_macros(params_for(c), c->prec, c->het, thermal_of(c), nullptr, c->uprev, c->uprev + nn, nullptr, c->stream),
+           "macros kernel");
+  return run_steps(c, 1);
 }
 
 int lbm_set_walls(lbm_ctx* c, const float* u_wall) {
@@ -692,9 +753,14 @@ int lbm_set_populations(lbm_ctx* c, const float* f, const float* g) {
   const float *df = nullptr, *dg = nullptr;
   if ((rc = input_ptr(c, f, 8 * n, 0, &df)) || (rc = input_ptr(c, g, 5 * n, 8 * n, &dg))) return rc;
   StepParams P = params_for(c);
-  P.dst = c->f[c->cur];
-  P.gdst = c->g[c->cur];
-  LBM_CUDA(launch_import(P, c->prec, df, dg, c->stream), "import kernel");
+  if (c->inplace) {
+    LBM_CUDA(launch_put_inplace(P, c->prec, c->het, df, dg, df != nullptr, dg != nullptr, 0.0f, 0.0f, 0.0f, 0, 0.0f, c->stream),
+             "import kernel");
+  } else {
+    P.dst = c->f[c->cur];
+    P.gdst = c->g[c->cur];
+    LBM_CUDA(launch_import(P, c->prec, df, dg, c->stream), "import kernel");
+  }
   c->history = 0;
   if (any_host(c, ptrs, 2)) LBM_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
   return LBM_OK;
@@ -706,8 +772,13 @@ int lbm_residual(lbm_ctx* c, double* r) {
   StepParams P = params_for(c);
   const int nb = residual_blocks((int)c->cfg.nx, (int)c->cfg.ny);
   double* out = c->red + 2 * kResidualMaxBlocks;
-  LBM_CUDA(launch_residual(P, c->prec, c->het, thermal_of(c), c->f[c->cur ^ 1], c->g[c->cur ^ 1], c->red, nb, out, c->stream),
-           "residual kernels");
+  if (c->inplace)
+    LBM_CUDA(launch_residual(P, c->prec, c->het, thermal_of(c), nullptr, nullptr, c->uprev, c->red, nb, out, c->stream),
+             "residual kernels");
+  else
+    LBM_CUDA(launch_residual(P, c->prec, c->het, thermal_of(c), c->f[c->cur ^ 1], c->g[c->cur ^ 1], nullptr, c->red, nb, out,
+                             c->stream),
+             "residual kernels");
   double h[2];
   LBM_CUDA(cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "read of residual");
   LBM_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
@@ -804,6 +875,7 @@ int lbm_adjoint(lbm_ctx* c, int T, int loss_kind, const float* target_ux, const 
   if (loss_kind != LBM_LOSS_OUTLET_FLUX && loss_kind != LBM_LOSS_VELOCITY_MISFIT) return fail(LBM_EINVAL, "unknown loss kind");
   if (loss_kind == LBM_LOSS_VELOCITY_MISFIT && (!target_ux || !target_uy)) return fail(LBM_EINVAL, "misfit loss needs a target");
   if (thermal_of(c)) return fail(LBM_ESTATE, "the adjoint covers the isothermal flow step only");
+  if (c->inplace) return fail(LBM_ESTATE, "the adjoint needs A-B streaming (its checkpoints are A-B states)");
   if (c->cfg.bc_x == LBM_NEE || c->cfg.bc_y == LBM_NEE)
     return fail(LBM_ESTATE, "the adjoint covers halfway walls, periodic sides and pressure columns, not extrapolated wall nodes");
   if (c->steps != 0 || c->history != 0)
@@ -908,12 +980,12 @@ int lbm_release_workspace(lbm_ctx* c) {
 namespace {
 
 constexpr uint32_t kSaveMagic = 0x4C424D53u;  // "LBMS"
-constexpr uint32_t kSaveVersion = 2u;
+constexpr uint32_t kSaveVersion = 3u;
 
 struct SaveHeader {
   uint32_t magic, version, config_size, precision;
   uint32_t nx, ny, pitch, thermal;
-  int32_t cur, het, init_phip, pad;
+  int32_t cur, het, init_phip, inplace;
   int64_t steps, history;
   double init_p0, init_ux, init_uy;
   uint64_t pop_bytes, therm_bytes, medium_bytes, sv_bytes;
@@ -941,6 +1013,7 @@ int lbm_save(lbm_ctx* c, const char* path) {
   h.cur = c->cur;
   h.het = c->het ? 1 : 0;
   h.init_phip = c->init_phip;
+  h.inplace = c->inplace ? 1 : 0;
   h.steps = c->steps;
   h.history = c->history;
   h.init_p0 = c->init_p0;
@@ -957,14 +1030,21 @@ int lbm_save(lbm_ctx* c, const char* path) {
   lbm_config cfg = c->cfg;
   cfg.stream = nullptr;
   if (fwrite(&h, sizeof(h), 1, f) != 1 || fwrite(&cfg, sizeof(cfg), 1, f) != 1) return io_fail(f, "write failed");
-  // both population buffers (the previous one serves the residual), temperature, medium
-  for (int b = 0; b < 2; ++b) {
+  // both population buffers (the previous one serves the residual; in-place: the one buffer and
+  // the recorded u(t-1)), temperature, medium
+  for (int b = 0; b < (c->inplace ? 1 : 2); ++b) {
     if (cudaMemcpy(host.data(), c->f[b], h.pop_bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return io_fail(f, "device read failed");
     if (fwrite(host.data(), 1, h.pop_bytes, f) != h.pop_bytes) return io_fail(f, "write failed");
     if (h.therm_bytes) {
       if (cudaMemcpy(host.data(), c->g[b], h.therm_bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return io_fail(f, "device read failed");
       if (fwrite(host.data(), 1, h.therm_bytes, f) != h.therm_bytes) return io_fail(f, "write failed");
     }
+  }
+  if (c->inplace) {
+    const size_t ub = 2 * (size_t)c->cfg.nx * c->cfg.ny * sizeof(float);
+    std::vector<char> u(ub);
+    if (cudaMemcpy(u.data(), c->uprev, ub, cudaMemcpyDeviceToHost) != cudaSuccess) return io_fail(f, "device read failed");
+    if (fwrite(u.data(), 1, ub, f) != ub) return io_fail(f, "write failed");
   }
   if (h.medium_bytes) {
     float* fields[2] = {c->phi, c->K};
@@ -991,12 +1071,12 @@ int lbm_load(lbm_ctx* c, const char* path) {
   if (h.version != kSaveVersion || h.config_size != sizeof(lbm_config)) return io_fail(f, "state file of another format version");
   if (fread(&cfg, sizeof(cfg), 1, f) != 1) return io_fail(f, "truncated state file");
   if (h.nx != c->cfg.nx || h.ny != c->cfg.ny || (int)h.precision != c->prec || (h.thermal != 0) != (c->cfg.thermal != 0) ||
-      (int)h.pitch != c->pitch)
-    return io_fail(f, "state file does not match the context (size, precision or thermal)");
+      (int)h.pitch != c->pitch || (h.inplace != 0) != c->inplace)
+    return io_fail(f, "state file does not match the context (size, precision, thermal or streaming)");
   if (h.pop_bytes != 8 * (uint64_t)c->plane * c->elem) return io_fail(f, "state file layout mismatch");
   std::vector<char> host(h.pop_bytes > h.medium_bytes ? h.pop_bytes : h.medium_bytes);
   LBM_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
-  for (int b = 0; b < 2; ++b) {
+  for (int b = 0; b < (c->inplace ? 1 : 2); ++b) {
     if (fread(host.data(), 1, h.pop_bytes, f) != h.pop_bytes) return io_fail(f, "truncated state file");
     if (cudaMemcpy(c->f[b], host.data(), h.pop_bytes, cudaMemcpyHostToDevice) != cudaSuccess) return io_fail(f, "device write failed");
     if (h.therm_bytes) {
@@ -1004,6 +1084,12 @@ int lbm_load(lbm_ctx* c, const char* path) {
       if (cudaMemcpy(c->g[b], host.data(), h.therm_bytes, cudaMemcpyHostToDevice) != cudaSuccess)
         return io_fail(f, "device write failed");
     }
+  }
+  if (c->inplace) {
+    const size_t ub = 2 * (size_t)c->cfg.nx * c->cfg.ny * sizeof(float);
+    std::vector<char> u(ub);
+    if (fread(u.data(), 1, ub, f) != ub) return io_fail(f, "truncated state file");
+    if (cudaMemcpy(c->uprev, u.data(), ub, cudaMemcpyHostToDevice) != cudaSuccess) return io_fail(f, "device write failed");
   }
   drop_graphs(c);
   if (h.medium_bytes) {

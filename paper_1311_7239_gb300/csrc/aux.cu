@@ -276,9 +276,12 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
   }
 }
 
-// Pass 1: per-block partial sums of |u(t) - u(t-1)|^2 and |u(t)|^2 into partial[2 * block].
+// Pass 1: per-block partial sums of |u(t) - u(t-1)|^2 and |u(t)|^2 into partial[2 * block];
+// u(t-1) from the previous state (prev, gprev) or, if uprev is given, from its recorded
+// components (dense [2][ny][nx]).
 template <int PREC, bool HET, bool THERMAL>
-__global__ void k_residual_partial(const StepParams P, const void* prev, const void* gprev, double* __restrict__ partial) {
+__global__ void k_residual_partial(const StepParams P, const void* prev, const void* gprev, const float* __restrict__ uprev,
+                                   double* __restrict__ partial) {
   double num = 0.0, den = 0.0;
   const int64_t n = (int64_t)P.nx * P.ny;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
@@ -287,9 +290,17 @@ __global__ void k_residual_partial(const StepParams P, const void* prev, const v
     float d[8], gd[5], ay;
     gather_state<PREC, HET, THERMAL>(P, P.src, P.gsrc, x, y, d, gd, ay);
     const Macro a = macro_d2q8(d, c, P.ax, ay, P.rho0);
-    gather_state<PREC, HET, THERMAL>(P, prev, gprev, x, y, d, gd, ay);
-    const Macro b = macro_d2q8(d, c, P.ax, ay, P.rho0);
-    const double dx = (double)a.ux - (double)b.ux, dy = (double)a.uy - (double)b.uy;
+    double bx, by;
+    if (uprev) {
+      bx = uprev[k];
+      by = uprev[n + k];
+    } else {
+      gather_state<PREC, HET, THERMAL>(P, prev, gprev, x, y, d, gd, ay);
+      const Macro b = macro_d2q8(d, c, P.ax, ay, P.rho0);
+      bx = b.ux;
+      by = b.uy;
+    }
+    const double dx = (double)a.ux - bx, dy = (double)a.uy - by;
     num += dx * dx + dy * dy;
     den += (double)a.ux * a.ux + (double)a.uy * a.uy;
   }
@@ -438,8 +449,8 @@ int residual_blocks(int nx, int ny) {
 }
 
 cudaError_t launch_residual(const StepParams& P, int prec, bool het, bool thermal, const void* prev, const void* gprev,
-                            double* partial, int nblocks, double* out, cudaStream_t s) {
-#define CALL_RES(PR, H, TH) k_residual_partial<PR, H, TH><<<nblocks, 256, 0, s>>>(P, prev, gprev, partial)
+                            const float* uprev, double* partial, int nblocks, double* out, cudaStream_t s) {
+#define CALL_RES(PR, H, TH) k_residual_partial<PR, H, TH><<<nblocks, 256, 0, s>>>(P, prev, gprev, uprev, partial)
   LBM_DISPATCH_PHT(prec, het, thermal, CALL_RES);
 #undef CALL_RES
   k_sum_partials<<<1, 256, 0, s>>>(partial, nblocks, out);

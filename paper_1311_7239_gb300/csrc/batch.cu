@@ -220,6 +220,7 @@ int lbm_batch_create(const lbm_config* cfgs, int n, lbm_batch** out) {
     int rc = validate_config(&cfgs[d]);
     if (rc) return rc;
     if (cfgs[d].thermal) return fail_msg(LBM_EINVAL, "lbm_batch_create: batches hold isothermal lattices only");
+    if (cfgs[d].streaming != LBM_STREAM_AB) return fail_msg(LBM_EINVAL, "lbm_batch_create: batches use A-B streaming");
     if (cfgs[d].precision != cfgs[0].precision) return fail_msg(LBM_EINVAL, "lbm_batch_create: all lattices need one precision");
   }
   lbm_batch* b = new (std::nothrow) lbm_batch();

@@ -1,0 +1,270 @@
+// In-place ("esoteric pull") form of the fused stream-collide step: one population buffer instead
+// of the two of the A-B form, with the same arithmetic per cell (Eqs. 6-20, and Eq. B.2 for the
+// temperature).  The slot rules are those of ip_off in lbm_device.cuh: at parity PAR a cell reads
+// population i from plane (PAR ? i : opp(i)), at the cell itself for the positive member of each
+// opposite pair (e1, e2, e5, e8) and at c - e_i for the others, and writes its post-collision
+// population opp(i) back into the slot it read i from.  Per step and cell the traffic is that of
+// the A-B form (8 loads, 8 stores); the footprint of the populations halves.
+//
+// Work split: a thread updates four consecutive cells of one row.  Of the slots it touches, five
+// are the aligned four-cell vectors of rows y and y + 1 (positive members and e4 = (0, -1)); the
+// three with e_x = -1 sit one cell to the right (x0 + 1 .. x0 + 4) and are moved as one cell, an
+// aligned pair and one cell, so that a thread touches no slot of another thread's cells.  Groups
+// with a cell on a wall or on the last column (where the right neighbour wraps or is a ghost
+// slot) take the generic per-cell rules.
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+
+namespace lbm {
+
+constexpr int kIpThreads = 128;
+constexpr int kIpCells = 4;
+
+// one cell with the generic slot rules: pulls with bounce-back, collision, stores into the slots
+// of the next parity (ghost slots for populations that leave through a wall)
+template <int PREC, bool HET, bool THERMAL>
+__device__ __forceinline__ void ip_cell(const StepParams& P, typename Store<PREC>::T* A, typename Store<PREC>::T* G, int x, int y) {
+  using S = Store<PREC>;
+  float d[8], g[5];
+  pull_cell<PREC>(P, A, x, y, d);
+  float ay = P.ay;
+  if (THERMAL) {
+    pull_cell_g<PREC>(P, G, x, y, g);
+    ay += P.g_beta * (g[0] + g[1] + g[2] + g[3] + g[4]);  // a = g beta (T - T0) j
+  }
+  const Coef cf = coef_at<HET>(P, x, y);
+  float ux, uy, phip;
+  collide_d2q8(d, cf, P.ax, ay, P, ux, uy, phip);
+  if (!(fabsf(ux) + fabsf(uy) < 1e30f)) atomicOr(P.err, 1u);
+  const int nxt = P.parity ^ 1;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) A[ip_off(P, x + ex_of(j), y + ey_of(j), j, nxt)] = S::enc(d[j], P.scale);
+  if (THERMAL) {
+    collide_d2q5(g, ux, uy, P);
+#pragma unroll
+    for (int j = 0; j < 5; ++j) G[ip_off5(P, x + ex5(j), y + ey5(j), j, nxt)] = S::enc(g[j], P.scale);
+  }
+}
+
+// cells x0 + 1 .. x0 + 4 of a row: one cell, an aligned pair, one cell
+template <int PREC>
+__device__ __forceinline__ void load_right(const typename Store<PREC>::T* row, int x0, float inv, float o[4]) {
+  using S = Store<PREC>;
+  o[0] = S::dec(row[x0 + 1], inv);
+  S::load2(row + x0 + 2, o + 1, inv);
+  o[3] = S::dec(row[x0 + 4], inv);
+}
+
+template <int PREC>
+__device__ __forceinline__ void store_right(typename Store<PREC>::T* row, int x0, const float v[4], float sc) {
+  using S = Store<PREC>;
+  row[x0 + 1] = S::enc(v[0], sc);
+  S::store2r(row + x0 + 2, make_float2(v[1] * sc, v[2] * sc));
+  row[x0 + 4] = S::enc(v[3], sc);
+}
+
+template <int PAR>
+__device__ __forceinline__ constexpr int plane_of(int i) {
+  return PAR ? i : (i < 4 ? (i + 2) & 3 : 4 + ((i - 4 + 2) & 3));
+}
+
+// Register caps: 8 CTAs of 128 threads per SM for the flow (64 registers, as the A-B step), 5 with
+// the temperature populations (96; at 80 the FP32 thermal step spills).
+template <int PREC, bool HET, bool THERMAL, int PAR>
+__global__ void __launch_bounds__(kIpThreads, THERMAL ? 5 : 8) k_step_ip(const StepParams P) {
+  using S = Store<PREC>;
+  using T = typename S::T;
+  constexpr int C = kIpCells;
+  const int y = blockIdx.y;
+  const int x0 = (blockIdx.x * kIpThreads + threadIdx.x) * C;
+  if (x0 >= P.nx) return;
+  T* __restrict__ A = static_cast<T*>(P.dst);
+  T* __restrict__ G = static_cast<T*>(P.gdst);
+  const bool edge = (P.bc_x == BC_WALL && x0 == 0) || x0 + C >= P.nx || (P.bc_y == BC_WALL && (y == 0 || y == P.ny - 1));
+  if (edge) {
+    for (int c = 0; c < C && x0 + c < P.nx; ++c) ip_cell<PREC, HET, THERMAL>(P, A, G, x0 + c, y);
+    return;
+  }
+  // rows y - 1 and y + 1 (periodic wrap; wall rows are edge groups)
+  const int ym = y == 0 ? P.ny - 1 : y - 1;
+  const int yp = y == P.ny - 1 ? 0 : y + 1;
+  const int64_t rm = (int64_t)ym * P.pitch, r0 = (int64_t)y * P.pitch, rp = (int64_t)yp * P.pitch;
+  const float inv = P.inv_scale;
+  float4 ph4, k4;
+  if (HET) {
+    ph4 = __ldg(reinterpret_cast<const float4*>(P.phi + r0 + x0));
+    k4 = __ldg(reinterpret_cast<const float4*>(P.K + r0 + x0));
+  }
+  // pull, Eq. 15: the slot of population i (see ip_off), as 32-bit element offsets from A (a
+  // buffer holds fewer than 2^32 elements; lbm_create checks): plane * pl + y0x (+ the row change
+  // dp or dm for the slots of rows y + 1 and y - 1)
+  const uint32_t pl = (uint32_t)P.plane;
+  const uint32_t y0x = (uint32_t)r0 + (uint32_t)x0;
+  const uint32_t dp = (uint32_t)(rp - r0), dm = (uint32_t)(rm - r0);
+  float d[8][C];
+  S::load4(A + plane_of<PAR>(0) * pl + y0x, d[0], inv);             // e1 = ( 1, 0): own cells
+  S::load4(A + plane_of<PAR>(1) * pl + y0x, d[1], inv);             // e2 = ( 0, 1): own cells
+  load_right<PREC>(A + plane_of<PAR>(2) * pl + y0x, 0, inv, d[2]);  // e3 = (-1, 0): cells x + 1 of row y
+  S::load4(A + (plane_of<PAR>(3) * pl + y0x + dp), d[3], inv);      // e4 = ( 0,-1): cells of row y + 1
+  S::load4(A + plane_of<PAR>(4) * pl + y0x, d[4], inv);             // e5 = ( 1, 1): own cells
+  load_right<PREC>(A + (plane_of<PAR>(5) * pl + y0x + dm), 0, inv, d[5]);  // e6 = (-1, 1): cells x + 1 of row y - 1
+  load_right<PREC>(A + (plane_of<PAR>(6) * pl + y0x + dp), 0, inv, d[6]);  // e7 = (-1,-1): cells x + 1 of row y + 1
+  S::load4(A + plane_of<PAR>(7) * pl + y0x, d[7], inv);             // e8 = ( 1,-1): own cells
+  float g[5][C];
+  if (THERMAL) {
+    S::load4(G + y0x, g[0], inv);                                    // rest population
+    S::load4(G + (PAR ? 1 : 3) * pl + y0x, g[1], inv);               // ( 1, 0): own cells
+    S::load4(G + (PAR ? 2 : 4) * pl + y0x, g[2], inv);               // ( 0, 1): own cells
+    load_right<PREC>(G + (PAR ? 3 : 1) * pl + y0x, 0, inv, g[3]);    // (-1, 0): cells x + 1
+    S::load4(G + ((PAR ? 4 : 2) * pl + y0x + dp), g[4], inv);        // ( 0,-1): row y + 1
+  }
+  float check = 0.0f;
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    float dc[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) dc[i] = d[i][c];
+    const Coef cf = HET ? coef_of(P, f4_get(ph4, c), f4_get(k4, c), P.sv ? __ldg(P.sv + r0 + x0 + c) : P.s_v) : coef_uniform(P);
+    float ay = P.ay;
+    if (THERMAL) ay += P.g_beta * (g[0][c] + g[1][c] + g[2][c] + g[3][c] + g[4][c]);
+    float ux, uy, phip;
+    collide_d2q8(dc, cf, P.ax, ay, P, ux, uy, phip);
+    check += fabsf(ux) + fabsf(uy);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) d[i][c] = dc[i];
+    if (THERMAL) {
+      float gc[5];
+#pragma unroll
+      for (int i = 0; i < 5; ++i) gc[i] = g[i][c];
+      collide_d2q5(gc, ux, uy, P);
+#pragma unroll
+      for (int i = 0; i < 5; ++i) g[i][c] = gc[i];
+    }
+  }
+  if (!(check < 1e30f)) atomicOr(P.err, 1u);  // non-finite velocity in these cells
+  // post-collision population opp(i) into the slot population i came from; the offsets are formed
+  // again from an opaque copy of y0x rather than kept live through the collision
+  uint32_t b0 = y0x;
+  asm volatile("" : "+r"(b0));
+  const float sc = P.scale;
+  S::store4(A + plane_of<PAR>(0) * pl + b0, d[2], sc);
+  S::store4(A + plane_of<PAR>(1) * pl + b0, d[3], sc);
+  store_right<PREC>(A + plane_of<PAR>(2) * pl + b0, 0, d[0], sc);
+  S::store4(A + (plane_of<PAR>(3) * pl + b0 + dp), d[1], sc);
+  S::store4(A + plane_of<PAR>(4) * pl + b0, d[6], sc);
+  store_right<PREC>(A + (plane_of<PAR>(5) * pl + b0 + dm), 0, d[7], sc);
+  store_right<PREC>(A + (plane_of<PAR>(6) * pl + b0 + dp), 0, d[4], sc);
+  S::store4(A + plane_of<PAR>(7) * pl + b0, d[5], sc);
+  if (THERMAL) {
+    S::store4(G + b0, g[0], sc);
+    S::store4(G + (PAR ? 1 : 3) * pl + b0, g[3], sc);
+    S::store4(G + (PAR ? 2 : 4) * pl + b0, g[4], sc);
+    store_right<PREC>(G + (PAR ? 3 : 1) * pl + b0, 0, g[1], sc);
+    S::store4(G + ((PAR ? 4 : 2) * pl + b0 + dp), g[2], sc);
+  }
+}
+
+template <int PREC, bool HET, bool THERMAL>
+static cudaError_t launch_ip_t(const StepParams& P, cudaStream_t s) {
+  const int groups = (P.nx + kIpCells - 1) / kIpCells;
+  const dim3 grid((groups + kIpThreads - 1) / kIpThreads, P.ny);
+  if (P.parity)
+    k_step_ip<PREC, HET, THERMAL, 1><<<grid, kIpThreads, 0, s>>>(P);
+  else
+    k_step_ip<PREC, HET, THERMAL, 0><<<grid, kIpThreads, 0, s>>>(P);
+  return cudaGetLastError();
+}
+
+template <int PREC>
+static cudaError_t launch_ip_p(const StepParams& P, bool het, bool thermal, cudaStream_t s) {
+  if (thermal) return het ? launch_ip_t<PREC, true, true>(P, s) : launch_ip_t<PREC, false, true>(P, s);
+  return het ? launch_ip_t<PREC, true, false>(P, s) : launch_ip_t<PREC, false, false>(P, s);
+}
+
+cudaError_t launch_step_inplace(const StepParams& P, int prec, bool het, bool thermal, cudaStream_t s) {
+  switch (prec) {
+    case PREC_FP32: return launch_ip_p<PREC_FP32>(P, het, thermal, s);
+    case PREC_FP16: return launch_ip_p<PREC_FP16>(P, het, thermal, s);
+    default: return launch_ip_p<PREC_BF16>(P, het, thermal, s);
+  }
+}
+
+// --------------------------------------------------------------------------------------------
+// Writing a pre-collision state f(x, t) into the in-place layout of the current parity: every
+// population goes to the slot that the next step's pull reads it from (for a link that crosses a
+// wall, the parked slot, holding the value minus the moving-wall term, or for an isothermal wall
+// the anti-bounce-back inverse).
+// --------------------------------------------------------------------------------------------
+// flow: f (dense [8][ny][nx] float32, full populations) or, if f is null, the equilibrium of
+// Eq. 22 at (p0, u0) (phi p = p0 when phip_uniform, else phi p0)
+template <int PREC, bool HET>
+__global__ void k_put_flow_ip(const StepParams P, const float* __restrict__ f, float p0, float ux0, float uy0, int phip_uniform) {
+  using S = Store<PREC>;
+  using T = typename S::T;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  if (x >= P.nx) return;
+  T* A = static_cast<T*>(P.dst);
+  float d[8];
+  if (f) {
+    const int64_t dense = (int64_t)P.nx * P.ny, o = (int64_t)y * P.nx + x;
+    for (int i = 0; i < 8; ++i) d[i] = f[i * dense + o] - 3.0f * w_of(i) * P.p_rest;
+  } else {
+    const Coef c = coef_at<HET>(P, x, y);
+    feq_dev_d2q8((phip_uniform ? p0 : c.phi * p0) - P.p_rest, ux0, uy0, c.inv_phi, P.rho0, d);
+  }
+  for (int i = 0; i < 8; ++i) {
+    int w;
+    const int64_t at = ip_source(P, x, y, i, w);
+    A[at] = S::enc(w < 0 ? d[i] : d[i] - wall_term(P, i, w), P.scale);
+  }
+}
+
+// temperature: g (dense [5][ny][nx]) or, if g is null, the equilibrium of Eq. B.6 at T_init, u = 0
+template <int PREC>
+__global__ void k_put_thermal_ip(const StepParams P, const float* __restrict__ g, float T_init) {
+  using S = Store<PREC>;
+  using T = typename S::T;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  if (x >= P.nx) return;
+  T* G = static_cast<T*>(P.gdst);
+  float z[5];
+  if (g) {
+    const int64_t dense = (int64_t)P.nx * P.ny, o = (int64_t)y * P.nx + x;
+    for (int i = 0; i < 5; ++i) z[i] = g[i * dense + o] - 0.2f * P.T0;
+  } else {
+    geq_dev(P, T_init, 0.0f, 0.0f, z);
+  }
+  for (int i = 0; i < 5; ++i) {
+    int w;
+    const int64_t at = ip_source5(P, x, y, i, w);
+    // inverse of the pull: z = v (bounce-back) or z = -v + 2 (T_w - T0) / 5 (anti-bounce-back)
+    const float v = (w < 0 || !P.Tdir[w]) ? z[i] : (0.4f * (P.Tw[w] - P.T0) - z[i]);
+    G[at] = S::enc(v, P.scale);
+  }
+}
+
+cudaError_t launch_put_inplace(const StepParams& P, int prec, bool het, const float* f, const float* g, bool flow, bool temp,
+                               float p0, float ux0, float uy0, int phip_uniform, float T_init, cudaStream_t s) {
+  const dim3 grid((P.nx + 127) / 128, P.ny);
+  if (flow) {
+#define LBM_PUT(PR)                                                                                       \
+  do {                                                                                                    \
+    if (het) k_put_flow_ip<PR, true><<<grid, 128, 0, s>>>(P, f, p0, ux0, uy0, phip_uniform);            \
+    else k_put_flow_ip<PR, false><<<grid, 128, 0, s>>>(P, f, p0, ux0, uy0, phip_uniform);               \
+  } while (0)
+    if (prec == PREC_FP32) LBM_PUT(PREC_FP32);
+    else if (prec == PREC_FP16) LBM_PUT(PREC_FP16);
+    else LBM_PUT(PREC_BF16);
+#undef LBM_PUT
+  }
+  if (temp) {
+    if (prec == PREC_FP32) k_put_thermal_ip<PREC_FP32><<<grid, 128, 0, s>>>(P, g, T_init);
+    else if (prec == PREC_FP16) k_put_thermal_ip<PREC_FP16><<<grid, 128, 0, s>>>(P, g, T_init);
+    else k_put_thermal_ip<PREC_BF16><<<grid, 128, 0, s>>>(P, g, T_init);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -50,6 +50,8 @@ struct StepParams {
   int64_t plane;     // elements per plane = ny * pitch
   int bc_x, bc_y;
   int forch;
+  int inplace;       // 1: one population buffer with in-place streaming (see ip_off), 0: A-B buffers
+  int parity;        // in-place: parity of the next step (selects the slots it loads from)
   float rho0, inv_rho0, nu, s_e, s_q, s_v;
   float ax, ay;
   // uniform-medium coefficients
@@ -481,10 +483,91 @@ __device__ __forceinline__ int wall_of(int sx, int sy, int ny) {
   return sx < 0 ? 0 : 1;
 }
 
+// ---------------------------------------------------------------------------------------------
+// In-place streaming: one population buffer.  Of each pair of opposite velocities the member with
+// e_x > 0, or e_x = 0 and e_y > 0 (e1, e2, e5, e8), is "positive".  At parity par a cell c reads
+// population i from plane (par ? i : opp(i)) at c itself when i is positive and at c - e_i
+// otherwise, and writes its post-collision population j where the cell c + e_j reads j at the
+// next parity.  The slots a cell writes are then exactly the slots it read (each receives the
+// population opposite to the one read from it), so the two halves of Eq. 15 share one buffer
+// without races and the buffer alternates between two layouts.  Populations that leave through a
+// wall are parked in ghost slots (rows -1 and ny, column nx; never updated as cells) until the
+// same cell reads them back as its bounce-back (Eq. 15 at a wall).  Only periodic and halfway-wall
+// sides are supported.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ bool ip_positive(int i) { return i == 0 || i == 1 || i == 4 || i == 7; }
+
+__device__ __forceinline__ int wrap_periodic(int v, int n, bool periodic) {
+  return periodic ? (v < 0 ? v + n : (v >= n ? v - n : v)) : v;
+}
+
+// element offset of the slot from which cell (cx, cy) (a lattice or ghost cell) reads population
+// i at parity par
+__device__ __forceinline__ int64_t ip_off(const StepParams& P, int cx, int cy, int i, int par) {
+  if (!ip_positive(i)) {
+    cx -= ex_of(i);
+    cy -= ey_of(i);
+  }
+  cx = wrap_periodic(cx, P.nx, P.bc_x == BC_PERIODIC);
+  cy = wrap_periodic(cy, P.ny, P.bc_y == BC_PERIODIC);
+  dbg_check(P, cx >= 0 && cx <= P.nx && cx < P.pitch && cy >= -1 && cy <= P.ny);
+  return (int64_t)(par ? i : opp_of(i)) * P.plane + (int64_t)cy * P.pitch + cx;
+}
+
+// the same for the D2Q5 temperature populations (positive: 1 and 2; the rest population stays)
+__device__ __forceinline__ int64_t ip_off5(const StepParams& P, int cx, int cy, int i, int par) {
+  if (i == 3 || i == 4) {
+    cx -= ex5(i);
+    cy -= ey5(i);
+  }
+  cx = wrap_periodic(cx, P.nx, P.bc_x == BC_PERIODIC);
+  cy = wrap_periodic(cy, P.ny, P.bc_y == BC_PERIODIC);
+  dbg_check(P, cx >= 0 && cx <= P.nx && cx < P.pitch && cy >= -1 && cy <= P.ny);
+  const int plane = i == 0 ? 0 : (par ? i : opp5(i));
+  return (int64_t)plane * P.plane + (int64_t)cy * P.pitch + cx;
+}
+
+// Source of the pull of population i into cell (x, y) at the current parity: the slot the cell
+// reads (wall = -1), or, where x - e_i lies beyond a wall, the slot in which the cell parked its
+// own post-collision population opp(i) (wall = the wall's index).
+__device__ __forceinline__ int64_t ip_source(const StepParams& P, int x, int y, int i, int& wall) {
+  int sx = x - ex_of(i), sy = y - ey_of(i);
+  sx = wrap_periodic(sx, P.nx, P.bc_x == BC_PERIODIC);
+  sy = wrap_periodic(sy, P.ny, P.bc_y == BC_PERIODIC);
+  if (sx >= 0 && sx < P.nx && sy >= 0 && sy < P.ny) {
+    wall = -1;
+    return ip_off(P, x, y, i, P.parity);
+  }
+  wall = wall_of(sx, sy, P.ny);
+  return ip_off(P, sx, sy, opp_of(i), P.parity);
+}
+
+__device__ __forceinline__ int64_t ip_source5(const StepParams& P, int x, int y, int i, int& wall) {
+  int sx = x - ex5(i), sy = y - ey5(i);
+  sx = wrap_periodic(sx, P.nx, P.bc_x == BC_PERIODIC);
+  sy = wrap_periodic(sy, P.ny, P.bc_y == BC_PERIODIC);
+  if (sx >= 0 && sx < P.nx && sy >= 0 && sy < P.ny) {
+    wall = -1;
+    return ip_off5(P, x, y, i, P.parity);
+  }
+  wall = wall_of(sx, sy, P.ny);
+  return ip_off5(P, sx, sy, opp5(i), P.parity);
+}
+
+// momentum correction of the moving-wall bounce-back, 2 w_i rho0 (e_i . u_w) / c_s^2
+__device__ __forceinline__ float wall_term(const StepParams& P, int i, int w) {
+  return 6.0f * w_of(i) * P.rho0 * ((float)ex_of(i) * __ldg(P.uw + 2 * w) + (float)ey_of(i) * __ldg(P.uw + 2 * w + 1));
+}
+
 template <int PREC>
 __device__ __forceinline__ float pull_one(const StepParams& P, const typename Store<PREC>::T* src, int x, int y, int i) {
   using S = Store<PREC>;
   if (!dbg_check(P, x >= 0 && x < P.pitch && y >= 0 && y < P.ny)) return 0.0f;
+  if (P.inplace) {
+    int w;
+    const float v = S::dec(src[ip_source(P, x, y, i, w)], P.inv_scale);
+    return w < 0 ? v : v + wall_term(P, i, w);
+  }
   int sx = x - ex_of(i), sy = y - ey_of(i);
   if (P.bc_x != BC_WALL) sx = (sx + P.nx) % P.nx;
   if (P.bc_y != BC_WALL) sy = (sy + P.ny) % P.ny;
@@ -508,6 +591,11 @@ template <int PREC>
 __device__ __forceinline__ float pull_one_g(const StepParams& P, const typename Store<PREC>::T* src, int x, int y, int i) {
   using S = Store<PREC>;
   if (!dbg_check(P, x >= 0 && x < P.pitch && y >= 0 && y < P.ny)) return 0.0f;
+  if (P.inplace) {
+    int w;
+    const float v = S::dec(src[ip_source5(P, x, y, i, w)], P.inv_scale);
+    return (w < 0 || !P.Tdir[w]) ? v : (-v + 0.4f * (P.Tw[w] - P.T0));
+  }
   if (i == 0) return S::dec(src[(int64_t)y * P.pitch + x], P.inv_scale);
   int sx = x - ex5(i), sy = y - ey5(i);
   if (P.bc_x != BC_WALL) sx = (sx + P.nx) % P.nx;

@@ -21,6 +21,9 @@ int batch_max_ctas_per_sm(int prec, int nt);
 cudaError_t launch_step_batch(const StepParams* Pd, const int64_t* item_start, const int* item_lattice, int n, int64_t total, int prec,
                               int nt, int grid, cudaStream_t s);
 cudaError_t launch_step(const StepParams& P, int prec, bool het, bool thermal, cudaStream_t s);
+cudaError_t launch_step_inplace(const StepParams& P, int prec, bool het, bool thermal, cudaStream_t s);
+cudaError_t launch_put_inplace(const StepParams& P, int prec, bool het, const float* f, const float* g, bool flow, bool temp,
+                               float p0, float ux0, float uy0, int phip_uniform, float T_init, cudaStream_t s);
 cudaError_t launch_medium(const float* eps, const float* K, float phi_u, float K_u, int nx, int ny, int pitch, float* phi_out,
                           float* K_out, unsigned int* err, int log_k, cudaStream_t s);
 cudaError_t launch_viscous_rate(const float* J, int nx, int ny, int pitch, float nu, float* sv, unsigned int* err, cudaStream_t s);
@@ -33,7 +36,7 @@ cudaError_t launch_macros(const StepParams& P, int prec, bool het, bool thermal,
 cudaError_t launch_probe(const StepParams& P, int prec, bool het, bool thermal, int x, int y, float* out, cudaStream_t s);
 int residual_blocks(int nx, int ny);
 cudaError_t launch_residual(const StepParams& P, int prec, bool het, bool thermal, const void* prev, const void* gprev,
-                            double* partial, int nblocks, double* out, cudaStream_t s);
+                            const float* uprev, double* partial, int nblocks, double* out, cudaStream_t s);
 cudaError_t launch_nusselt(const StepParams& P, int prec, int side, double* out, cudaStream_t s);
 
 cudaError_t launch_adj_seed(const StepParams& P, int prec, bool het, float* nu_out, float* g_l, float* g_phi, int kind,

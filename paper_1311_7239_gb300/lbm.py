@@ -15,9 +15,10 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 # LBM_LIBRARY selects another build of the library (e.g. liblbm_debug.so, with kernel index checks)
 LIB_PATH = os.environ.get("LBM_LIBRARY") or os.path.join(PKG, "liblbm.so")
 
-ABI_VERSION = 1
+ABI_VERSION = 2
 FP32, FP16_DEV, BF16_DEV = 0, 1, 2
 PERIODIC, WALL, PRESSURE, NEE = 0, 1, 2, 3
+STREAM_AB, STREAM_INPLACE = 0, 1
 LEFT, RIGHT, BOTTOM, TOP = 0, 1, 2, 3
 CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy
 LOSS_OUTLET_FLUX, LOSS_VELOCITY_MISFIT = 0, 1
@@ -62,6 +63,8 @@ class Config(ctypes.Structure):
         ("T0", ctypes.c_double),
         ("T_wall", ctypes.c_double * 4),
         ("stream", ctypes.c_void_p),
+        ("streaming", ctypes.c_uint32),
+        ("reserved0", ctypes.c_uint32),
     ]
 
 

@@ -34,6 +34,7 @@ class Case:
     precision: int = 0
     seed: int = 5
     thermal: dict | None = None  # keys of oracle.thermal_d2q5.Thermal
+    streaming: int = 0           # 0: A-B buffers, 1: in-place (one buffer)
 
     def medium(self):
         if not self.het:
@@ -63,7 +64,7 @@ class Case:
         w = [self.walls.get(s, (0.0, 0.0)) for s in ("left", "right", "bottom", "top")]
         kw = dict(nx=self.nx, ny=self.ny, nu=self.nu, phi=self.phi, K=self.K, forchheimer=int(self.forch), ax=self.ax,
                   ay=self.ay, bc_x=_BC[self.bc_x], bc_y=_BC[self.bc_y], u_wall=w, p_in=self.p_in, p_out=self.p_out,
-                  precision=self.precision, p_rest=self.p_rest())
+                  precision=self.precision, p_rest=self.p_rest(), streaming=self.streaming)
         if self.thermal:
             t = self.thermal
             kw.update(thermal=1, tau_T=t["tau_T"], g_beta=t["g_beta"], T0=t["T0"],

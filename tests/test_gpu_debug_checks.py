@@ -1,7 +1,7 @@
 """The debug build of the library (-DLBM_DEBUG: every kernel checks its index invariants and sets
 an error bit instead of leaving its buffers) runs small and ragged lattices of every boundary set-up
-and storage precision, the thermal step, ensembles in both launch forms and the adjoint without
-reporting a violation."""
+and storage precision, both streaming forms (A-B and in-place), the thermal step, ensembles in both
+launch forms and the adjoint without reporting a violation."""
 import os
 import subprocess
 import sys
@@ -23,9 +23,11 @@ for (nx, ny), (bx, by), prec in itertools.product([(2, 3), (3, 2), (5, 7), (33, 
                                                   [("periodic", "wall"), ("wall", "wall"), ("pressure", "wall"), ("nee", "nee"),
                                                    ("periodic", "periodic"), ("wall", "periodic"), ("periodic", "nee")],
                                                   [0, 1, 2]):
-    for thermal in (0, 1):
+    for thermal, streaming in itertools.product((0, 1), (0, 1)):
+        if streaming and (bx not in ("periodic", "wall") or by not in ("periodic", "wall")):
+            continue  # in-place streaming takes periodic and halfway-wall sides only
         kw = dict(nx=nx, ny=ny, bc_x=bcs[bx], bc_y=bcs[by], precision=prec, u_wall=[(0, 0.01), (0, 0), (0, 0), (0.05, 0)],
-                  p_in=1.001, p_out=0.999, ax=1e-5)
+                  p_in=1.001, p_out=0.999, ax=1e-5, streaming=streaming)
         if thermal:
             kw.update(thermal=1, tau_T=0.8, g_beta=1e-4, T0=11.0, T_wall=[21.0, 1.0, None, None])
         try:
@@ -37,6 +39,9 @@ for (nx, ny), (bx, by), prec in itertools.product([(2, 3), (3, 2), (5, 7), (33, 
             lat.set_medium(eps, torch.full((ny, nx), 5.0, device="cuda"))
             lat.init_equilibrium(0.5, 0.0, 0.0, phi_p_uniform=True)
             lat.step(37)
+            pops = lat.get_populations()
+            lat.set_populations(*(pops if thermal else (pops,)))
+            lat.step(2)
             lat.macros()
             lat.residual()
             if thermal and bx in ("wall", "nee"):

@@ -7,7 +7,7 @@ cell depends only on the cells within k of it (one link per step, Eq. 15), so th
 computes each sampled cell on the (2k+1)^2 crop around it: where the crop meets the lattice's walls
 they are the real walls; its other edges are k cells from the centre and cannot reach it in k
 steps.  The samples cover the four corners (two under the moving lid), the four walls and the
-interior.
+interior.  The in-place streaming form is checked the same way.
 
 The same property checks the 512-lattice ensemble in the launch form its benchmark uses, and the
 full-size adjoint (2048 x 1024 channel, T = 4000) is checked through a property that holds at any
@@ -61,14 +61,15 @@ def _crop_flow(x, y, nx, ny, k, phi, K, nu, lid):
     return flow, (x0, x1, y0, y1)
 
 
-def _sampled_parity(lbm, precision, tol):
+def _sampled_parity(lbm, precision, tol, streaming=0):
     import torch
 
     nu, phi, K = LID * L / 100.0, 0.4, 1e-3 * L * L
     full = fl.Flow(nx=L, ny=L, phi=phi, K=K, nu=nu, bc_x="wall", bc_y="wall", u_top=(LID, 0.0))
     f0 = random_state(full, seed=2024, amp=0.02, u_amp=0.03).astype(np.float32)
     cfg = lbm.default_config(nx=L, ny=L, bc_x=lbm.WALL, bc_y=lbm.WALL, nu=nu, phi=phi, K=K,
-                             u_wall=[(0, 0), (0, 0), (0, 0), (LID, 0)], precision=precision, p_rest=phi, dev_scale_log2=10)
+                             u_wall=[(0, 0), (0, 0), (0, 0), (LID, 0)], precision=precision, p_rest=phi, dev_scale_log2=10,
+                             streaming=streaming)
     lat = lbm.Lattice(cfg)
     try:
         lat.set_populations(torch.from_numpy(f0).cuda())
@@ -105,6 +106,17 @@ def test_bench_cavity_4096_bf16_sampled_cells(lbm):
     """BF16 deviation storage (unscaled, 8-bit significand): a unit of 2^-8 |d|, |d| <= 0.1."""
     worst = _sampled_parity(lbm, 2, K_STEPS * 4e-4)
     print(f"4096^2 BF16, {K_STEPS} steps: max |df| over 64 sampled cells = {worst:.2e}")
+
+
+def test_bench_cavity_4096_inplace_fp32_sampled_cells(lbm):
+    """The same with in-place streaming (one population buffer, 32 steps: both parities)."""
+    worst = _sampled_parity(lbm, 0, 2e-5, streaming=1)
+    print(f"4096^2 FP32 in-place, {K_STEPS} steps: max |df| over 64 sampled cells = {worst:.2e}")
+
+
+def test_bench_cavity_4096_inplace_fp16_sampled_cells(lbm):
+    worst = _sampled_parity(lbm, 1, K_STEPS * 3.1e-5, streaming=1)
+    print(f"4096^2 FP16 in-place, {K_STEPS} steps: max |df| over 64 sampled cells = {worst:.2e}")
 
 
 def test_ensemble_512_in_bench_launch_form(lbm):
