@@ -86,6 +86,7 @@ def _trajectory(lbm, case, steps):
     flow = case.flow()
     f = fl.initial_state(flow)
     with case.lattice(lbm) as lat:
+        lat.init_equilibrium(1.0, 0.0, 0.0)  # after the medium: p = 1 with the per-cell porosity
         lat.step(steps)
         p, ux, uy = [t.cpu().numpy() for t in lat.macros()]
         lat.sync()
