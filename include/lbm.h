@@ -70,7 +70,12 @@ extern "C" {
                                * LBM_STREAM_AB with half the population memory.  Sides: LBM_PERIODIC and
                                * LBM_WALL only (the extrapolated sides read a neighbour's state while it is
                                * being overwritten); not for lbm_adjoint or batches.  lbm_step records u
-                               * before the last step of each call (8 B per cell) for lbm_residual. */
+                               * before the last step of each call (8 B per cell, one read of the state per
+                               * call) for lbm_residual, unless LBM_OPT_NO_RESIDUAL_RECORD is set.  Limit:
+                               * 8 ((ny + 2) pitch + ny + 2) <= 2^32 elements, pitch = nx rounded up to 128
+                               * (about 23000 x 23000). */
+/* lbm_config.options bits */
+#define LBM_OPT_NO_RESIDUAL_RECORD 1u /* in-place contexts: keep no u(t-1) record (lbm_residual returns LBM_ESTATE) */
 
 /* wall indices of u_wall / T_wall */
 #define LBM_LEFT 0
@@ -107,7 +112,7 @@ typedef struct lbm_config {
   double T_wall[4];     /* wall temperature (anti-bounce-back), NaN = adiabatic (bounce-back) */
   void* stream;         /* cudaStream_t to use, or NULL */
   uint32_t streaming;   /* LBM_STREAM_AB (default) | LBM_STREAM_INPLACE */
-  uint32_t reserved0;   /* must be 0 */
+  uint32_t options;     /* LBM_OPT_* bits, 0 by default */
 } lbm_config;
 
 typedef struct lbm_ctx lbm_ctx;

@@ -129,7 +129,8 @@ struct lbm_ctx {
   void* f[2] = {nullptr, nullptr};
   void* g[2] = {nullptr, nullptr};
   int cur = 0;                   // A-B: buffer of the current state; in-place: parity of the next step
-  bool inplace = false;          // one buffer (f[0], g[0]) with rows -1..ny; see ip_off
+  bool inplace = false;          // one buffer (f[0], g[0]) with rows -1..ny and a ghost column; see ip_off
+  size_t fbytes = 0, gbytes = 0; // bytes of one flow / temperature population buffer
   float* uprev = nullptr;        // in-place: u before the last step of the last lbm_step call, [2][ny][nx]
   float* phi = nullptr;
   float* K = nullptr;
@@ -322,7 +323,8 @@ int validate_config(const lbm_config* c) {
   if (!(c->phi > 0 && c->phi <= 1) || !(c->K > 0)) return fail(LBM_EINVAL, "uniform phi must be in (0, 1], K > 0");
   if (!isfinite(c->ax) || !isfinite(c->ay) || !isfinite(c->p_rest)) return fail(LBM_EINVAL, "non-finite a or p_rest");
   if (c->dev_scale_log2 < -30 || c->dev_scale_log2 > 30) return fail(LBM_EINVAL, "dev_scale_log2 out of [-30, 30]");
-  if (c->streaming > LBM_STREAM_INPLACE || c->reserved0 != 0) return fail(LBM_EINVAL, "unknown streaming mode %u", c->streaming);
+  if (c->streaming > LBM_STREAM_INPLACE) return fail(LBM_EINVAL, "unknown streaming mode %u", c->streaming);
+  if (c->options & ~LBM_OPT_NO_RESIDUAL_RECORD) return fail(LBM_EINVAL, "unknown option bits %#x", c->options);
   if (c->streaming == LBM_STREAM_INPLACE && (c->bc_x > LBM_WALL || c->bc_y > LBM_WALL))
     return fail(LBM_EINVAL, "in-place streaming supports periodic and halfway-wall sides only");
   if (c->thermal) {
@@ -418,14 +420,18 @@ int lbm_create(const lbm_config* cfg, lbm_ctx** out) {
   }
   c->prec = (int)cfg->precision;
   c->elem = c->prec == PREC_FP32 ? 4 : 2;
-  // in-place: a ghost column right of the lattice and ghost rows below and above it
+  // in-place: ghost rows below and above the lattice (rows of the planes) and a ghost column right
+  // of it (q columns of ny + 2 slots after the last plane)
   c->inplace = cfg->streaming == LBM_STREAM_INPLACE;
-  c->pitch = (int)((cfg->nx + (c->inplace ? 1 : 0) + 127) / 128 * 128);
+  c->pitch = (int)((cfg->nx + 127) / 128 * 128);
   c->plane = (int64_t)c->pitch * (cfg->ny + (c->inplace ? 2 : 0));
   const int nbuf = c->inplace ? 1 : 2;
-  if (c->inplace && 8 * (uint64_t)c->plane > (1ull << 32)) {  // the in-place step indexes a buffer with 32-bit offsets
+  const int64_t ghost_col = c->inplace ? (int64_t)cfg->ny + 2 : 0;
+  c->fbytes = 8 * (size_t)(c->plane + ghost_col) * c->elem;
+  c->gbytes = 5 * (size_t)(c->plane + ghost_col) * c->elem;
+  if (c->inplace && 8 * (uint64_t)(c->plane + ghost_col) > (1ull << 32)) {  // the in-place step indexes with 32-bit offsets
     delete c;
-    return fail(LBM_EINVAL, "in-place streaming needs 8 (ny + 2) pitch <= 2^32 elements (pitch = nx + 1 rounded up to 128)");
+    return fail(LBM_EINVAL, "in-place streaming needs 8 ((ny + 2) pitch + ny + 2) <= 2^32 elements (pitch = nx rounded up to 128)");
   }
   if (cfg->stream) {
     c->stream = static_cast<cudaStream_t>(cfg->stream);
@@ -437,13 +443,13 @@ int lbm_create(const lbm_config* cfg, lbm_ctx** out) {
     }
     c->own_stream = true;
   }
-  const size_t fbytes = 8 * (size_t)c->plane * c->elem;
-  const size_t gbytes = 5 * (size_t)c->plane * c->elem;
+  const size_t fbytes = c->fbytes;
+  const size_t gbytes = c->gbytes;
   for (int b = 0; b < nbuf && rc == LBM_OK; ++b) {
     rc = dev_alloc(c, &c->f[b], fbytes, "cudaMalloc(populations)");
     if (rc == LBM_OK && cfg->thermal) rc = dev_alloc(c, &c->g[b], gbytes, "cudaMalloc(temperature populations)");
   }
-  if (rc == LBM_OK && c->inplace)
+  if (rc == LBM_OK && c->inplace && !(cfg->options & LBM_OPT_NO_RESIDUAL_RECORD))
     rc = dev_alloc(c, reinterpret_cast<void**>(&c->uprev), 2 * (size_t)cfg->nx * cfg->ny * sizeof(float), "cudaMalloc(previous velocity)");
   if (rc == LBM_OK) rc = dev_alloc(c, reinterpret_cast<void**>(&c->err), sizeof(unsigned int), "cudaMalloc(error word)");
   if (rc == LBM_OK)
@@ -677,7 +683,7 @@ int run_steps(lbm_ctx* c, int n) {
 int lbm_step(lbm_ctx* c, int n) {
   if (!c) return fail(LBM_EINVAL, "null context");
   if (n < 0) return fail(LBM_EINVAL, "negative step count");
-  if (!c->inplace || n == 0) return run_steps(c, n);
+  if (!c->uprev || n == 0) return run_steps(c, n);
   // in-place: u(t-1) of the residual is recorded before the last step (its state is overwritten)
   int rc = run_steps(c, n - 1);
   if (rc) return rc;
@@ -769,6 +775,7 @@ int lbm_set_populations(lbm_ctx* c, const float* f, const float* g) {
 int lbm_residual(lbm_ctx* c, double* r) {
   if (!c || !r) return fail(LBM_EINVAL, "null argument");
   if (c->history < 1) return fail(LBM_ESTATE, "the residual needs one step since the last initialisation");
+  if (c->inplace && !c->uprev) return fail(LBM_ESTATE, "in-place context created with LBM_OPT_NO_RESIDUAL_RECORD");
   StepParams P = params_for(c);
   const int nb = residual_blocks((int)c->cfg.nx, (int)c->cfg.ny);
   double* out = c->red + 2 * kResidualMaxBlocks;
@@ -1013,14 +1020,14 @@ int lbm_save(lbm_ctx* c, const char* path) {
   h.cur = c->cur;
   h.het = c->het ? 1 : 0;
   h.init_phip = c->init_phip;
-  h.inplace = c->inplace ? 1 : 0;
+  h.inplace = c->inplace ? (c->uprev ? 1 : 2) : 0;  // 1: with the u(t-1) record
   h.steps = c->steps;
   h.history = c->history;
   h.init_p0 = c->init_p0;
   h.init_ux = c->init_ux;
   h.init_uy = c->init_uy;
-  h.pop_bytes = 8 * (uint64_t)c->plane * c->elem;
-  h.therm_bytes = c->cfg.thermal ? 5 * (uint64_t)c->plane * c->elem : 0;
+  h.pop_bytes = c->fbytes;
+  h.therm_bytes = c->cfg.thermal ? c->gbytes : 0;
   h.medium_bytes = c->het ? (uint64_t)c->plane * sizeof(float) : 0;
   h.sv_bytes = (c->het && c->sv) ? (uint64_t)c->plane * sizeof(float) : 0;
   std::vector<char> host(h.pop_bytes > h.medium_bytes ? h.pop_bytes : h.medium_bytes);
@@ -1040,7 +1047,7 @@ int lbm_save(lbm_ctx* c, const char* path) {
       if (fwrite(host.data(), 1, h.therm_bytes, f) != h.therm_bytes) return io_fail(f, "write failed");
     }
   }
-  if (c->inplace) {
+  if (c->uprev) {
     const size_t ub = 2 * (size_t)c->cfg.nx * c->cfg.ny * sizeof(float);
     std::vector<char> u(ub);
     if (cudaMemcpy(u.data(), c->uprev, ub, cudaMemcpyDeviceToHost) != cudaSuccess) return io_fail(f, "device read failed");
@@ -1071,9 +1078,9 @@ int lbm_load(lbm_ctx* c, const char* path) {
   if (h.version != kSaveVersion || h.config_size != sizeof(lbm_config)) return io_fail(f, "state file of another format version");
   if (fread(&cfg, sizeof(cfg), 1, f) != 1) return io_fail(f, "truncated state file");
   if (h.nx != c->cfg.nx || h.ny != c->cfg.ny || (int)h.precision != c->prec || (h.thermal != 0) != (c->cfg.thermal != 0) ||
-      (int)h.pitch != c->pitch || (h.inplace != 0) != c->inplace)
-    return io_fail(f, "state file does not match the context (size, precision, thermal or streaming)");
-  if (h.pop_bytes != 8 * (uint64_t)c->plane * c->elem) return io_fail(f, "state file layout mismatch");
+      (int)h.pitch != c->pitch || h.inplace != (c->inplace ? (c->uprev ? 1 : 2) : 0))
+    return io_fail(f, "state file does not match the context (size, precision, thermal, streaming or residual record)");
+  if (h.pop_bytes != c->fbytes) return io_fail(f, "state file layout mismatch");
   std::vector<char> host(h.pop_bytes > h.medium_bytes ? h.pop_bytes : h.medium_bytes);
   LBM_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
   for (int b = 0; b < (c->inplace ? 1 : 2); ++b) {
@@ -1085,7 +1092,7 @@ int lbm_load(lbm_ctx* c, const char* path) {
         return io_fail(f, "device write failed");
     }
   }
-  if (c->inplace) {
+  if (c->uprev) {
     const size_t ub = 2 * (size_t)c->cfg.nx * c->cfg.ny * sizeof(float);
     std::vector<char> u(ub);
     if (fread(u.data(), 1, ub, f) != ub) return io_fail(f, "truncated state file");

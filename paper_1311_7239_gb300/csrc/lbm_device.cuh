@@ -492,13 +492,21 @@ __device__ __forceinline__ int wall_of(int sx, int sy, int ny) {
 // population opposite to the one read from it), so the two halves of Eq. 15 share one buffer
 // without races and the buffer alternates between two layouts.  Populations that leave through a
 // wall are parked in ghost slots (rows -1 and ny, column nx; never updated as cells) until the
-// same cell reads them back as its bounce-back (Eq. 15 at a wall).  Only periodic and halfway-wall
-// sides are supported.
+// same cell reads them back as its bounce-back (Eq. 15 at a wall).  Ghost rows -1 and ny are rows of
+// the planes; the ghost column lives after the last plane, q columns of ny + 2 slots (so that a
+// lattice width that is a multiple of the row pitch needs no wider rows).  Only periodic and
+// halfway-wall sides are supported.
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ bool ip_positive(int i) { return i == 0 || i == 1 || i == 4 || i == 7; }
 
 __device__ __forceinline__ int wrap_periodic(int v, int n, bool periodic) {
   return periodic ? (v < 0 ? v + n : (v >= n ? v - n : v)) : v;
+}
+
+// element offset (from row 0 of plane 0) of slot (plane, cx, cy) of a buffer of q planes
+__device__ __forceinline__ int64_t ip_slot(const StepParams& P, int q, int plane, int cx, int cy) {
+  if (cx >= P.nx) return (int64_t)q * P.plane - P.pitch + (int64_t)plane * (P.ny + 2) + (cy + 1);  // ghost column
+  return (int64_t)plane * P.plane + (int64_t)cy * P.pitch + cx;
 }
 
 // element offset of the slot from which cell (cx, cy) (a lattice or ghost cell) reads population
@@ -510,8 +518,8 @@ __device__ __forceinline__ int64_t ip_off(const StepParams& P, int cx, int cy, i
   }
   cx = wrap_periodic(cx, P.nx, P.bc_x == BC_PERIODIC);
   cy = wrap_periodic(cy, P.ny, P.bc_y == BC_PERIODIC);
-  dbg_check(P, cx >= 0 && cx <= P.nx && cx < P.pitch && cy >= -1 && cy <= P.ny);
-  return (int64_t)(par ? i : opp_of(i)) * P.plane + (int64_t)cy * P.pitch + cx;
+  dbg_check(P, cx >= 0 && cx <= P.nx && cy >= -1 && cy <= P.ny);
+  return ip_slot(P, 8, par ? i : opp_of(i), cx, cy);
 }
 
 // the same for the D2Q5 temperature populations (positive: 1 and 2; the rest population stays)
@@ -522,9 +530,8 @@ __device__ __forceinline__ int64_t ip_off5(const StepParams& P, int cx, int cy, 
   }
   cx = wrap_periodic(cx, P.nx, P.bc_x == BC_PERIODIC);
   cy = wrap_periodic(cy, P.ny, P.bc_y == BC_PERIODIC);
-  dbg_check(P, cx >= 0 && cx <= P.nx && cx < P.pitch && cy >= -1 && cy <= P.ny);
-  const int plane = i == 0 ? 0 : (par ? i : opp5(i));
-  return (int64_t)plane * P.plane + (int64_t)cy * P.pitch + cx;
+  dbg_check(P, cx >= 0 && cx <= P.nx && cy >= -1 && cy <= P.ny);
+  return ip_slot(P, 5, i == 0 ? 0 : (par ? i : opp5(i)), cx, cy);
 }
 
 // Source of the pull of population i into cell (x, y) at the current parity: the slot the cell

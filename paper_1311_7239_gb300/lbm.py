@@ -19,6 +19,7 @@ ABI_VERSION = 2
 FP32, FP16_DEV, BF16_DEV = 0, 1, 2
 PERIODIC, WALL, PRESSURE, NEE = 0, 1, 2, 3
 STREAM_AB, STREAM_INPLACE = 0, 1
+OPT_NO_RESIDUAL_RECORD = 1
 LEFT, RIGHT, BOTTOM, TOP = 0, 1, 2, 3
 CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy
 LOSS_OUTLET_FLUX, LOSS_VELOCITY_MISFIT = 0, 1
@@ -64,7 +65,7 @@ class Config(ctypes.Structure):
         ("T_wall", ctypes.c_double * 4),
         ("stream", ctypes.c_void_p),
         ("streaming", ctypes.c_uint32),
-        ("reserved0", ctypes.c_uint32),
+        ("options", ctypes.c_uint32),
     ]
 
 

@@ -241,13 +241,23 @@ def test_save_load_continues_bitwise(lbm):
 
 
 def test_memory_and_rejections(lbm):
+    """One population buffer instead of two: a 1024^2 FP32 context saves one buffer (32 MiB) less the
+    ghost rows/column and, unless LBM_OPT_NO_RESIDUAL_RECORD is set, the 8 B per cell u(t-1) record."""
     import torch
 
+    n = 1024 * 1024
+    one = 8 * n * 4
     base = Case(1024, 1024, bc_x="wall", bc_y="wall", walls=CAV)
-    with base.lattice(lbm) as a, dataclasses.replace(base, streaming=IP).lattice(lbm) as b:
-        ma, mb = a.memory_bytes(), b.memory_bytes()
-    pop = 2 * 8 * 1024 * 1024 * 4
-    assert mb <= ma - 0.45 * pop, (ma, mb)  # one population buffer instead of two
+    cfg_nr = dataclasses.replace(base, streaming=IP).config(lbm)
+    cfg_nr.options = lbm.OPT_NO_RESIDUAL_RECORD
+    with base.lattice(lbm) as a, dataclasses.replace(base, streaming=IP).lattice(lbm) as b, lbm.Lattice(cfg_nr) as c:
+        ma, mb, mc = a.memory_bytes(), b.memory_bytes(), c.memory_bytes()
+        c.step(5)
+        with pytest.raises(lbm.LbmError) as e:
+            c.residual()
+        assert e.value.code == lbm.ESTATE
+    assert ma - mc >= 0.99 * one, (ma, mc)
+    assert ma - mb >= 0.99 * one - 8 * n, (ma, mb)
     for bx, by in (("nee", "wall"), ("wall", "nee"), ("pressure", "wall")):
         with pytest.raises(lbm.LbmError) as e:
             Case(32, 16, bc_x=bx, bc_y=by, streaming=IP).lattice(lbm)
