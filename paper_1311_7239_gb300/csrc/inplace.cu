@@ -9,9 +9,10 @@
 // Work split: a thread updates four consecutive cells of one row.  Of the slots it touches, five
 // are the aligned four-cell vectors of rows y and y + 1 (positive members and e4 = (0, -1)); the
 // three with e_x = -1 sit one cell to the right (x0 + 1 .. x0 + 4) and are moved as one cell, an
-// aligned pair and one cell, so that a thread touches no slot of another thread's cells.  Groups
-// with a cell on a wall or on the last column (where the right neighbour wraps or is a ghost
-// slot) take the generic per-cell rules.
+// aligned pair and one cell, so that a thread touches no slot of another thread's cells.  The
+// groups with a cell on a wall or on the last column (where the right neighbour wraps or is a
+// ghost slot) form a "frame" that the launch's first blocks do cell by cell with the generic
+// rules, so that the warps of the interior never diverge.
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
 
@@ -63,115 +64,222 @@ __device__ __forceinline__ void store_right(typename Store<PREC>::T* row, int x0
   row[x0 + 4] = S::enc(v[3], sc);
 }
 
+// 16-bit storage as words of two cells: the aligned four cells at p (two words), and cells
+// p + 1 .. p + 4 (one half-word, one word, one half-word) repacked as (p+1, p+2), (p+3, p+4)
+__device__ __forceinline__ void load4w(const void* p, uint32_t w[2]) {
+  const uint2 v = *reinterpret_cast<const uint2*>(p);
+  w[0] = v.x;
+  w[1] = v.y;
+}
+__device__ __forceinline__ void store4w(void* p, const uint32_t w[2]) { *reinterpret_cast<uint2*>(p) = make_uint2(w[0], w[1]); }
+__device__ __forceinline__ void load_right_w(const unsigned short* row, uint32_t w[2]) {
+  const uint32_t a = row[1], m = *reinterpret_cast<const uint32_t*>(row + 2), b = row[4];
+  w[0] = __byte_perm(a, m, 0x5410);
+  w[1] = __byte_perm(m, b, 0x5432);
+}
+__device__ __forceinline__ void store_right_w(unsigned short* row, const uint32_t w[2]) {
+  row[1] = (unsigned short)(w[0] & 0xffffu);
+  *reinterpret_cast<uint32_t*>(row + 2) = __byte_perm(w[0], w[1], 0x5432);
+  row[4] = (unsigned short)(w[1] >> 16);
+}
+
 template <int PAR>
 __device__ __forceinline__ constexpr int plane_of(int i) {
   return PAR ? i : (i < 4 ? (i + 2) & 3 : 4 + ((i - 4 + 2) & 3));
 }
 
+// Cells of the frame, the groups with a cell on a wall or on the last column (see k_step_ip):
+// whole wall rows (y = 0 and ny - 1 when the y sides are walls), and in the other rows the cells
+// x < L (the first group, when the x sides are walls) and x >= R (the groups that reach column
+// nx - 1 through their right neighbours).
+struct IpFrame {
+  int L, R, E, wall_rows;
+  int64_t total;
+};
+
+__host__ __device__ __forceinline__ IpFrame ip_frame_of(int nx, int ny, int bc_x, int bc_y) {
+  IpFrame F;
+  F.L = bc_x == BC_WALL ? (nx < 4 ? nx : 4) : 0;
+  const int x0e = nx <= 4 ? 0 : (nx - 1) / 4 * 4;  // first group start with x0 + 4 >= nx
+  F.R = x0e > F.L ? x0e : F.L;
+  F.E = F.L + (nx - F.R);
+  F.wall_rows = bc_y == BC_WALL ? 2 : 0;
+  F.total = (int64_t)F.wall_rows * nx + (int64_t)(ny - F.wall_rows) * F.E;
+  return F;
+}
+
+__device__ __forceinline__ void ip_frame_cell(const IpFrame& F, int nx, int ny, int64_t k, int& x, int& y) {
+  const int64_t wc = (int64_t)F.wall_rows * nx;
+  if (k < wc) {
+    y = k < nx ? 0 : ny - 1;
+    x = (int)(k < nx ? k : k - nx);
+  } else {
+    const int64_t r = (k - wc) / F.E;
+    const int j = (int)(k - wc - r * F.E);
+    y = (int)r + (F.wall_rows ? 1 : 0);
+    x = j < F.L ? j : F.R + (j - F.L);
+  }
+}
+
+// Interior cells of a uniform medium with 16-bit storage, collided two at a time (collide_pair)
+// on the stored words, as the A-B step does where it is bound by instruction issue.
+template <int PREC, bool HET, bool THERMAL>
+constexpr bool kIpPacked = PREC != PREC_FP32 && !HET && !THERMAL;
+
 // Register caps: 8 CTAs of 128 threads per SM for the flow (64 registers, as the A-B step), 5 with
-// the temperature populations (96; at 80 the FP32 thermal step spills).
+// the temperature populations (96; at 80 the FP32 thermal step spills).  Blocks [0, frame_blocks)
+// do the frame cells, one per thread, with the generic rules; the others do groups of four cells
+// of one row, gx blocks per row, and skip the groups of the frame.
 template <int PREC, bool HET, bool THERMAL, int PAR>
-__global__ void __launch_bounds__(kIpThreads, THERMAL ? 5 : 8) k_step_ip(const StepParams P) {
+__global__ void __launch_bounds__(kIpThreads, THERMAL ? 5 : 8) k_step_ip(const StepParams P, int frame_blocks, int gx) {
   using S = Store<PREC>;
   using T = typename S::T;
   constexpr int C = kIpCells;
-  const int y = blockIdx.y;
-  const int x0 = (blockIdx.x * kIpThreads + threadIdx.x) * C;
-  if (x0 >= P.nx) return;
   T* __restrict__ A = static_cast<T*>(P.dst);
   T* __restrict__ G = static_cast<T*>(P.gdst);
-  const bool edge = (P.bc_x == BC_WALL && x0 == 0) || x0 + C >= P.nx || (P.bc_y == BC_WALL && (y == 0 || y == P.ny - 1));
-  if (edge) {
-    for (int c = 0; c < C && x0 + c < P.nx; ++c) ip_cell<PREC, HET, THERMAL>(P, A, G, x0 + c, y);
+  if ((int)blockIdx.x < frame_blocks) {
+    const IpFrame F = ip_frame_of(P.nx, P.ny, P.bc_x, P.bc_y);
+    const int64_t k = (int64_t)blockIdx.x * kIpThreads + threadIdx.x;
+    if (k >= F.total) return;
+    int x, y;
+    ip_frame_cell(F, P.nx, P.ny, k, x, y);
+    if (!dbg_check(P, x >= 0 && x < P.nx && y >= 0 && y < P.ny)) return;
+    ip_cell<PREC, HET, THERMAL>(P, A, G, x, y);
     return;
   }
-  // rows y - 1 and y + 1 (periodic wrap; wall rows are edge groups)
+  const int b = (int)blockIdx.x - frame_blocks;
+  const int y = b / gx;
+  const int x0 = ((b - y * gx) * kIpThreads + (int)threadIdx.x) * C;
+  if (x0 >= P.nx || !dbg_check(P, y < P.ny)) return;
+  const bool edge = (P.bc_x == BC_WALL && x0 == 0) || x0 + C >= P.nx || (P.bc_y == BC_WALL && (y == 0 || y == P.ny - 1));
+  if (edge) return;  // a frame group
+  // rows y - 1 and y + 1 (periodic wrap; wall rows are frame rows)
   const int ym = y == 0 ? P.ny - 1 : y - 1;
   const int yp = y == P.ny - 1 ? 0 : y + 1;
   const int64_t rm = (int64_t)ym * P.pitch, r0 = (int64_t)y * P.pitch, rp = (int64_t)yp * P.pitch;
-  const float inv = P.inv_scale;
-  float4 ph4, k4;
-  if (HET) {
-    ph4 = __ldg(reinterpret_cast<const float4*>(P.phi + r0 + x0));
-    k4 = __ldg(reinterpret_cast<const float4*>(P.K + r0 + x0));
-  }
-  // pull, Eq. 15: the slot of population i (see ip_off), as 32-bit element offsets from A (a
-  // buffer holds fewer than 2^32 elements; lbm_create checks): plane * pl + y0x (+ the row change
-  // dp or dm for the slots of rows y + 1 and y - 1)
+  // the slot of population i (see ip_off), as 32-bit element offsets from A (a buffer holds fewer
+  // than 2^32 elements; lbm_create checks): plane * pl + y0x (+ the row change dp or dm for the
+  // slots of rows y + 1 and y - 1)
   const uint32_t pl = (uint32_t)P.plane;
   const uint32_t y0x = (uint32_t)r0 + (uint32_t)x0;
   const uint32_t dp = (uint32_t)(rp - r0), dm = (uint32_t)(rm - r0);
-  float d[8][C];
-  S::load4(A + plane_of<PAR>(0) * pl + y0x, d[0], inv);             // e1 = ( 1, 0): own cells
-  S::load4(A + plane_of<PAR>(1) * pl + y0x, d[1], inv);             // e2 = ( 0, 1): own cells
-  load_right<PREC>(A + plane_of<PAR>(2) * pl + y0x, 0, inv, d[2]);  // e3 = (-1, 0): cells x + 1 of row y
-  S::load4(A + (plane_of<PAR>(3) * pl + y0x + dp), d[3], inv);      // e4 = ( 0,-1): cells of row y + 1
-  S::load4(A + plane_of<PAR>(4) * pl + y0x, d[4], inv);             // e5 = ( 1, 1): own cells
-  load_right<PREC>(A + (plane_of<PAR>(5) * pl + y0x + dm), 0, inv, d[5]);  // e6 = (-1, 1): cells x + 1 of row y - 1
-  load_right<PREC>(A + (plane_of<PAR>(6) * pl + y0x + dp), 0, inv, d[6]);  // e7 = (-1,-1): cells x + 1 of row y + 1
-  S::load4(A + plane_of<PAR>(7) * pl + y0x, d[7], inv);             // e8 = ( 1,-1): own cells
-  float g[5][C];
-  if (THERMAL) {
-    S::load4(G + y0x, g[0], inv);                                    // rest population
-    S::load4(G + (PAR ? 1 : 3) * pl + y0x, g[1], inv);               // ( 1, 0): own cells
-    S::load4(G + (PAR ? 2 : 4) * pl + y0x, g[2], inv);               // ( 0, 1): own cells
-    load_right<PREC>(G + (PAR ? 3 : 1) * pl + y0x, 0, inv, g[3]);    // (-1, 0): cells x + 1
-    S::load4(G + ((PAR ? 4 : 2) * pl + y0x + dp), g[4], inv);        // ( 0,-1): row y + 1
-  }
-  float check = 0.0f;
+  if constexpr (kIpPacked<PREC, HET, THERMAL>) {
+    unsigned short* const W = reinterpret_cast<unsigned short*>(A);
+    uint32_t w[8][2];
+    load4w(W + plane_of<PAR>(0) * pl + y0x, w[0]);             // e1 = ( 1, 0): own cells
+    load4w(W + plane_of<PAR>(1) * pl + y0x, w[1]);             // e2 = ( 0, 1): own cells
+    load_right_w(W + plane_of<PAR>(2) * pl + y0x, w[2]);       // e3 = (-1, 0): cells x + 1 of row y
+    load4w(W + (plane_of<PAR>(3) * pl + y0x + dp), w[3]);      // e4 = ( 0,-1): cells of row y + 1
+    load4w(W + plane_of<PAR>(4) * pl + y0x, w[4]);             // e5 = ( 1, 1): own cells
+    load_right_w(W + (plane_of<PAR>(5) * pl + y0x + dm), w[5]);  // e6 = (-1, 1): cells x + 1 of row y - 1
+    load_right_w(W + (plane_of<PAR>(6) * pl + y0x + dp), w[6]);  // e7 = (-1,-1): cells x + 1 of row y + 1
+    load4w(W + plane_of<PAR>(7) * pl + y0x, w[7]);             // e8 = ( 1,-1): own cells
+    float check = 0.0f;
 #pragma unroll
-  for (int c = 0; c < C; ++c) {
-    float dc[8];
+    for (int h = 0; h < C / 2; ++h) {
+      float2 dp2[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) dc[i] = d[i][c];
-    const Coef cf = HET ? coef_of(P, f4_get(ph4, c), f4_get(k4, c), P.sv ? __ldg(P.sv + r0 + x0 + c) : P.s_v) : coef_uniform(P);
-    float ay = P.ay;
-    if (THERMAL) ay += P.g_beta * (g[0][c] + g[1][c] + g[2][c] + g[3][c] + g[4][c]);
-    float ux, uy, phip;
-    collide_d2q8(dc, cf, P.ax, ay, P, ux, uy, phip);
-    check += fabsf(ux) + fabsf(uy);
+      for (int i = 0; i < 8; ++i) dp2[i] = S::w2f(w[i][h]);
+      float2 ux, uy;
+      collide_pair(dp2, pair_coef_uniform(P.pc), f2(P.pc.u_hx), f2(P.pc.u_hy), P.pc, ux, uy);
+      check += (fabsf(ux.x) + fabsf(uy.x)) + (fabsf(ux.y) + fabsf(uy.y));
 #pragma unroll
-    for (int i = 0; i < 8; ++i) d[i][c] = dc[i];
-    if (THERMAL) {
-      float gc[5];
-#pragma unroll
-      for (int i = 0; i < 5; ++i) gc[i] = g[i][c];
-      collide_d2q5(gc, ux, uy, P);
-#pragma unroll
-      for (int i = 0; i < 5; ++i) g[i][c] = gc[i];
+      for (int i = 0; i < 8; ++i) w[i][h] = S::f2w(dp2[i]);
     }
-  }
-  if (!(check < 1e30f)) atomicOr(P.err, 1u);  // non-finite velocity in these cells
-  // post-collision population opp(i) into the slot population i came from; the offsets are formed
-  // again from an opaque copy of y0x rather than kept live through the collision
-  uint32_t b0 = y0x;
-  asm volatile("" : "+r"(b0));
-  const float sc = P.scale;
-  S::store4(A + plane_of<PAR>(0) * pl + b0, d[2], sc);
-  S::store4(A + plane_of<PAR>(1) * pl + b0, d[3], sc);
-  store_right<PREC>(A + plane_of<PAR>(2) * pl + b0, 0, d[0], sc);
-  S::store4(A + (plane_of<PAR>(3) * pl + b0 + dp), d[1], sc);
-  S::store4(A + plane_of<PAR>(4) * pl + b0, d[6], sc);
-  store_right<PREC>(A + (plane_of<PAR>(5) * pl + b0 + dm), 0, d[7], sc);
-  store_right<PREC>(A + (plane_of<PAR>(6) * pl + b0 + dp), 0, d[4], sc);
-  S::store4(A + plane_of<PAR>(7) * pl + b0, d[5], sc);
-  if (THERMAL) {
-    S::store4(G + b0, g[0], sc);
-    S::store4(G + (PAR ? 1 : 3) * pl + b0, g[3], sc);
-    S::store4(G + (PAR ? 2 : 4) * pl + b0, g[4], sc);
-    store_right<PREC>(G + (PAR ? 3 : 1) * pl + b0, 0, g[1], sc);
-    S::store4(G + ((PAR ? 4 : 2) * pl + b0 + dp), g[2], sc);
+    if (!(check < 1e30f)) atomicOr(P.err, 1u);  // non-finite velocity in these cells
+    uint32_t b0 = y0x;
+    asm volatile("" : "+r"(b0));
+    store4w(W + plane_of<PAR>(0) * pl + b0, w[2]);
+    store4w(W + plane_of<PAR>(1) * pl + b0, w[3]);
+    store_right_w(W + plane_of<PAR>(2) * pl + b0, w[0]);
+    store4w(W + (plane_of<PAR>(3) * pl + b0 + dp), w[1]);
+    store4w(W + plane_of<PAR>(4) * pl + b0, w[6]);
+    store_right_w(W + (plane_of<PAR>(5) * pl + b0 + dm), w[7]);
+    store_right_w(W + (plane_of<PAR>(6) * pl + b0 + dp), w[4]);
+    store4w(W + plane_of<PAR>(7) * pl + b0, w[5]);
+    return;
+  } else {
+    const float inv = P.inv_scale;
+    float4 ph4, k4;
+    if (HET) {
+      ph4 = __ldg(reinterpret_cast<const float4*>(P.phi + r0 + x0));
+      k4 = __ldg(reinterpret_cast<const float4*>(P.K + r0 + x0));
+    }
+    float d[8][C];
+    S::load4(A + plane_of<PAR>(0) * pl + y0x, d[0], inv);             // e1 = ( 1, 0): own cells
+    S::load4(A + plane_of<PAR>(1) * pl + y0x, d[1], inv);             // e2 = ( 0, 1): own cells
+    load_right<PREC>(A + plane_of<PAR>(2) * pl + y0x, 0, inv, d[2]);  // e3 = (-1, 0): cells x + 1 of row y
+    S::load4(A + (plane_of<PAR>(3) * pl + y0x + dp), d[3], inv);      // e4 = ( 0,-1): cells of row y + 1
+    S::load4(A + plane_of<PAR>(4) * pl + y0x, d[4], inv);             // e5 = ( 1, 1): own cells
+    load_right<PREC>(A + (plane_of<PAR>(5) * pl + y0x + dm), 0, inv, d[5]);  // e6 = (-1, 1): cells x + 1 of row y - 1
+    load_right<PREC>(A + (plane_of<PAR>(6) * pl + y0x + dp), 0, inv, d[6]);  // e7 = (-1,-1): cells x + 1 of row y + 1
+    S::load4(A + plane_of<PAR>(7) * pl + y0x, d[7], inv);             // e8 = ( 1,-1): own cells
+    float g[5][C];
+    if (THERMAL) {
+      S::load4(G + y0x, g[0], inv);                                    // rest population
+      S::load4(G + (PAR ? 1 : 3) * pl + y0x, g[1], inv);               // ( 1, 0): own cells
+      S::load4(G + (PAR ? 2 : 4) * pl + y0x, g[2], inv);               // ( 0, 1): own cells
+      load_right<PREC>(G + (PAR ? 3 : 1) * pl + y0x, 0, inv, g[3]);    // (-1, 0): cells x + 1
+      S::load4(G + ((PAR ? 4 : 2) * pl + y0x + dp), g[4], inv);        // ( 0,-1): row y + 1
+    }
+    float check = 0.0f;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      float dc[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) dc[i] = d[i][c];
+      const Coef cf = HET ? coef_of(P, f4_get(ph4, c), f4_get(k4, c), P.sv ? __ldg(P.sv + r0 + x0 + c) : P.s_v) : coef_uniform(P);
+      float ay = P.ay;
+      if (THERMAL) ay += P.g_beta * (g[0][c] + g[1][c] + g[2][c] + g[3][c] + g[4][c]);  // a = g beta (T - T0) j
+      float ux, uy, phip;
+      collide_d2q8(dc, cf, P.ax, ay, P, ux, uy, phip);
+      check += fabsf(ux) + fabsf(uy);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) d[i][c] = dc[i];
+      if (THERMAL) {
+        float gc[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) gc[i] = g[i][c];
+        collide_d2q5(gc, ux, uy, P);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) g[i][c] = gc[i];
+      }
+    }
+    if (!(check < 1e30f)) atomicOr(P.err, 1u);  // non-finite velocity in these cells
+    // post-collision population opp(i) into the slot population i came from; the offsets are
+    // formed again from an opaque copy of y0x rather than kept live through the collision
+    uint32_t b0 = y0x;
+    asm volatile("" : "+r"(b0));
+    const float sc = P.scale;
+    S::store4(A + plane_of<PAR>(0) * pl + b0, d[2], sc);
+    S::store4(A + plane_of<PAR>(1) * pl + b0, d[3], sc);
+    store_right<PREC>(A + plane_of<PAR>(2) * pl + b0, 0, d[0], sc);
+    S::store4(A + (plane_of<PAR>(3) * pl + b0 + dp), d[1], sc);
+    S::store4(A + plane_of<PAR>(4) * pl + b0, d[6], sc);
+    store_right<PREC>(A + (plane_of<PAR>(5) * pl + b0 + dm), 0, d[7], sc);
+    store_right<PREC>(A + (plane_of<PAR>(6) * pl + b0 + dp), 0, d[4], sc);
+    S::store4(A + plane_of<PAR>(7) * pl + b0, d[5], sc);
+    if (THERMAL) {
+      S::store4(G + b0, g[0], sc);
+      S::store4(G + (PAR ? 1 : 3) * pl + b0, g[3], sc);
+      S::store4(G + (PAR ? 2 : 4) * pl + b0, g[4], sc);
+      store_right<PREC>(G + (PAR ? 3 : 1) * pl + b0, 0, g[1], sc);
+      S::store4(G + ((PAR ? 4 : 2) * pl + b0 + dp), g[2], sc);
+    }
   }
 }
 
 template <int PREC, bool HET, bool THERMAL>
 static cudaError_t launch_ip_t(const StepParams& P, cudaStream_t s) {
+  const IpFrame F = ip_frame_of(P.nx, P.ny, P.bc_x, P.bc_y);
+  const int frame_blocks = (int)((F.total + kIpThreads - 1) / kIpThreads);
   const int groups = (P.nx + kIpCells - 1) / kIpCells;
-  const dim3 grid((groups + kIpThreads - 1) / kIpThreads, P.ny);
+  const int gx = (groups + kIpThreads - 1) / kIpThreads;
+  const long long blocks = (long long)frame_blocks + (long long)gx * P.ny;
   if (P.parity)
-    k_step_ip<PREC, HET, THERMAL, 1><<<grid, kIpThreads, 0, s>>>(P);
+    k_step_ip<PREC, HET, THERMAL, 1><<<(unsigned)blocks, kIpThreads, 0, s>>>(P, frame_blocks, gx);
   else
-    k_step_ip<PREC, HET, THERMAL, 0><<<grid, kIpThreads, 0, s>>>(P);
+    k_step_ip<PREC, HET, THERMAL, 0><<<(unsigned)blocks, kIpThreads, 0, s>>>(P, frame_blocks, gx);
   return cudaGetLastError();
 }
 
