@@ -55,12 +55,15 @@ def cavity_params(L):
     return dict(nu=lid * L / 100.0, phi=0.4, K=1e-3 * L * L, lid=lid)
 
 
-def source_hash():
-    """Hash of the sources that define the fused step kernel (a recorded ncu traffic figure is
-    only reported while these are unchanged)."""
+KERNEL_SOURCES = {"k_step": ("lbm_device.cuh", "tiles.cuh", "step.cu"), "k_step_ip": ("lbm_device.cuh", "inplace.cu")}
+
+
+def source_hash(kernel="k_step"):
+    """Hash of the sources that define a step kernel (a recorded ncu traffic figure is only
+    reported while these are unchanged)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1311_7239_gb300", "csrc")
-    for f in ("lbm_device.cuh", "tiles.cuh", "step.cu"):
+    for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -73,7 +76,7 @@ def traffic_for(kernel_key):
         with open(path) as fh:
             d = json.load(fh)
         e = d.get(kernel_key)
-        if e and e.get("source_hash") == source_hash():
+        if e and e.get("source_hash") == source_hash("k_step_ip" if kernel_key.startswith("k_step_ip") else "k_step"):
             return float(e["bytes_per_launch"])
     except Exception:
         pass
