@@ -469,7 +469,7 @@ def run_gpu(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs", "kernel": "k_step_ip" if streaming else "k_step",
                      "algorithmic_bytes_per_lu": bpl},
-        "gpu_launches": args.steps + (1 if streaming else 0),  # in-place: + the u(t-1) record before the last step
+        "gpu_launches": args.steps,
         "e2e": {"value": e2e_mlups, "unit": "MLUPS", "h2d_bytes_per_step": int(walls.numel() * 4),
                 "d2h_bytes_per_step": int(probe.numel() * 4), "steps": e2e_steps,
                 "call": "lbm_set_walls(host) + lbm_step(1) + lbm_probe(host) per step"},

@@ -69,9 +69,10 @@ extern "C" {
                                * ghost column right of the lattice).  Same arithmetic and results as
                                * LBM_STREAM_AB with half the population memory.  Sides: LBM_PERIODIC and
                                * LBM_WALL only (the extrapolated sides read a neighbour's state while it is
-                               * being overwritten); not for lbm_adjoint or batches.  lbm_step records u
-                               * before the last step of each call (8 B per cell, one read of the state per
-                               * call) for lbm_residual, unless LBM_OPT_NO_RESIDUAL_RECORD is set.  Limit:
+                               * being overwritten); not for lbm_adjoint or batches.  The last step of each
+                               * lbm_step call records the velocity of its collisions, u(t-1) for
+                               * lbm_residual (8 B per cell kept and written once per call), unless
+                               * LBM_OPT_NO_RESIDUAL_RECORD is set.  Limit:
                                * 8 ((ny + 2) pitch + ny + 2) <= 2^32 elements, pitch = nx rounded up to 128
                                * (about 23000 x 23000). */
 /* lbm_config.options bits */

@@ -684,13 +684,17 @@ int lbm_step(lbm_ctx* c, int n) {
   if (!c) return fail(LBM_EINVAL, "null context");
   if (n < 0) return fail(LBM_EINVAL, "negative step count");
   if (!c->uprev || n == 0) return run_steps(c, n);
-  // in-place: u(t-1) of the residual is recorded before the last step (its state is overwritten)
+  // in-place: the last step records the velocity of its collisions, u(t-1) of the residual once it
+  // is done (the state it came from is overwritten)
   int rc = run_steps(c, n - 1);
   if (rc) return rc;
-  const size_t nn = (size_t)c->cfg.nx * c->cfg.ny;
-  LBM_CUDA(launch_macros(params_for(c), c->prec, c->het, thermal_of(c), nullptr, c->uprev, c->uprev + nn, nullptr, c->stream),
-           "macros kernel");
-  return run_steps(c, 1);
+  StepParams P = params_at(c, c->cur);
+  P.urec = c->uprev;
+  LBM_CUDA(launch_step_inplace(P, c->prec, c->het, thermal_of(c), c->stream), "step kernel");
+  c->cur ^= 1;
+  ++c->steps;
+  ++c->history;
+  return LBM_OK;
 }
 
 int lbm_set_walls(lbm_ctx* c, const float* u_wall) {

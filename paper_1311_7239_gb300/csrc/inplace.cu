@@ -21,10 +21,18 @@ namespace lbm {
 constexpr int kIpThreads = 128;
 constexpr int kIpCells = 4;
 
+// u of the collision at (x, y) into the record of the previous state's velocity (the residual's
+// u(t-1) once the step is done)
+__device__ __forceinline__ void record_u(const StepParams& P, int x, int y, float ux, float uy) {
+  const int64_t o = (int64_t)y * P.nx + x;
+  P.urec[o] = ux;
+  P.urec[(int64_t)P.nx * P.ny + o] = uy;
+}
+
 // one cell with the generic slot rules: pulls with bounce-back, collision, stores into the slots
 // of the next parity (ghost slots for populations that leave through a wall)
-template <int PREC, bool HET, bool THERMAL>
-__device__ __forceinline__ void ip_cell(const StepParams& P, typename Store<PREC>::T* A, typename Store<PREC>::T* G, int x, int y) {
+template <int PREC, bool HET, bool THERMAL, bool REC>
+__device__ __noinline__ void ip_cell(const StepParams& P, typename Store<PREC>::T* A, typename Store<PREC>::T* G, int x, int y) {
   using S = Store<PREC>;
   float d[8], g[5];
   pull_cell<PREC>(P, A, x, y, d);
@@ -37,6 +45,7 @@ __device__ __forceinline__ void ip_cell(const StepParams& P, typename Store<PREC
   float ux, uy, phip;
   collide_d2q8(d, cf, P.ax, ay, P, ux, uy, phip);
   if (!(fabsf(ux) + fabsf(uy) < 1e30f)) atomicOr(P.err, 1u);
+  if (REC) record_u(P, x, y, ux, uy);
   const int nxt = P.parity ^ 1;
 #pragma unroll
   for (int j = 0; j < 8; ++j) A[ip_off(P, x + ex_of(j), y + ey_of(j), j, nxt)] = S::enc(d[j], P.scale);
@@ -130,7 +139,7 @@ constexpr bool kIpPacked = PREC != PREC_FP32 && !HET && !THERMAL;
 // the temperature populations (96; at 80 the FP32 thermal step spills).  Blocks [0, frame_blocks)
 // do the frame cells, one per thread, with the generic rules; the others do groups of four cells
 // of one row, gx blocks per row, and skip the groups of the frame.
-template <int PREC, bool HET, bool THERMAL, int PAR>
+template <int PREC, bool HET, bool THERMAL, int PAR, bool REC>
 __global__ void __launch_bounds__(kIpThreads, THERMAL ? 5 : 8) k_step_ip(const StepParams P, int frame_blocks, int gx) {
   using S = Store<PREC>;
   using T = typename S::T;
@@ -144,7 +153,7 @@ __global__ void __launch_bounds__(kIpThreads, THERMAL ? 5 : 8) k_step_ip(const S
     int x, y;
     ip_frame_cell(F, P.nx, P.ny, k, x, y);
     if (!dbg_check(P, x >= 0 && x < P.nx && y >= 0 && y < P.ny)) return;
-    ip_cell<PREC, HET, THERMAL>(P, A, G, x, y);
+    ip_cell<PREC, HET, THERMAL, REC>(P, A, G, x, y);
     return;
   }
   const int b = (int)blockIdx.x - frame_blocks;
@@ -183,6 +192,10 @@ __global__ void __launch_bounds__(kIpThreads, THERMAL ? 5 : 8) k_step_ip(const S
       float2 ux, uy;
       collide_pair(dp2, pair_coef_uniform(P.pc), f2(P.pc.u_hx), f2(P.pc.u_hy), P.pc, ux, uy);
       check += (fabsf(ux.x) + fabsf(uy.x)) + (fabsf(ux.y) + fabsf(uy.y));
+      if (REC) {
+        record_u(P, x0 + 2 * h, y, ux.x, uy.x);
+        record_u(P, x0 + 2 * h + 1, y, ux.y, uy.y);
+      }
 #pragma unroll
       for (int i = 0; i < 8; ++i) w[i][h] = S::f2w(dp2[i]);
     }
@@ -234,6 +247,7 @@ __global__ void __launch_bounds__(kIpThreads, THERMAL ? 5 : 8) k_step_ip(const S
       float ux, uy, phip;
       collide_d2q8(dc, cf, P.ax, ay, P, ux, uy, phip);
       check += fabsf(ux) + fabsf(uy);
+      if (REC) record_u(P, x0 + c, y, ux, uy);
 #pragma unroll
       for (int i = 0; i < 8; ++i) d[i][c] = dc[i];
       if (THERMAL) {
@@ -276,10 +290,17 @@ static cudaError_t launch_ip_t(const StepParams& P, cudaStream_t s) {
   const int groups = (P.nx + kIpCells - 1) / kIpCells;
   const int gx = (groups + kIpThreads - 1) / kIpThreads;
   const long long blocks = (long long)frame_blocks + (long long)gx * P.ny;
-  if (P.parity)
-    k_step_ip<PREC, HET, THERMAL, 1><<<(unsigned)blocks, kIpThreads, 0, s>>>(P, frame_blocks, gx);
-  else
-    k_step_ip<PREC, HET, THERMAL, 0><<<(unsigned)blocks, kIpThreads, 0, s>>>(P, frame_blocks, gx);
+  // the variant that records u runs once per lbm_step call
+  if (P.urec) {
+    if (P.parity)
+      k_step_ip<PREC, HET, THERMAL, 1, true><<<(unsigned)blocks, kIpThreads, 0, s>>>(P, frame_blocks, gx);
+    else
+      k_step_ip<PREC, HET, THERMAL, 0, true><<<(unsigned)blocks, kIpThreads, 0, s>>>(P, frame_blocks, gx);
+  } else if (P.parity) {
+    k_step_ip<PREC, HET, THERMAL, 1, false><<<(unsigned)blocks, kIpThreads, 0, s>>>(P, frame_blocks, gx);
+  } else {
+    k_step_ip<PREC, HET, THERMAL, 0, false><<<(unsigned)blocks, kIpThreads, 0, s>>>(P, frame_blocks, gx);
+  }
   return cudaGetLastError();
 }
 

@@ -65,6 +65,7 @@ struct StepParams {
   float Tw[4];
   int Tdir[4];        // 1 = wall temperature prescribed, 0 = adiabatic
   unsigned int* err;  // bit 0: non-finite velocity
+  float* urec;        // in-place step: if set, the velocity of every cell's collision, dense [2][ny][nx]
   PairConst pc;
 };
 

@@ -185,7 +185,7 @@ def test_same_result_as_ab_streaming(lbm):
         ra, rb = a.residual(), b.residual()
         pa, pb = a.probe(75, 69), b.probe(75, 69)
     assert rel_l2(fb, fa) <= 1e-6, rel_l2(fb, fa)
-    assert abs(ra - rb) <= 1e-4 * abs(ra), (ra, rb)
+    assert abs(ra - rb) <= 1e-3 * abs(ra), (ra, rb)  # u(t-1): the collision's sums vs the read-out's (rounding order)
     assert np.allclose(np.asarray(pa), np.asarray(pb), rtol=1e-5, atol=1e-7)
     print("in-place vs A-B after 101 steps: max |df| =", float(np.abs(fb - fa).max()), "bitwise:", bool(np.array_equal(fa, fb)))
 
@@ -200,7 +200,7 @@ def test_residual_matches_oracle(lbm):
     want = fl.residual(u_now[0], u_now[1], u_prev[0], u_prev[1])
     with case.lattice(lbm) as lat:
         lat.step(20)
-        lat.step(40)  # u(t-1) is recorded before the last step of each call
+        lat.step(40)  # the last step of each call records the u(t-1) of the residual
         got = lat.residual()
     assert abs(got - want) <= 1e-3 * want, (got, want)
 
