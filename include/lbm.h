@@ -183,7 +183,9 @@ LBM_API int lbm_get_populations(lbm_ctx* ctx, float* f, float* g);
 LBM_API int lbm_set_populations(lbm_ctx* ctx, const float* f, const float* g);
 
 /* Steady-state residual r = ||u(t) - u(t-1)||_2 / ||u(t)||_2 over all cells, summed in FP64
- * on the device (needs one step since the last initialisation or import; ESTATE before that).  Waits for the stream. */
+ * on the device (needs one step since the last initialisation or import; ESTATE before that).
+ * In-place contexts take u(t-1) from the velocity the last step of the last lbm_step call
+ * recorded (ESTATE with LBM_OPT_NO_RESIDUAL_RECORD).  Waits for the stream. */
 LBM_API int lbm_residual(lbm_ctx* ctx, double* r);
 
 /* Allocation-free residual, for callers that must not allocate device memory (a service that
@@ -276,10 +278,11 @@ LBM_API int lbm_batch_info(const lbm_batch* b, int64_t* cells, int64_t* steps, u
 /* Wait for the batch's stream and report a deferred error. */
 LBM_API int lbm_batch_sync(lbm_batch* b);
 
-/* Checkpoint / resume: write the context's state (both population buffers, temperature
- * populations, medium, step counters, configuration) to a file, and read it back into a context
- * of the same size, precision and thermal mode; stepping after lbm_load continues bitwise as the
- * saved context would have.  Both wait for the stream.  EINVAL on I/O or format errors. */
+/* Checkpoint / resume: write the context's state (both population buffers -- in-place contexts:
+ * the one buffer and the u(t-1) record --, temperature populations, medium, step counters,
+ * configuration) to a file, and read it back into a context of the same size, precision, thermal
+ * mode, streaming form and record option; stepping after lbm_load continues bitwise as the saved
+ * context would have.  Both wait for the stream.  EINVAL on I/O or format errors. */
 LBM_API int lbm_save(lbm_ctx* ctx, const char* path);
 LBM_API int lbm_load(lbm_ctx* ctx, const char* path);
 
