@@ -247,7 +247,9 @@ LBM_API int lbm_nusselt(lbm_ctx* ctx, int side, double* nu);
  * boundaries, parameters, medium; one storage precision for all), advanced together by one
  * persistent launch per time step over the concatenated work items of all lattices, with
  * runs of 32 steps replayed as a captured CUDA graph.  The batch runs on cfgs[0].stream (NULL:
- * a stream of its own).  Every lattice keeps per-cell medium fields (8 B per cell).
+ * a stream of its own).  Every lattice keeps per-cell medium fields (8 B per cell).  All lattices
+ * use one streaming form: LBM_STREAM_AB (two population pools), or LBM_STREAM_INPLACE (one pool,
+ * periodic and halfway-wall sides, launch shape 128 threads per CTA and one CTA per work item).
  * ------------------------------------------------------------------------------------------- */
 typedef struct lbm_batch lbm_batch;
 
@@ -264,7 +266,8 @@ LBM_API int lbm_batch_step(lbm_batch* b, int n);
 LBM_API int lbm_batch_step_each(lbm_batch* b, int n);
 /* Launch shape of the batched kernel: threads per CTA (64, 128, 256) and CTAs per SM: 0 = one CTA
  * per work item (a lattice table of 4 bytes per item is kept on the device), 1..32 = a persistent
- * grid of SMs x k CTAs, k lowered to the kernel's occupancy limit so that every CTA is resident. */
+ * grid of SMs x k CTAs, k lowered to the kernel's occupancy limit so that every CTA is resident.
+ * In-place batches take (128, 0) only (EINVAL otherwise). */
 LBM_API int lbm_batch_set_launch(lbm_batch* b, int threads_per_cta, int ctas_per_sm);
 LBM_API int lbm_batch_get_launch(const lbm_batch* b, int* threads_per_cta, int* ctas_per_sm);
 /* Time `steps` steps for every launch shape on a copy of the current state, keep the fastest,

@@ -3,7 +3,9 @@
 //
 // Memory: the population buffers of all lattices live in two pools (A-B streaming for the whole
 // batch), each lattice's planes at its own offset with its own pitch; the medium fields and
-// wall velocities likewise.  Per step, the work items of all lattices (frame groups and row
+// wall velocities likewise.  With in-place streaming (every lattice LBM_STREAM_INPLACE) there is one
+// pool, each lattice's buffer laid out as for a single in-place context (ghost rows and column),
+// and one CTA per work item of the in-place step.  Per step, the work items of all lattices (frame groups and row
 // chunks, exactly as for a single lattice) are concatenated and either one CTA per item (k = 0,
 // with a per-item lattice table) or a persistent grid of SMs x k CTAs walks them; the CTA size
 // and k are tuning parameters (lbm_batch_tune times the choices on the live batch).
@@ -44,6 +46,8 @@ struct lbm_batch {
   std::vector<int> pitch;
   std::vector<int64_t> plane, foff, moff;
   void* pool[2] = {nullptr, nullptr};
+  bool inplace = false;
+  int64_t pool_elems = 0;  // elements of one pool
   float* phi = nullptr;
   float* K = nullptr;
   float* walls = nullptr;
@@ -110,11 +114,14 @@ StepParams params_of(const lbm_batch* b, int d, int cur) { return b->hp[cur][d];
 int set_launch(lbm_batch* b, int nt, int ctas_per_sm) {
   if (nt != 64 && nt != 128 && nt != 256) return fail_msg(LBM_EINVAL, "threads per CTA must be 64, 128 or 256");
   if (ctas_per_sm < 0 || ctas_per_sm > 32) return fail_msg(LBM_EINVAL, "CTAs per SM must be in [0, 32]");
+  if (b->inplace && (nt != 128 || ctas_per_sm != 0))
+    return fail_msg(LBM_EINVAL, "in-place batches run one CTA of 128 threads per work item (launch shape 128, 0)");
   std::vector<int64_t> start(b->n);
   int64_t total = 0;
   for (int d = 0; d < b->n; ++d) {
     start[d] = total;
-    total += batch_items((int)b->cfg[d].nx, (int)b->cfg[d].ny, (int)b->cfg[d].bc_y, nt);
+    const lbm_config& c = b->cfg[d];
+    total += b->inplace ? inplace_items((int)c.nx, (int)c.ny, (int)c.bc_x, (int)c.bc_y) : batch_items((int)c.nx, (int)c.ny, (int)c.bc_y, nt);
   }
   LBM_BCUDA(cudaMemcpy(b->item_start, start.data(), b->n * sizeof(int64_t), cudaMemcpyHostToDevice), "copy of the item table");
   b->total_items = total;
@@ -152,6 +159,10 @@ int set_launch(lbm_batch* b, int nt, int ctas_per_sm) {
 }
 
 int launch_once(lbm_batch* b, int cur, cudaStream_t s) {
+  if (b->inplace) {
+    LBM_BCUDA(launch_step_batch_inplace(b->dp[cur], b->item_start, b->item_lattice, b->total_items, b->prec, cur, s), "batched step kernel");
+    return LBM_OK;
+  }
   LBM_BCUDA(launch_step_batch(b->dp[cur], b->item_start, b->ctas_per_sm == 0 ? b->item_lattice : nullptr, b->n, b->total_items, b->prec,
                               b->nt, b->grid, s),
             "batched step kernel");
@@ -163,8 +174,10 @@ int capture(lbm_batch* b, int cur) {
   LBM_BCUDA(cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
   cudaError_t le = cudaSuccess;
   for (int k = 0; k < kBatchGraphSteps && le == cudaSuccess; ++k)
-    le = launch_step_batch(b->dp[cur ^ (k & 1)], b->item_start, b->ctas_per_sm == 0 ? b->item_lattice : nullptr, b->n, b->total_items,
-                           b->prec, b->nt, b->grid, b->capture_stream);
+    le = b->inplace ? launch_step_batch_inplace(b->dp[cur ^ (k & 1)], b->item_start, b->item_lattice, b->total_items, b->prec,
+                                                cur ^ (k & 1), b->capture_stream)
+                    : launch_step_batch(b->dp[cur ^ (k & 1)], b->item_start, b->ctas_per_sm == 0 ? b->item_lattice : nullptr, b->n,
+                                        b->total_items, b->prec, b->nt, b->grid, b->capture_stream);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(b->capture_stream, &g);
   if (le != cudaSuccess || e != cudaSuccess) {
@@ -220,7 +233,7 @@ int lbm_batch_create(const lbm_config* cfgs, int n, lbm_batch** out) {
     int rc = validate_config(&cfgs[d]);
     if (rc) return rc;
     if (cfgs[d].thermal) return fail_msg(LBM_EINVAL, "lbm_batch_create: batches hold isothermal lattices only");
-    if (cfgs[d].streaming != LBM_STREAM_AB) return fail_msg(LBM_EINVAL, "lbm_batch_create: batches use A-B streaming");
+    if (cfgs[d].streaming != cfgs[0].streaming) return fail_msg(LBM_EINVAL, "lbm_batch_create: all lattices need one streaming form");
     if (cfgs[d].precision != cfgs[0].precision) return fail_msg(LBM_EINVAL, "lbm_batch_create: all lattices need one precision");
   }
   lbm_batch* b = new (std::nothrow) lbm_batch();
@@ -229,6 +242,7 @@ int lbm_batch_create(const lbm_config* cfgs, int n, lbm_batch** out) {
   b->cfg.assign(cfgs, cfgs + n);
   b->prec = (int)cfgs[0].precision;
   b->elem = b->prec == PREC_FP32 ? 4 : 2;
+  b->inplace = cfgs[0].streaming == LBM_STREAM_INPLACE;
   if (cudaGetDevice(&b->device) != cudaSuccess || cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess) {
     delete b;
     return fail_msg(LBM_ECUDA, "no usable current device");
@@ -248,15 +262,24 @@ int lbm_batch_create(const lbm_config* cfgs, int n, lbm_batch** out) {
   int64_t fel = 0, mel = 0;
   for (int d = 0; d < n; ++d) {
     b->pitch[d] = (int)((cfgs[d].nx + 127) / 128 * 128);
-    b->plane[d] = (int64_t)b->pitch[d] * cfgs[d].ny;
+    b->plane[d] = (int64_t)b->pitch[d] * (cfgs[d].ny + (b->inplace ? 2 : 0));
     b->foff[d] = fel;
     b->moff[d] = mel;
-    fel += 8 * b->plane[d];
+    // in-place: the planes with their ghost rows, then the ghost column (rounded to 128 elements
+    // so that the next lattice's rows stay aligned); the step indexes a buffer with 32-bit offsets
+    const int64_t buf = b->inplace ? (8 * (b->plane[d] + cfgs[d].ny + 2) + 127) / 128 * 128 : 8 * b->plane[d];
+    if (b->inplace && buf > (1ll << 32)) {
+      if (b->own_stream) cudaStreamDestroy(b->stream);
+      delete b;
+      return fail_msg(LBM_EINVAL, "lbm_batch_create: an in-place lattice needs 8 ((ny + 2) pitch + ny + 2) <= 2^32 elements");
+    }
+    fel += buf;
     mel += b->plane[d];
     b->cells += (int64_t)cfgs[d].nx * cfgs[d].ny;
   }
+  b->pool_elems = fel;
   int rc = LBM_OK;
-  for (int k = 0; k < 2 && rc == LBM_OK; ++k) rc = balloc(b, &b->pool[k], fel * b->elem, "cudaMalloc(population pools)");
+  for (int k = 0; k < (b->inplace ? 1 : 2) && rc == LBM_OK; ++k) rc = balloc(b, &b->pool[k], fel * b->elem, "cudaMalloc(population pools)");
   if (rc == LBM_OK) rc = balloc(b, reinterpret_cast<void**>(&b->phi), mel * sizeof(float), "cudaMalloc(porosity pool)");
   if (rc == LBM_OK) rc = balloc(b, reinterpret_cast<void**>(&b->K), mel * sizeof(float), "cudaMalloc(permeability pool)");
   if (rc == LBM_OK) rc = balloc(b, reinterpret_cast<void**>(&b->walls), 8 * n * sizeof(float), "cudaMalloc(walls)");
@@ -272,7 +295,7 @@ int lbm_batch_create(const lbm_config* cfgs, int n, lbm_batch** out) {
     for (int i = 0; i < 8; ++i) w[8 * d + i] = (float)cfgs[d].u_wall[i / 2][i % 2];
   cudaError_t e = cudaMemcpy(b->walls, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->err, 0, sizeof(unsigned int), b->stream);
-  for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaMemsetAsync(b->pool[k], 0, fel * b->elem, b->stream);
+  for (int k = 0; k < (b->inplace ? 1 : 2) && e == cudaSuccess; ++k) e = cudaMemsetAsync(b->pool[k], 0, fel * b->elem, b->stream);
   if (e != cudaSuccess) {
     release(b);
     return fail_msg(LBM_ECUDA, "batch set-up copies");
@@ -287,14 +310,24 @@ int lbm_batch_create(const lbm_config* cfgs, int n, lbm_batch** out) {
     P.err = b->err;
     P.phi = b->phi + b->moff[d];
     P.K = b->K + b->moff[d];
-    void* A = pool0 + b->foff[d] * b->elem;
-    void* B = pool1 + b->foff[d] * b->elem;
-    b->hp[0][d] = P;
-    b->hp[0][d].src = A;
-    b->hp[0][d].dst = B;
-    b->hp[1][d] = P;
-    b->hp[1][d].src = B;
-    b->hp[1][d].dst = A;
+    if (b->inplace) {  // one buffer from its row 0; the parity selects the slots
+      void* A = pool0 + (b->foff[d] + b->pitch[d]) * b->elem;
+      P.inplace = 1;
+      for (int k = 0; k < 2; ++k) {
+        b->hp[k][d] = P;
+        b->hp[k][d].src = b->hp[k][d].dst = A;
+        b->hp[k][d].parity = k;
+      }
+    } else {
+      void* A = pool0 + b->foff[d] * b->elem;
+      void* B = pool1 + b->foff[d] * b->elem;
+      b->hp[0][d] = P;
+      b->hp[0][d].src = A;
+      b->hp[0][d].dst = B;
+      b->hp[1][d] = P;
+      b->hp[1][d].src = B;
+      b->hp[1][d].dst = A;
+    }
     // every lattice keeps per-cell medium fields, filled with its uniform values until set
     e = launch_medium(nullptr, nullptr, (float)cfgs[d].phi, (float)cfgs[d].K, (int)cfgs[d].nx, (int)cfgs[d].ny, b->pitch[d],
                       b->phi + b->moff[d], b->K + b->moff[d], b->err, 0, b->stream);
@@ -306,7 +339,7 @@ int lbm_batch_create(const lbm_config* cfgs, int n, lbm_batch** out) {
     release(b);
     return fail_msg(LBM_ECUDA, "batch parameter upload");
   }
-  if ((rc = set_launch(b, 64, 0)) || (rc = lbm_batch_init_equilibrium(b, -1, 1.0, 0.0, 0.0, 0))) {
+  if ((rc = set_launch(b, b->inplace ? 128 : 64, 0)) || (rc = lbm_batch_init_equilibrium(b, -1, 1.0, 0.0, 0.0, 0))) {
     release(b);
     return rc;
   }
@@ -354,6 +387,12 @@ int lbm_batch_init_equilibrium(lbm_batch* b, int d, double p0, double ux0, doubl
   const int lo = d < 0 ? 0 : d, hi = d < 0 ? b->n : d + 1;
   for (int k = lo; k < hi; ++k) {
     StepParams P = params_of(b, k, b->cur);
+    if (b->inplace) {
+      LBM_BCUDA(launch_put_inplace(P, b->prec, true, nullptr, nullptr, true, false, (float)p0, (float)ux0, (float)uy0,
+                                   phi_p_uniform ? 1 : 0, 0.0f, b->stream),
+                "init kernel");
+      continue;
+    }
     P.dst = const_cast<void*>(P.src);  // the init writes the current buffer
     LBM_BCUDA(launch_init(P, b->prec, true, false, (float)p0, (float)ux0, (float)uy0, phi_p_uniform ? 1 : 0, 0.0f, true, false,
                           b->stream),
@@ -390,7 +429,9 @@ int lbm_batch_step_each(lbm_batch* b, int n) {
   for (int d = 0; d < b->n; ++d) {
     int cur = b->cur;
     for (int k = 0; k < n; ++k) {
-      LBM_BCUDA(launch_step(params_of(b, d, cur), b->prec, true, false, b->stream), "step kernel");
+      const StepParams P = params_of(b, d, cur);
+      LBM_BCUDA(b->inplace ? launch_step_inplace(P, b->prec, true, false, b->stream) : launch_step(P, b->prec, true, false, b->stream),
+                "step kernel");
       cur ^= 1;
     }
   }
@@ -414,23 +455,26 @@ int lbm_batch_get_launch(const lbm_batch* b, int* threads_per_cta, int* ctas_per
 int lbm_batch_tune(lbm_batch* b, int steps, int* threads_per_cta, int* ctas_per_sm, float* ms_per_step) {
   if (!b) return fail_msg(LBM_EINVAL, "null batch");
   if (steps < 1) return fail_msg(LBM_EINVAL, "steps must be positive");
-  // time every choice on a copy of the current state, then restore it
-  const size_t pool_bytes = (size_t)(b->foff[b->n - 1] + 8 * b->plane[b->n - 1]) * b->elem;
+  // time every choice on a copy of the current state, then restore it (in-place batches have one)
+  const size_t pool_bytes = (size_t)b->pool_elems * b->elem;
   void* save = nullptr;
   LBM_BCUDA(cudaMalloc(&save, pool_bytes), "cudaMalloc(tuning copy)");
-  cudaMemcpyAsync(save, b->pool[b->cur], pool_bytes, cudaMemcpyDeviceToDevice, b->stream);
+  void* live = b->pool[b->inplace ? 0 : b->cur];
+  cudaMemcpyAsync(save, live, pool_bytes, cudaMemcpyDeviceToDevice, b->stream);
   const int nts[3] = {64, 128, 256};
   const int ks[6] = {0, 1, 2, 4, 8, 16};  // 0: one CTA per work item
+  const int n_nt = b->inplace ? 1 : 3, n_k = b->inplace ? 1 : 6;
+  const int* nt_list = b->inplace ? &nts[1] : nts;
   float best = 1e30f;
   int best_nt = b->nt, best_k = b->ctas_per_sm;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   int rc = LBM_OK;
-  for (int a = 0; a < 3 && rc == LBM_OK; ++a)
-    for (int c = 0; c < 6 && rc == LBM_OK; ++c) {
-      if (ks[c] > batch_max_ctas_per_sm(b->prec, nts[a])) continue;  // persistent CTAs must be resident
-      if ((rc = set_launch(b, nts[a], ks[c]))) break;
+  for (int a = 0; a < n_nt && rc == LBM_OK; ++a)
+    for (int c = 0; c < n_k && rc == LBM_OK; ++c) {
+      if (ks[c] > batch_max_ctas_per_sm(b->prec, nt_list[a])) continue;  // persistent CTAs must be resident
+      if ((rc = set_launch(b, nt_list[a], ks[c]))) break;
       if ((rc = launch_once(b, b->cur, b->stream))) break;  // warm-up
       cudaEventRecord(e0, b->stream);
       for (int s = 0; s < steps && rc == LBM_OK; ++s) rc = launch_once(b, b->cur ^ ((s + 1) & 1), b->stream);
@@ -441,11 +485,11 @@ int lbm_batch_tune(lbm_batch* b, int steps, int* threads_per_cta, int* ctas_per_
       ms /= steps;
       if (ms < best) {
         best = ms;
-        best_nt = nts[a];
+        best_nt = nt_list[a];
         best_k = ks[c];
       }
     }
-  cudaMemcpyAsync(b->pool[b->cur], save, pool_bytes, cudaMemcpyDeviceToDevice, b->stream);
+  cudaMemcpyAsync(live, save, pool_bytes, cudaMemcpyDeviceToDevice, b->stream);
   cudaStreamSynchronize(b->stream);
   cudaFree(save);
   cudaEventDestroy(e0);

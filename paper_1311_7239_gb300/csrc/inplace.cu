@@ -135,20 +135,19 @@ __device__ __forceinline__ void ip_frame_cell(const IpFrame& F, int nx, int ny, 
 template <int PREC, bool HET, bool THERMAL>
 constexpr bool kIpPacked = PREC != PREC_FP32 && !HET && !THERMAL;
 
-// Register caps: 8 CTAs of 128 threads per SM for the flow (64 registers, as the A-B step), 5 with
-// the temperature populations (96; at 80 the FP32 thermal step spills).  Blocks [0, frame_blocks)
-// do the frame cells, one per thread, with the generic rules; the others do groups of four cells
-// of one row, gx blocks per row, and skip the groups of the frame.
+// Block blk of one in-place step of a lattice: blocks [0, frame_blocks) do the frame cells, one
+// per thread, with the generic rules; the others do groups of four cells of one row, gx blocks per
+// row, and skip the groups of the frame.
 template <int PREC, bool HET, bool THERMAL, int PAR, bool REC>
-__global__ void __launch_bounds__(kIpThreads, THERMAL ? 5 : 8) k_step_ip(const StepParams P, int frame_blocks, int gx) {
+__device__ __forceinline__ void ip_block(const StepParams& P, int frame_blocks, int gx, int blk) {
   using S = Store<PREC>;
   using T = typename S::T;
   constexpr int C = kIpCells;
   T* __restrict__ A = static_cast<T*>(P.dst);
   T* __restrict__ G = static_cast<T*>(P.gdst);
-  if ((int)blockIdx.x < frame_blocks) {
+  if (blk < frame_blocks) {
     const IpFrame F = ip_frame_of(P.nx, P.ny, P.bc_x, P.bc_y);
-    const int64_t k = (int64_t)blockIdx.x * kIpThreads + threadIdx.x;
+    const int64_t k = (int64_t)blk * kIpThreads + threadIdx.x;
     if (k >= F.total) return;
     int x, y;
     ip_frame_cell(F, P.nx, P.ny, k, x, y);
@@ -156,7 +155,7 @@ __global__ void __launch_bounds__(kIpThreads, THERMAL ? 5 : 8) k_step_ip(const S
     ip_cell<PREC, HET, THERMAL, REC>(P, A, G, x, y);
     return;
   }
-  const int b = (int)blockIdx.x - frame_blocks;
+  const int b = blk - frame_blocks;
   const int y = b / gx;
   const int x0 = ((b - y * gx) * kIpThreads + (int)threadIdx.x) * C;
   if (x0 >= P.nx || !dbg_check(P, y < P.ny)) return;
@@ -283,6 +282,34 @@ __global__ void __launch_bounds__(kIpThreads, THERMAL ? 5 : 8) k_step_ip(const S
   }
 }
 
+// Register caps: 8 CTAs of 128 threads per SM for the flow (64 registers, as the A-B step), 5 with
+// the temperature populations (96; at 80 the FP32 thermal step spills).
+template <int PREC, bool HET, bool THERMAL, int PAR, bool REC>
+__global__ void __launch_bounds__(kIpThreads, THERMAL ? 5 : 8) k_step_ip(const StepParams P, int frame_blocks, int gx) {
+  ip_block<PREC, HET, THERMAL, PAR, REC>(P, frame_blocks, gx, (int)blockIdx.x);
+}
+
+// Batched ensembles with in-place streaming: one CTA per work item, the item's lattice from a
+// per-item table and the lattice's parameters staged once per CTA in shared memory, as in the A-B
+// batched step; the lattices' items are those of k_step_ip, concatenated (item_start ascending).
+template <int PREC, int PAR>
+__global__ void __launch_bounds__(kIpThreads, 8) k_step_ip_batch(const StepParams* __restrict__ Pd, const int64_t* __restrict__ item_start,
+                                                               const int* __restrict__ item_lattice) {
+  __shared__ StepParams sP;
+  const int d = item_lattice[blockIdx.x];
+  {
+    static_assert(sizeof(StepParams) % 8 == 0, "parameters are copied as 8-byte words");
+    const unsigned long long* from = reinterpret_cast<const unsigned long long*>(Pd + d);
+    unsigned long long* to = reinterpret_cast<unsigned long long*>(&sP);
+    for (int i = threadIdx.x; i < (int)(sizeof(StepParams) / 8); i += kIpThreads) to[i] = from[i];
+  }
+  __syncthreads();
+  const IpFrame F = ip_frame_of(sP.nx, sP.ny, sP.bc_x, sP.bc_y);
+  const int frame_blocks = (int)((F.total + kIpThreads - 1) / kIpThreads);
+  const int gx = ((sP.nx + kIpCells - 1) / kIpCells + kIpThreads - 1) / kIpThreads;
+  ip_block<PREC, true, false, PAR, false>(sP, frame_blocks, gx, (int)((int64_t)blockIdx.x - item_start[d]));
+}
+
 template <int PREC, bool HET, bool THERMAL>
 static cudaError_t launch_ip_t(const StepParams& P, cudaStream_t s) {
   const IpFrame F = ip_frame_of(P.nx, P.ny, P.bc_x, P.bc_y);
@@ -308,6 +335,27 @@ template <int PREC>
 static cudaError_t launch_ip_p(const StepParams& P, bool het, bool thermal, cudaStream_t s) {
   if (thermal) return het ? launch_ip_t<PREC, true, true>(P, s) : launch_ip_t<PREC, false, true>(P, s);
   return het ? launch_ip_t<PREC, true, false>(P, s) : launch_ip_t<PREC, false, false>(P, s);
+}
+
+// work items (CTAs) of one in-place step of a lattice
+int64_t inplace_items(int nx, int ny, int bc_x, int bc_y) {
+  const IpFrame F = ip_frame_of(nx, ny, bc_x, bc_y);
+  const int64_t gx = ((nx + kIpCells - 1) / kIpCells + kIpThreads - 1) / kIpThreads;
+  return (F.total + kIpThreads - 1) / kIpThreads + gx * ny;
+}
+
+cudaError_t launch_step_batch_inplace(const StepParams* Pd, const int64_t* item_start, const int* item_lattice, int64_t total, int prec,
+                                      int parity, cudaStream_t s) {
+#define LBM_IPB(PR)                                                                                   \
+  do {                                                                                                \
+    if (parity) k_step_ip_batch<PR, 1><<<(unsigned)total, kIpThreads, 0, s>>>(Pd, item_start, item_lattice); \
+    else k_step_ip_batch<PR, 0><<<(unsigned)total, kIpThreads, 0, s>>>(Pd, item_start, item_lattice);        \
+  } while (0)
+  if (prec == PREC_FP32) LBM_IPB(PREC_FP32);
+  else if (prec == PREC_FP16) LBM_IPB(PREC_FP16);
+  else LBM_IPB(PREC_BF16);
+#undef LBM_IPB
+  return cudaGetLastError();
 }
 
 cudaError_t launch_step_inplace(const StepParams& P, int prec, bool het, bool thermal, cudaStream_t s) {

@@ -22,6 +22,9 @@ cudaError_t launch_step_batch(const StepParams* Pd, const int64_t* item_start, c
                               int nt, int grid, cudaStream_t s);
 cudaError_t launch_step(const StepParams& P, int prec, bool het, bool thermal, cudaStream_t s);
 cudaError_t launch_step_inplace(const StepParams& P, int prec, bool het, bool thermal, cudaStream_t s);
+int64_t inplace_items(int nx, int ny, int bc_x, int bc_y);
+cudaError_t launch_step_batch_inplace(const StepParams* Pd, const int64_t* item_start, const int* item_lattice, int64_t total, int prec,
+                                      int parity, cudaStream_t s);
 cudaError_t launch_put_inplace(const StepParams& P, int prec, bool het, const float* f, const float* g, bool flow, bool temp,
                                float p0, float ux0, float uy0, int phip_uniform, float T_init, cudaStream_t s);
 cudaError_t launch_medium(const float* eps, const float* K, float phi_u, float K_u, int nx, int ny, int pitch, float* phi_out,

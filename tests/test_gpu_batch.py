@@ -1,6 +1,7 @@
 """Batched ensembles (lbm_batch_*): the persistent batched kernel gives bitwise the results of the
 single-lattice kernel on every lattice, for every launch shape; the one-by-one mode and the
-autotuner leave results unchanged; a small lattice of the batch matches the FP64 oracle."""
+autotuner leave results unchanged; a small lattice of the batch matches the FP64 oracle.  Batches
+with in-place streaming give bitwise the results of single in-place lattices."""
 import numpy as np
 import pytest
 
@@ -93,3 +94,44 @@ def test_tuning_choice_is_cached_on_disk(lbm, tmp_path):
     with ensemble.build(lbm, cfgs, media) as b:
         nt2, k2, ms2, hit2 = b.tune_cached(path, steps=2)
         assert hit2 and (nt2, k2) == (nt, k) and b.get_launch() == (nt, k)
+
+
+def _inplace(lbm, cfgs):
+    for c in cfgs:
+        c.streaming = lbm.STREAM_INPLACE
+    return cfgs
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_inplace_batch_equals_single_inplace_lattices_bitwise(lbm, prec):
+    cfgs, media = ensemble.ensemble(lbm, n=7, seed=3, lo=8, hi=300, precision=prec)
+    cfgs = _inplace(lbm, cfgs)
+    steps = 45
+    want = _singles(lbm, cfgs, media, steps)
+    with ensemble.build(lbm, cfgs, media) as b:
+        assert b.get_launch() == (128, 0)
+        with pytest.raises(lbm.LbmError):
+            b.set_launch(64, 0)
+        b.step(steps)  # a graph of 32 + 13 launches (both parities)
+        b.sync()
+        for d in range(len(cfgs)):
+            assert np.array_equal(b.get_populations(d).cpu().numpy(), want[d]), d
+
+
+def test_inplace_batch_step_each_tune_and_memory(lbm):
+    cfgs, media = ensemble.ensemble(lbm, n=5, seed=11, lo=16, hi=200)
+    with ensemble.build(lbm, cfgs, media) as ab:
+        bytes_ab = ab.info()["bytes"]
+    cfgs = _inplace(lbm, cfgs)
+    with ensemble.build(lbm, cfgs, media) as a, ensemble.build(lbm, cfgs, media) as b:
+        nt, k, ms = a.tune(steps=3)
+        assert (nt, k) == (128, 0) and ms > 0
+        a.step(41)
+        b.step_each(41)
+        for d in range(len(cfgs)):
+            assert np.array_equal(a.get_populations(d).cpu().numpy(), b.get_populations(d).cpu().numpy())
+        assert a.info()["bytes"] < 0.75 * bytes_ab  # one population pool instead of two (media stay)
+    mixed = list(cfgs)
+    mixed[1].streaming = lbm.STREAM_AB
+    with pytest.raises(lbm.LbmError):
+        ensemble.build(lbm, mixed, media)

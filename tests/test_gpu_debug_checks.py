@@ -54,6 +54,15 @@ with workloads.build(lbm, cfgs, media) as b:
         b.set_launch(*shape)
         b.step(11)
         b.sync()
+for prec in (0, 1):
+    cfgs, media = workloads.ensemble(lbm, n=9, seed=3, lo=8, hi=300, precision=prec)
+    for c in cfgs:
+        c.streaming = lbm.STREAM_INPLACE
+    with workloads.build(lbm, cfgs, media) as b:
+        b.step(11)
+        b.step_each(3)
+        b.macros(4)
+        b.sync()
 cfg = lbm.default_config(nx=40, ny=17, bc_x=lbm.PRESSURE, bc_y=lbm.WALL, p_in=1.002, p_out=0.998, phi=0.4, K=4.0, p_rest=0.4)
 with lbm.Lattice(cfg) as lat:
     lat.set_medium(torch.full((17, 40), 0.4, device="cuda") + 0.05 * torch.rand(17, 40, device="cuda"), None)

@@ -266,8 +266,4 @@ def test_memory_and_rejections(lbm):
         with pytest.raises(lbm.LbmError) as e:
             lat.adjoint(4, "flux")
         assert e.value.code == lbm.ESTATE
-    cfg = Case(32, 16, streaming=IP).config(lbm)
-    with pytest.raises(lbm.LbmError) as e:
-        lbm.Batch([cfg])
-    assert e.value.code == lbm.EINVAL
     torch.cuda.synchronize()
