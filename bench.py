@@ -322,10 +322,15 @@ def ensemble_form(lbm, steps, local_rank):
 
     res = {}
     peak, _ = peaks()
-    for prec in ("fp32", "fp16"):
+    for key in ("fp32", "fp16", "fp32_inplace"):
+        prec = key.split("_")[0]
         cfgs, media = workloads.ensemble(lbm, n=512, seed=42, precision=PREC[prec])
+        if key.endswith("inplace"):  # one population pool updated in place
+            for c in cfgs:
+                c.streaming = lbm.STREAM_INPLACE
         b = workloads.build(lbm, cfgs, media)
         cells = b.info()["cells"]
+        device_bytes = b.info()["bytes"]
         nt, k, _ = b.tune(steps=4)
         b.step(32)
         b.sync()
@@ -347,10 +352,10 @@ def ensemble_form(lbm, steps, local_rank):
         b.close()
         bpl = BYTES_PER_LU[prec] + 8  # + per-cell eps and K
         mlups = cells * steps / (ms_b * 1e-3) / 1e6
-        res[prec] = {"batched_MLUPS": mlups, "one_by_one_MLUPS": cells * each / (ms_e * 1e-3) / 1e6,
-                     "batched_roofline_frac": mlups * 1e6 * bpl / 1e9 / peak, "algorithmic_bytes_per_lu": bpl,
-                     "launch": {"threads_per_cta": nt, "ctas_per_sm": k}, "steps": steps, "one_by_one_steps": each,
-                     "clocks": clk.summary()}
+        res[key] = {"batched_MLUPS": mlups, "one_by_one_MLUPS": cells * each / (ms_e * 1e-3) / 1e6,
+                    "batched_roofline_frac": mlups * 1e6 * bpl / 1e9 / peak, "algorithmic_bytes_per_lu": bpl,
+                    "launch": {"threads_per_cta": nt, "ctas_per_sm": k}, "steps": steps, "one_by_one_steps": each,
+                    "device_bytes": device_bytes, "clocks": clk.summary()}
         torch.cuda.empty_cache()
     return {"workload": "512 heterogeneous porous cavities/channels, sides U{64..1024}, Re U[10,400], seed 42",
             "cells": cells, **res}
