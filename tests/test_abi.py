@@ -55,6 +55,8 @@ def test_config_layout_matches(L):
         ("s_q", 2.5, -1),
         ("phi", 1.5, -1),
         ("dev_scale_log2", 99, -1),
+        ("streaming", 2, -1),
+        ("options", 2, -1),
     ],
 )
 def test_create_rejects_bad_configs_without_a_device(L, field, value, code):
@@ -66,6 +68,27 @@ def test_create_rejects_bad_configs_without_a_device(L, field, value, code):
     assert L.lbm_create(ctypes.byref(cfg), ctypes.byref(h)) == code
     assert not h.value
     assert L.lbm_last_error()
+
+
+@pytest.mark.parametrize("bc_x,bc_y", [(2, 1), (3, 1), (1, 3), (0, 3)])
+def test_inplace_streaming_rejects_extrapolated_sides_without_a_device(L, bc_x, bc_y):
+    """In-place streaming takes periodic and halfway-wall sides only: pressure columns and wall nodes
+    read a neighbour's state while it is overwritten."""
+    from paper_1311_7239_gb300 import lbm
+
+    cfg = lbm.default_config(bc_x=bc_x, bc_y=bc_y, streaming=lbm.STREAM_INPLACE)
+    h = ctypes.c_void_p()
+    assert L.lbm_create(ctypes.byref(cfg), ctypes.byref(h)) == lbm.EINVAL
+    assert not h.value and b"in-place" in L.lbm_last_error()
+
+
+def test_batch_rejects_mixed_streaming_without_a_device(L):
+    from paper_1311_7239_gb300 import lbm
+
+    cfgs = (lbm.Config * 2)(lbm.default_config(), lbm.default_config(streaming=lbm.STREAM_INPLACE))
+    h = ctypes.c_void_p()
+    assert L.lbm_batch_create(cfgs, 2, ctypes.byref(h)) == lbm.EINVAL
+    assert not h.value and b"streaming" in L.lbm_last_error()
 
 
 def test_strerror_names_every_code(L):
