@@ -386,3 +386,18 @@ def test_nee_wall_node_is_equilibrium_at_wall_velocity_for_equilibrium_neighbour
         assert np.allclose(g[:, y, x], want, atol=1e-13), (y, x)
     # interior untouched
     assert np.array_equal(g[:, 1:3, 1:4], f[:, 1:3, 1:4])
+
+
+def test_residual_hand_example_and_invariants():
+    """The steady-state residual ||u(t) - u(t-1)||_2 / ||u(t)||_2 on a two-cell example worked by
+    hand: u(t) = ((1, 2), (2, 0)), u(t-1) = ((1, 2), (1, 1)) differ by (0, 0) and (1, -1), so the
+    numerator is sqrt(2) and the denominator sqrt(1 + 4 + 4 + 0) = 3."""
+    ux_new, uy_new = np.array([1.0, 2.0]), np.array([2.0, 0.0])
+    ux_old, uy_old = np.array([1.0, 1.0]), np.array([2.0, 1.0])
+    assert abs(fl.residual(ux_new, uy_new, ux_old, uy_old) - np.sqrt(2.0) / 3.0) < 1e-15
+    # invariants: zero for an unchanged field, unchanged by a common scale, zero for a zero field
+    rng = np.random.default_rng(1)
+    a, b, c, d = rng.standard_normal((4, 5, 7))
+    assert fl.residual(a, b, a, b) == 0.0
+    assert abs(fl.residual(3 * a, 3 * b, 3 * c, 3 * d) - fl.residual(a, b, c, d)) < 1e-14
+    assert fl.residual(0 * a, 0 * b, c, d) == 0.0
