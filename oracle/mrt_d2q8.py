@@ -12,7 +12,7 @@ One time step follows the paper's order (Eq. 6 split as Eqs. 14-15):
     f(x, t)  --m = M f (Eq. 8)-->  u (Eqs. 17-19), p (Eq. 20), F (Eq. 3), S (Eq. 16), m_eq (Eqs. 11-12)
              --collide (Eq. 14)-->  m+  --f+ = M^-1 m+ (Eq. 15)-->  stream (Eq. 15)  -->  f(x, t+1)
 
-Readings of the paper used here (each one is listed with its reason in the design doc):
+Readings of the paper used here, where it is silent or ambiguous:
   * The third and fifth equilibrium moments j_x, j_y of Eq. 11 are rho0*u_x, rho0*u_y (the
     incompressible approximation J ~ rho0 u stated after Eq. 12, confirmed by Eq. A.3, whose
     first-order j_x is -rho0 F_x / 2).

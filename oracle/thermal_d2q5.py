@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``); shares no code with the C
 
 Populations g have shape (5, ny, nx), index 0..4 = the paper's i = 0..4 (Eq. B.3).
 
-Coupled step (readings listed in the design doc): from the pre-collision f(t), g(t):
+Coupled step (the coupling order is not printed in the paper; this is the reading used):
     T = sum_i g_i (Eq. B.5, n_0)  ->  a = g beta (T - T0) j (Sec. 3.4)
     flow collision with that a (Eqs. 14-20)  ->  u(t)
     temperature collision with u(t) (Eq. B.2 with n_eq of Eq. B.6)

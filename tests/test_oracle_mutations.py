@@ -27,6 +27,8 @@ THERMAL_PINS = [
     tpins.test_collision_keeps_T_and_relaxes_flux_to_uT,
     tpins.test_conduction_between_isothermal_walls_is_linear_and_nu_is_one,
     tpins.test_advected_sine_mode_decays_and_moves_as_eqB1,
+    tpins.test_stably_stratified_rest_state_is_hydrostatic_with_upward_buoyancy,
+    tpins.test_side_heated_cavity_rises_at_the_hot_wall,
 ]
 
 
@@ -139,7 +141,18 @@ def _mut_thermal_rate(monkeypatch):
     monkeypatch.setattr(th.Thermal, "rates", lambda self: orig(self)[[0, 3, 3, 3, 4]])
 
 
-@pytest.mark.parametrize("mutation", [_mut_thermal_flux, _mut_thermal_antibb, _mut_thermal_rate])
+def _mut_buoyancy_sign(monkeypatch):
+    """a = -g beta (T - T0) j: gravity taken along +y."""
+    from dataclasses import replace
+
+    def wrong(flow, p, T):
+        ax0, ay0 = fl._accel(flow, T)
+        return replace(flow, accel=np.stack([ax0 + 0.0 * T, ay0 - p.g_beta * (T - p.T0)]))
+
+    monkeypatch.setattr(th, "_buoyant", wrong)
+
+
+@pytest.mark.parametrize("mutation", [_mut_thermal_flux, _mut_thermal_antibb, _mut_thermal_rate, _mut_buoyancy_sign])
 def test_thermal_pins_catch_planted_mistake(monkeypatch, mutation):
     mutation(monkeypatch)
     with np.errstate(all="ignore"):

@@ -98,9 +98,14 @@ def test_eq26_parameters_of_the_table1_case():
     assert abs(g_beta * 20.0 * 2048**3 * 1.0 / nu**2 - 1e5) < 1e-6 * 1e5
 
 
-def test_buoyancy_drives_no_flow_in_stably_stratified_rest_state():
-    """A hot-over-cold linear T profile between isothermal top/bottom walls with phi p in
-    hydrostatic balance stays at rest: the coupling adds phi a to F exactly where grad(phi p) balances it."""
+def test_stably_stratified_rest_state_is_hydrostatic_with_upward_buoyancy():
+    """A hot-over-cold linear T profile between isothermal top/bottom walls stays at rest, and its
+    pressure is hydrostatic with the buoyancy a = g beta (T - T0) pointing up (+y, Sec. 3.4).
+
+    At rest Eq. 2 reduces to grad(phi p) = rho0 phi a, so with uniform phi and rho0 = 1
+    dp/dy = g beta (T - T0); T is linear in y, so p is quadratic and the difference of two adjacent
+    cells equals g beta (T_mid - T0) exactly, T_mid the mean of the two cells' temperatures.
+    A buoyancy pointing down (-y) reverses the sign of every difference."""
     nx, ny = 4, 16
     flow = fl.Flow(nx=nx, ny=ny, phi=np.full((ny, nx), 0.6), K=np.full((ny, nx), 0.01 * ny * ny), nu=0.1, bc_x="periodic", bc_y="wall")
     p = th.Thermal(tau_T=0.8, g_beta=1e-4, T0=11.0, T_bottom=1.0, T_top=21.0)
@@ -113,6 +118,31 @@ def test_buoyancy_drives_no_flow_in_stably_stratified_rest_state():
     y = np.arange(ny) + 0.5
     assert np.allclose(T[:, 0], 1.0 + 20.0 * y / ny, atol=1e-8)
     assert np.abs(ux).max() < 1e-12 and np.abs(uy).max() < 1e-10
+    dp = np.diff(pr, axis=0)
+    expect = p.g_beta * (0.5 * (T[1:] + T[:-1]) - p.T0)
+    assert np.abs(dp - expect).max() < 1e-10 * np.abs(expect).max()
+
+
+def test_side_heated_cavity_rises_at_the_hot_wall():
+    """Hot left wall, cold right wall, adiabatic bottom/top (the Table 1 cavity, Sec. 3.4) at
+    Ra = 1e4, Da = 1e-2: warm fluid rises along the hot wall and sinks along the cold one, so the
+    cavity turns clockwise (u_x > 0 under the top wall, u_x < 0 over the bottom wall).  Hot-wall
+    Nusselt numbers cannot see the direction of a (a y-mirror leaves them unchanged); this does."""
+    L = 24
+    nu, _, tau_T, g_beta = th.parameters_from_Ra(L, 1e4, 1.0, 0.1)
+    flow = fl.Flow(nx=L, ny=L, phi=np.full((L, L), 0.6), K=np.full((L, L), 1e-2 * L * L), nu=nu, bc_x="wall",
+                   bc_y="wall")
+    p = th.Thermal(tau_T=tau_T, g_beta=g_beta, T0=11.0, T_left=21.0, T_right=1.0)
+    f = fl.initial_state(flow)
+    g = th.initial_state(flow, p)
+    for _ in range(1000):
+        f, g = th.coupled_step(f, g, flow, p)
+    ux, uy, _, T = th.coupled_macroscopic(f, g, flow, p)
+    scale = np.sqrt(g_beta * 20.0 * L)  # the buoyancy velocity U of Eq. 26; the Darcy drag holds u near 0.016 U
+    assert uy[:, 0].mean() > 0.005 * scale and uy[:, -1].mean() < -0.005 * scale
+    assert ux[-1].mean() > 0.005 * scale and ux[0].mean() < -0.005 * scale
+    # the hot wall side is the warmer half at mid height: the field is not mirrored either
+    assert T[L // 2, : L // 2].mean() > T[L // 2, L // 2 :].mean()
 
 
 def test_conduction_between_extrapolated_wall_nodes_is_linear_and_nu_is_one():
