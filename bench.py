@@ -215,13 +215,33 @@ def timed_steps(lbm, L, prec, steps, warmup, local_rank, dist=None, streaming=0)
     return start.elapsed_time(stop), clk.summary(), lat
 
 
+TARGETS = {"fp32": 1e-5, "fp16": 1e-3, "bf16": 1e-3}  # relative L2 error against the FP64 oracle
+
+
 def accuracy_record():
-    """Relative L2 errors vs the FP64 oracle measured by the GPU parity tests (committed record)."""
+    """Relative L2 errors vs the FP64 oracle measured by the GPU parity tests (committed record),
+    with a per-precision summary: the target, the worst recorded field error and whether it is met
+    (BF16 storage misses its 1e-3 target; its runs are recorded, not counted as parity)."""
     try:
         with open(os.path.join(ROOT, "profiles", "accuracy.json")) as fh:
-            return json.load(fh)
+            rec = json.load(fh)
     except Exception:
         return None
+    summary = {}
+    for c in rec.get("cases", []):
+        prec = c.get("precision")
+        if prec not in TARGETS:
+            continue
+        errs = [v for k, v in c.items() if k.startswith("rel_l2") and isinstance(v, float)]
+        if not errs:
+            continue
+        s = summary.setdefault(prec, {"target": TARGETS[prec], "worst_rel_l2": 0.0, "cases": 0})
+        s["worst_rel_l2"] = max(s["worst_rel_l2"], max(errs))
+        s["cases"] += 1
+    for s in summary.values():
+        s["meets_target"] = s["worst_rel_l2"] <= s["target"]
+    rec["by_precision"] = summary
+    return rec
 
 
 def inplace_form(lbm, L, steps, warmup, local_rank):

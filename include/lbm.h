@@ -195,6 +195,8 @@ LBM_API int lbm_residual(lbm_ctx* ctx, double* r);
  * two velocity fields the caller holds instead of from a context.
  *   ux, uy, ux_prev, uy_prev: device float32 arrays of n cells (any layout, the same for all four);
  *   r: device or host double receiving ||u - u_prev||_2 / ||u||_2 (sums in FP64; 0 if u = 0);
+ *      managed memory counts as device memory: r is then written asynchronously on the stream,
+ *      and the caller synchronises the stream before reading it on the host;
  *   stream: cudaStream_t to run on (NULL = the default stream).
  * Limits: 1 <= n <= 67108864 (2^26, an 8192 x 8192 lattice); larger n is EINVAL.  The partial
  * sums use a fixed 64 KB array in device memory that liblbm.so reserves on every GPU that loads

@@ -24,9 +24,21 @@ def accuracy():
     return _ACCURACY
 
 
+def _with_target(case):
+    """The entry with its accuracy target (the stated bound, or the target a bounded-only run
+    misses) and whether every recorded error meets it."""
+    c = dict(case)
+    target = c.get("target", c.get("bound"))
+    errs = [v for k, v in c.items() if k.startswith(("rel_", "max_rel_")) and isinstance(v, float)]
+    if target is not None and errs:
+        c["target"] = target
+        c["meets_target"] = bool(max(errs) <= target)
+    return c
+
+
 def pytest_sessionfinish(session, exitstatus):
     out = os.environ.get("LBM_ACCURACY_OUT")
     if out and _ACCURACY:
         with open(out, "w") as fh:
             json.dump({"source": "python -m pytest tests -m gpu (FP64 oracle vs liblbm.so on the same seeded inputs)",
-                       "cases": _ACCURACY}, fh, indent=1)
+                       "cases": [_with_target(c) for c in _ACCURACY]}, fh, indent=1)

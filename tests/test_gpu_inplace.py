@@ -113,14 +113,28 @@ def test_heterogeneous_channel_trajectory(lbm, accuracy):
     assert e_u <= 1e-5 and e_p <= 1e-5, (e_u, e_p)
 
 
-@pytest.mark.parametrize("prec,bound", [(1, 1e-3), (2, 1e-2)])
-def test_reduced_precision_cavity(lbm, accuracy, prec, bound):
+def _reduced_precision_cavity(lbm, prec):
     L = 96
     case = Case(L, L, nu=0.1 * L / 100, phi=0.4, K=1e-3 * L * L, bc_x="wall", bc_y="wall", walls=CAV, precision=prec, streaming=IP)
-    e_u, e_p = _trajectory(lbm, case, 800)
+    return _trajectory(lbm, case, 800)
+
+
+def test_reduced_precision_cavity(lbm, accuracy):
+    """FP16 storage with in-place streaming, within the 1e-3 target."""
+    e_u, e_p = _reduced_precision_cavity(lbm, 1)
     accuracy.append({"case": "lid-driven porous cavity 96x96, eps 0.4, Da 1e-3, Re 100, in-place streaming",
-                     "precision": {1: "fp16", 2: "bf16"}[prec], "steps": 800, "rel_l2_u": e_u, "rel_l2_p": e_p, "bound": bound})
-    assert e_u <= bound and e_p <= bound, (e_u, e_p)
+                     "precision": "fp16", "steps": 800, "rel_l2_u": e_u, "rel_l2_p": e_p, "bound": 1e-3})
+    assert e_u <= 1e-3 and e_p <= 1e-3, (e_u, e_p)
+
+
+def test_bf16_cavity_error_bounded_target_missed(lbm, accuracy):
+    """BF16 storage with in-place streaming: its 8-bit significand misses the 1e-3 target (about
+    6e-3 here, as with A-B streaming); not a parity pass, regression bound 1e-2."""
+    e_u, e_p = _reduced_precision_cavity(lbm, 2)
+    accuracy.append({"case": "lid-driven porous cavity 96x96, eps 0.4, Da 1e-3, Re 100, in-place streaming",
+                     "precision": "bf16", "steps": 800, "rel_l2_u": e_u, "rel_l2_p": e_p, "target": 1e-3,
+                     "regression_bound": 1e-2})
+    assert e_u <= 1e-2 and e_p <= 1e-2, (e_u, e_p)
 
 
 def _thermal_case(prec=0, L=48, Ra=1e4):

@@ -212,31 +212,61 @@ def test_host_pointers_round_trip(lbm):
     assert np.array_equal(ux_h, ux_d) and np.array_equal(p_h, p_d)
 
 
-@pytest.mark.parametrize("prec,bound", [(1, 1e-3), (2, 1e-2)])
-def test_reduced_precision_storage_error(lbm, accuracy, prec, bound):
-    """FP16 / BF16 storage of f - f_rest with FP32 arithmetic: relative L2 error of u and p vs the
-    FP64 oracle on the lid-driven cavity (bound 1e-3 for FP16; BF16's 8-bit mantissa is reported
-    against a looser 1e-2)."""
+# BF16 keeps 8 significant bits: its measured errors against the FP64 oracle (6.6e-3 on the 96^2
+# cavity, 1.0e-2 on 600 x 64, a few percent on the thermal transient) miss the 1e-3 that FP16 meets.
+# The BF16 runs below are therefore not parity passes: they record the error with the 1e-3 target
+# and meets_target = false, and assert only a regression bound (about 1.5x the measured error).
+BF16_TARGET = 1e-3
+
+
+def _cavity_storage_error(lbm, prec):
     L = 96
     case = Case(L, L, nu=0.1 * L / 100, phi=0.4, K=1e-3 * L * L, bc_x="wall", bc_y="wall", walls=CAV, precision=prec)
-    e_u, e_p = _trajectory(lbm, case, 800)
-    print(f"precision {prec}: rel-L2 u {e_u:.3e}, p {e_p:.3e}")
-    accuracy.append({"case": "lid-driven porous cavity 96x96, eps 0.4, Da 1e-3, Re 100", "precision": {1: "fp16", 2: "bf16"}[prec],
-                     "steps": 800, "rel_l2_u": e_u, "rel_l2_p": e_p, "bound": bound})
-    assert e_u <= bound and e_p <= bound, (e_u, e_p)
+    return _trajectory(lbm, case, 800)
 
 
-@pytest.mark.parametrize("prec,bound", [(1, 1e-3), (2, 2e-2)])
-def test_reduced_precision_long_rows(lbm, accuracy, prec, bound):
-    """16-bit storage with rows longer than one work item: a 600 x 64 lid-driven cavity (two
-    512-cell items per row, the second ragged) against the oracle.  BF16's 8-bit significand
-    gives ~1e-2 here (1.0e-2 at 600 x 64, 9.6e-3 at 500 x 64)."""
+def test_reduced_precision_storage_error(lbm, accuracy):
+    """FP16 storage of f - f_rest with FP32 arithmetic: relative L2 error of u and p vs the FP64
+    oracle on the lid-driven cavity, within the 1e-3 target."""
+    e_u, e_p = _cavity_storage_error(lbm, 1)
+    print(f"fp16: rel-L2 u {e_u:.3e}, p {e_p:.3e}")
+    accuracy.append({"case": "lid-driven porous cavity 96x96, eps 0.4, Da 1e-3, Re 100", "precision": "fp16",
+                     "steps": 800, "rel_l2_u": e_u, "rel_l2_p": e_p, "bound": 1e-3})
+    assert e_u <= 1e-3 and e_p <= 1e-3, (e_u, e_p)
+
+
+def test_bf16_storage_error_bounded_target_missed(lbm, accuracy):
+    """BF16 storage on the same cavity: not a parity pass (see BF16_TARGET); regression bound 1e-2."""
+    e_u, e_p = _cavity_storage_error(lbm, 2)
+    print(f"bf16: rel-L2 u {e_u:.3e}, p {e_p:.3e} (target {BF16_TARGET:g} not met)")
+    accuracy.append({"case": "lid-driven porous cavity 96x96, eps 0.4, Da 1e-3, Re 100", "precision": "bf16",
+                     "steps": 800, "rel_l2_u": e_u, "rel_l2_p": e_p, "target": BF16_TARGET, "regression_bound": 1e-2})
+    assert e_u <= 1e-2 and e_p <= 1e-2, (e_u, e_p)
+
+
+def _long_rows_error(lbm, prec):
     case = Case(600, 64, nu=0.1 * 64 / 100, phi=0.4, K=1e-3 * 64 * 64, bc_x="wall", bc_y="wall", walls=CAV, precision=prec)
-    e_u, e_p = _trajectory(lbm, case, 400)
-    print(f"precision {prec}, 600x64: rel-L2 u {e_u:.3e}, p {e_p:.3e}")
-    accuracy.append({"case": "lid-driven porous cavity 600x64, eps 0.4, Da 1e-3", "precision": {1: "fp16", 2: "bf16"}[prec],
-                     "steps": 400, "rel_l2_u": e_u, "rel_l2_p": e_p, "bound": bound})
-    assert e_u <= bound and e_p <= bound, (e_u, e_p)
+    return _trajectory(lbm, case, 400)
+
+
+def test_reduced_precision_long_rows(lbm, accuracy):
+    """FP16 storage with rows longer than one work item: a 600 x 64 lid-driven cavity (two 512-cell
+    items per row, the second ragged) against the oracle, within the 1e-3 target."""
+    e_u, e_p = _long_rows_error(lbm, 1)
+    print(f"fp16, 600x64: rel-L2 u {e_u:.3e}, p {e_p:.3e}")
+    accuracy.append({"case": "lid-driven porous cavity 600x64, eps 0.4, Da 1e-3", "precision": "fp16",
+                     "steps": 400, "rel_l2_u": e_u, "rel_l2_p": e_p, "bound": 1e-3})
+    assert e_u <= 1e-3 and e_p <= 1e-3, (e_u, e_p)
+
+
+def test_bf16_long_rows_error_bounded_target_missed(lbm, accuracy):
+    """BF16 on the 600 x 64 cavity (1.0e-2 at 600 x 64, 9.6e-3 at 500 x 64): not a parity pass;
+    regression bound 2e-2."""
+    e_u, e_p = _long_rows_error(lbm, 2)
+    print(f"bf16, 600x64: rel-L2 u {e_u:.3e}, p {e_p:.3e} (target {BF16_TARGET:g} not met)")
+    accuracy.append({"case": "lid-driven porous cavity 600x64, eps 0.4, Da 1e-3", "precision": "bf16",
+                     "steps": 400, "rel_l2_u": e_u, "rel_l2_p": e_p, "target": BF16_TARGET, "regression_bound": 2e-2})
+    assert e_u <= 2e-2 and e_p <= 2e-2, (e_u, e_p)
 
 
 @pytest.mark.parametrize("bc", ["periodic", "nee"])
@@ -259,11 +289,7 @@ def test_reduced_precision_one_step_long_rows(lbm, prec, bc):
     assert np.abs(got - want).max() <= tol, np.abs(got - want).max()
 
 
-@pytest.mark.parametrize("prec,bound", [(1, 1e-3), (2, 5e-2)])
-def test_reduced_precision_thermal_error(lbm, accuracy, prec, bound):
-    """Natural convection with FP16 / BF16 storage.  BF16 keeps 8 significant bits (unit
-    roundoff 2^-9 ~ 2e-3 per stored value), which the slow thermal transient accumulates to a few
-    percent: it is reported against 5e-2, not the 1e-3 that FP16 meets."""
+def _thermal_storage_error(lbm, prec):
     case = _thermal_case(prec=prec)
     flow, tp = case.flow(), case.thermal_params()
     f, g = fl.initial_state(flow), th.initial_state(flow, tp)
@@ -274,12 +300,28 @@ def test_reduced_precision_thermal_error(lbm, accuracy, prec, bound):
     for _ in range(steps):
         f, g = th.coupled_step(f, g, flow, tp)
     uxo, uyo, po, To = th.coupled_macroscopic(f, g, flow, tp)
-    e_u = rel_l2(np.stack([ux, uy]), np.stack([uxo, uyo]))
-    e_T = rel_l2(T - 11.0, To - 11.0)
-    print(f"precision {prec}: rel-L2 u {e_u:.3e}, T-T0 {e_T:.3e}")
-    accuracy.append({"case": "natural convection 48x48, Ra 1e4, eps 0.6, Da 1e-2", "precision": {1: "fp16", 2: "bf16"}[prec],
-                     "steps": steps, "rel_l2_u": e_u, "rel_l2_T_minus_T0": e_T, "bound": bound})
-    assert e_u <= bound and e_T <= bound, (e_u, e_T)
+    return steps, rel_l2(np.stack([ux, uy]), np.stack([uxo, uyo])), rel_l2(T - 11.0, To - 11.0)
+
+
+def test_reduced_precision_thermal_error(lbm, accuracy):
+    """Natural convection with FP16 storage, within the 1e-3 target for u and T - T0."""
+    steps, e_u, e_T = _thermal_storage_error(lbm, 1)
+    print(f"fp16: rel-L2 u {e_u:.3e}, T-T0 {e_T:.3e}")
+    accuracy.append({"case": "natural convection 48x48, Ra 1e4, eps 0.6, Da 1e-2", "precision": "fp16",
+                     "steps": steps, "rel_l2_u": e_u, "rel_l2_T_minus_T0": e_T, "bound": 1e-3})
+    assert e_u <= 1e-3 and e_T <= 1e-3, (e_u, e_T)
+
+
+def test_bf16_thermal_error_bounded_target_missed(lbm, accuracy):
+    """Natural convection with BF16 storage: the 8-bit significand's rounding (2^-9 per stored
+    value) accumulates over the slow thermal transient to a few percent; not a parity pass,
+    regression bound 6e-2."""
+    steps, e_u, e_T = _thermal_storage_error(lbm, 2)
+    print(f"bf16: rel-L2 u {e_u:.3e}, T-T0 {e_T:.3e} (target {BF16_TARGET:g} not met)")
+    accuracy.append({"case": "natural convection 48x48, Ra 1e4, eps 0.6, Da 1e-2", "precision": "bf16",
+                     "steps": steps, "rel_l2_u": e_u, "rel_l2_T_minus_T0": e_T, "target": BF16_TARGET,
+                     "regression_bound": 6e-2})
+    assert e_u <= 6e-2 and e_T <= 6e-2, (e_u, e_T)
 
 
 def test_graph_replay_equals_single_launches(lbm):
