@@ -128,57 +128,95 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def cpu_baseline(L, seconds=12.0, size=256):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload (a size x size cavity
-    with the same parameters), on this host's cores."""
+def _oracle_job(job):
+    """One oracle process: (L, side, warmup, steps, seconds) -> (cell updates, seconds, steps) of the
+    FP64 oracle on a side x side sample of the L x L cavity; `steps` steps, or as many as fit in
+    `seconds` when steps is 0."""
     import numpy as np
 
     from oracle import mrt_d2q8 as fl
 
+    L, side, warmup, steps, seconds = job
     prm = cavity_params(L)
-    flow = fl.Flow(nx=size, ny=size, phi=np.full((size, size), prm["phi"]), K=np.full((size, size), prm["K"]),
+    flow = fl.Flow(nx=side, ny=side, phi=np.full((side, side), prm["phi"]), K=np.full((side, side), prm["K"]),
                    nu=prm["nu"], bc_x="wall", bc_y="wall", u_top=(prm["lid"], 0.0))
     f = fl.initial_state(flow)
-    f = fl.step(f, flow)
+    for _ in range(max(warmup, 1)):
+        f = fl.step(f, flow)
     n = 0
     t0 = time.perf_counter()
-    while time.perf_counter() - t0 < seconds:
+    while (n < steps) if steps else (time.perf_counter() - t0 < seconds):
         f = fl.step(f, flow)
         n += 1
-    dt = time.perf_counter() - t0
-    return {"value": size * size * n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"{size}x{size} lid-driven porous cavity with the workload's eps, Da, nu, lid; {n} steps of the numpy FP64 oracle, single thread"}
+    return side * side * n, time.perf_counter() - t0, n
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_pool(jobs):
+    """Run oracle jobs in fresh single-threaded processes (spawned, so safe after CUDA is up), one
+    process per job, all at once."""
+    import multiprocessing as mp
+
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(len(jobs)) as pool:
+            return pool.map(_oracle_job, jobs)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def cpu_baseline(L, seconds=6.0):
+    """The FP64 oracle, as it stands, on bounded samples of the workload (square cavities with the
+    workload's parameters) on this host's cores: one single-threaded process per core on its own
+    512^2 sample (the aggregate is the value), and one process alone at 512^2, 1024^2 and 2048^2."""
+    cores = host_cores()
+    allc = oracle_pool([(L, 512, 1, 0, seconds)] * cores)
+    total = sum(c for c, _, _ in allc) / max(t for _, t, _ in allc) / 1e6
+    single = {}
+    for side in (512, 1024, 2048):
+        c, t, n = oracle_pool([(L, side, 1, 0, seconds)])[0]
+        single[f"{side}x{side}"] = {"MLUPS": c / t / 1e6, "steps": n}
+    return {"value": total, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{cores} single-threaded processes of the numpy FP64 oracle, each on its own 512x512 lid-driven "
+                      f"porous cavity with the workload's eps, Da, nu, lid, for about {seconds:g} s; value = cells x steps "
+                      f"of all processes / the longest process time",
+            "host_nproc": os.cpu_count(), "single_core": single}
 
 
 def run_reference(args, rank, world):
-    """The oracle as it stands on this host: W untimed and K timed steps of a square sample of
-    the workload, the sample side chosen so that the K steps take about a minute at most."""
+    """The oracle as it stands on this host's cores: one single-threaded process per core, each
+    running W untimed and K timed steps of its own square sample of the workload, the sample side
+    chosen so that the K steps take about a minute at most; value = all processes' cell updates /
+    the longest process time."""
     if rank != 0:
         return 0
-    import numpy as np
-
-    from oracle import mrt_d2q8 as fl
-
     L = args.size
-    side = int(max(16, min(256, math.sqrt(60.0 / (max(args.steps, 1) * 2.5e-7)))))
-    prm = cavity_params(L)
-    flow = fl.Flow(nx=side, ny=side, phi=np.full((side, side), prm["phi"]), K=np.full((side, side), prm["K"]), nu=prm["nu"],
-                   bc_x="wall", bc_y="wall", u_top=(prm["lid"], 0.0))
-    f = fl.initial_state(flow)
-    for _ in range(args.warmup):
-        f = fl.step(f, flow)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        f = fl.step(f, flow)
-    dt = time.perf_counter() - t0
-    mlups = side * side * args.steps / dt / 1e6
-    b = {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-         "sample": f"{side}x{side} lid-driven porous cavity with the workload's eps, Da, nu, lid; numpy FP64 oracle, single thread"}
+    cores = host_cores()
+    side = int(max(16, min(256, math.sqrt(60.0 / (max(args.steps, 1) * 1e-6)))))
+    res = oracle_pool([(L, side, args.warmup, args.steps, 0.0)] * cores)
+    dt = max(t for _, t, _ in res)
+    mlups = sum(c for c, _, _ in res) / dt / 1e6
+    b = {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+         "sample": f"{cores} single-threaded processes of the numpy FP64 oracle, each on its own {side}x{side} lid-driven "
+                   f"porous cavity with the workload's eps, Da, nu, lid"}
     line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(args.steps, 1), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"lid-driven porous cavity {L}x{L} (each step sampled on {side}x{side}), eps=0.4, Da=1e-3, "
-                                   f"Re=100, lid=0.1", "nx": L, "ny": L},
+            "config": {"workload": f"lid-driven porous cavity {L}x{L} (each step sampled on {cores} x {side}x{side}), eps=0.4, "
+                                   f"Da=1e-3, Re=100, lid=0.1", "nx": L, "ny": L},
             "cpu_baseline": b, "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -462,6 +500,24 @@ def run_gpu(args, rank, world, local_rank):
     e2e_s = time.perf_counter() - t0
     lat.sync()
     e2e_mlups = cells * e2e_steps * world / e2e_s / 1e6
+    # the same loop with the fields a user reads: p, ux, uy of the whole lattice to pinned host
+    # memory through lbm_macros every `every` steps
+    every = 100
+    fields = [torch.empty(L, L, dtype=torch.float32).pin_memory() for _ in range(3)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        lat.set_walls(walls)
+        lat.step(1)
+        lat.probe(L // 2, L // 2, probe)
+        if (k + 1) % every == 0:
+            lat.macros(*fields)
+    lat.sync()
+    e2e_f_s = time.perf_counter() - t0
+    e2e_fields = {"value": cells * e2e_steps * world / e2e_f_s / 1e6, "unit": "MLUPS", "every_steps": every,
+                  "d2h_bytes_per_readout": int(sum(t.numel() for t in fields) * 4), "steps": e2e_steps,
+                  "call": "as e2e, plus lbm_macros(p, ux, uy to pinned host memory) every 100 steps"}
+    del fields
     lat.close()
 
     peak, peak_kind = peaks()
@@ -497,7 +553,7 @@ def run_gpu(args, rank, world, local_rank):
         "gpu_launches": args.steps,
         "e2e": {"value": e2e_mlups, "unit": "MLUPS", "h2d_bytes_per_step": int(walls.numel() * 4),
                 "d2h_bytes_per_step": int(probe.numel() * 4), "steps": e2e_steps,
-                "call": "lbm_set_walls(host) + lbm_step(1) + lbm_probe(host) per step"},
+                "call": "lbm_set_walls(host) + lbm_step(1) + lbm_probe(host) per step", "with_field_readout": e2e_fields},
         "clocks": clocks,
     }
     if not args.no_forms:
@@ -532,8 +588,8 @@ def run_case(args, local_rank):
         L, _, _ = lat.adjoint(64, "flux")
         lat.close()
         print(json.dumps({"case": "adjoint", "loss": L}))
-    elif args.case == "batch":  # 64 lattices of the ensemble, FP32, one 64-thread CTA per work item
-        cfgs, media = workloads.ensemble(lbm, n=64, seed=42)
+    elif args.case == "batch":  # 64 lattices of the ensemble (--precision), one 64-thread CTA per work item
+        cfgs, media = workloads.ensemble(lbm, n=64, seed=42, precision=PREC[args.precision])
         b = workloads.build(lbm, cfgs, media)
         b.set_launch(64, 0)
         b.step(8)
@@ -560,13 +616,13 @@ def run_case(args, local_rank):
         print(json.dumps({"case": "nusselt", "L": L, "precision": args.precision, "steps": steps, "Nu_left": nl, "Nu_right": nr,
                           "table1_present": 3.451, "rel_diff": abs(nl - 3.451) / 3.451, "seconds": time.perf_counter() - t0,
                           "history": hist[-5:]}))
-    elif args.case in ("fp16", "thermal", "inplace"):  # 2048^2 cavity FP16 storage / natural convection FP32 /
+    elif args.case in ("fp16", "thermal", "inplace"):  # 2048^2 cavity FP16 storage / natural convection (--precision) /
         stream = torch.cuda.Stream()                     # cavity with in-place streaming (--precision)
         if args.case in ("fp16", "inplace"):
             cfg = make_lattice(lbm, 2048, "fp16" if args.case == "fp16" else args.precision, stream,
                                1 if args.case == "inplace" else 0).cfg
         else:
-            cfg = workloads.natural_convection(lbm, L=2048)
+            cfg = workloads.natural_convection(lbm, L=2048, precision=PREC[args.precision])
             cfg.stream = stream.cuda_stream
         lat = lbm.Lattice(cfg)
         lat.step(10)

@@ -272,8 +272,20 @@ LBM_API int lbm_batch_step_each(lbm_batch* b, int n);
  * In-place batches take (128, 0) only (EINVAL otherwise). */
 LBM_API int lbm_batch_set_launch(lbm_batch* b, int threads_per_cta, int ctas_per_sm);
 LBM_API int lbm_batch_get_launch(const lbm_batch* b, int* threads_per_cta, int* ctas_per_sm);
-/* Time `steps` steps for every launch shape on a copy of the current state, keep the fastest,
- * restore the state; outputs may be NULL.  Waits for the stream. */
+/* Tiling of each lattice into work items of one CTA (A-B batches; in-place batches keep their own
+ * tiling and accept LBM_TILING_FLAT only, EINVAL otherwise):
+ *   LBM_TILING_ROWS  rows of work items: a row of G four-cell groups takes ceil(G / threads) items,
+ *                    or several short rows share one;
+ *   LBM_TILING_FLAT  the lattice's groups in row-major order, `threads` consecutive groups per item
+ *                    (an item may end one row and start the next; only the last item is ragged).
+ * The default is LBM_TILING_FLAT.  The work-item tables are rebuilt for the current launch shape. */
+#define LBM_TILING_ROWS 0
+#define LBM_TILING_FLAT 1
+LBM_API int lbm_batch_set_tiling(lbm_batch* b, int tiling);
+LBM_API int lbm_batch_get_tiling(const lbm_batch* b, int* tiling);
+/* Time `steps` steps for every launch shape and tiling on a copy of the current state, keep the
+ * fastest, restore the state; outputs may be NULL (the chosen tiling: lbm_batch_get_tiling).
+ * Waits for the stream. */
 LBM_API int lbm_batch_tune(lbm_batch* b, int steps, int* threads_per_cta, int* ctas_per_sm, float* ms_per_step);
 /* Read-outs of lattice d (float32 [ny_d][nx_d] / [8][ny_d][nx_d], host or device). */
 LBM_API int lbm_batch_macros(lbm_batch* b, int d, float* p, float* ux, float* uy);

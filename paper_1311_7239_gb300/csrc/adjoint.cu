@@ -30,15 +30,25 @@ struct VelBar {
   float jx, jy, clin, cnl, phi;
 };
 
-__device__ __forceinline__ VelBar velocity_vjp(float jx, float jy, const Coef& c, float ax, float ay, float inv_rho0, float ubx,
-                                               float uby, float umb) {
-  const float vx = jx * inv_rho0 + 0.5f * c.phi * ax;
-  const float vy = jy * inv_rho0 + 0.5f * c.phi * ay;
-  const float l0 = 0.5f + 0.25f * c.c_lin;
-  const float l1 = 0.5f * c.c_nl;
-  const float vmag = fast_sqrt(vx * vx + vy * vy);
-  const float sR = fast_sqrt(l0 * l0 + l1 * vmag);
-  const float inv = fast_rcp(l0 + sR);
+// Forward quantities of Eqs. 18-19 kept for the reverse pass (velocity_from_j's intermediates).
+struct VelFwd {
+  float vx, vy, vmag, sR, inv, l0, l1;
+};
+
+__device__ __forceinline__ VelFwd velocity_fwd(float jx, float jy, const Coef& c, float ax, float ay, float inv_rho0) {
+  VelFwd f;
+  f.vx = jx * inv_rho0 + 0.5f * c.phi * ax;
+  f.vy = jy * inv_rho0 + 0.5f * c.phi * ay;
+  f.l0 = 0.5f + 0.25f * c.c_lin;
+  f.l1 = 0.5f * c.c_nl;
+  f.vmag = fast_sqrt(f.vx * f.vx + f.vy * f.vy);
+  f.sR = fast_sqrt(f.l0 * f.l0 + f.l1 * f.vmag);
+  f.inv = fast_rcp(f.l0 + f.sR);
+  return f;
+}
+
+__device__ __forceinline__ VelBar velocity_vjp(const VelFwd& f, float inv_rho0, float ax, float ay, float ubx, float uby, float umb) {
+  const float vx = f.vx, vy = f.vy, vmag = f.vmag, sR = f.sR, inv = f.inv, l0 = f.l0, l1 = f.l1;
   float vbx = ubx * inv, vby = uby * inv;
   float inv_bar = ubx * vx + uby * vy + umb * vmag;
   float vmag_bar = umb * inv;
@@ -61,6 +71,11 @@ __device__ __forceinline__ VelBar velocity_vjp(float jx, float jy, const Coef& c
   return o;
 }
 
+__device__ __forceinline__ VelBar velocity_vjp(float jx, float jy, const Coef& c, float ax, float ay, float inv_rho0, float ubx,
+                                               float uby, float umb) {
+  return velocity_vjp(velocity_fwd(jx, jy, c, ax, ay, inv_rho0), inv_rho0, ax, ay, ubx, uby, umb);
+}
+
 // theta-gradients from the adjoints of c_lin, c_nl, 1/phi and phi itself.
 __device__ __forceinline__ void theta_bar(const Coef& c, float clin_bar, float cnl_bar, float iphi_bar, float phi_bar, float& g_l,
                                           float& g_phi) {
@@ -79,8 +94,9 @@ __device__ void collide_vjp(const float z[8], const Coef& c, float ax, float ay,
   const float t57 = z[4] - z[6], t68 = z[5] - z[7];
   const float m1 = a13 + a24 + s57 + s68;
   const float m3 = d13 + (t57 - t68), m5 = d24 + (t57 + t68);
-  float ux, uy, umag;
-  velocity_from_j(m3, m5, c, ax, ay, P.inv_rho0, ux, uy, umag);
+  // u = v / (l0 + sqrt(l0^2 + l1 |v|)) (Eqs. 18-19), its intermediates kept for the reverse pass
+  const VelFwd vf = velocity_fwd(m3, m5, c, ax, ay, P.inv_rho0);
+  const float ux = vf.vx * vf.inv, uy = vf.vy * vf.inv, umag = vf.vmag * vf.inv;
   const float usq = ux * ux + uy * uy;
   const float drag = c.c_lin + c.c_nl * umag;
   const float Fx = -drag * ux + c.phi * ax;
@@ -143,7 +159,7 @@ __device__ void collide_vjp(const float z[8], const Coef& c, float ax, float ay,
   const float umag_b = c.c_nl * drag_b;
   phib += ax * Fbx + ay * Fby;
   // u, |u| from j (Eqs. 18-19)
-  const VelBar vb = velocity_vjp(m3, m5, c, ax, ay, P.inv_rho0, ubx, uby, umag_b);
+  const VelBar vb = velocity_vjp(vf, P.inv_rho0, ax, ay, ubx, uby, umag_b);
   mb3 += vb.jx;
   mb5 += vb.jy;
   clin_b += vb.clin;

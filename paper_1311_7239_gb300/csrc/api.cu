@@ -113,6 +113,9 @@ void params_from_config(const lbm_config& k, int prec, int pitch, int64_t plane,
   q.u_cf8 = (float)(0.25 * hv * rs / k.phi);
   q.u_hx = (float)(0.5 * k.phi * k.ax);
   q.u_hy = (float)(0.5 * k.phi * k.ay);
+  q.k_c2 = (float)(0.1 * (1.0 - 0.5 * k.s_e) * rs);
+  q.k_rs = (float)rs;
+  q.hax = (float)(0.5 * k.ax);
 }
 
 }  // namespace lbm

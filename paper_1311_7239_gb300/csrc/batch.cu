@@ -61,6 +61,7 @@ struct lbm_batch {
   int64_t item_lattice_cap = 0;
   int64_t total_items = 0;
   int nt = 128, ctas_per_sm = 4, grid = 0, sms = 0;
+  int flat = 1;  // tiling of the A-B batched kernel (LBM_TILING_FLAT / LBM_TILING_ROWS)
   int cur = 0;
   int64_t steps = 0;
   int64_t cells = 0;
@@ -121,7 +122,8 @@ int set_launch(lbm_batch* b, int nt, int ctas_per_sm) {
   for (int d = 0; d < b->n; ++d) {
     start[d] = total;
     const lbm_config& c = b->cfg[d];
-    total += b->inplace ? inplace_items((int)c.nx, (int)c.ny, (int)c.bc_x, (int)c.bc_y) : batch_items((int)c.nx, (int)c.ny, (int)c.bc_y, nt);
+    total += b->inplace ? inplace_items((int)c.nx, (int)c.ny, (int)c.bc_x, (int)c.bc_y)
+                        : batch_items((int)c.nx, (int)c.ny, (int)c.bc_y, nt, b->flat);
   }
   LBM_BCUDA(cudaMemcpy(b->item_start, start.data(), b->n * sizeof(int64_t), cudaMemcpyHostToDevice), "copy of the item table");
   b->total_items = total;
@@ -164,7 +166,7 @@ int launch_once(lbm_batch* b, int cur, cudaStream_t s) {
     return LBM_OK;
   }
   LBM_BCUDA(launch_step_batch(b->dp[cur], b->item_start, b->ctas_per_sm == 0 ? b->item_lattice : nullptr, b->n, b->total_items, b->prec,
-                              b->nt, b->grid, s),
+                              b->nt, b->grid, b->flat, s),
             "batched step kernel");
   return LBM_OK;
 }
@@ -177,7 +179,7 @@ int capture(lbm_batch* b, int cur) {
     le = b->inplace ? launch_step_batch_inplace(b->dp[cur ^ (k & 1)], b->item_start, b->item_lattice, b->total_items, b->prec,
                                                 cur ^ (k & 1), b->capture_stream)
                     : launch_step_batch(b->dp[cur ^ (k & 1)], b->item_start, b->ctas_per_sm == 0 ? b->item_lattice : nullptr, b->n,
-                                        b->total_items, b->prec, b->nt, b->grid, b->capture_stream);
+                                        b->total_items, b->prec, b->nt, b->grid, b->flat, b->capture_stream);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(b->capture_stream, &g);
   if (le != cudaSuccess || e != cudaSuccess) {
@@ -452,6 +454,24 @@ int lbm_batch_get_launch(const lbm_batch* b, int* threads_per_cta, int* ctas_per
   return LBM_OK;
 }
 
+int lbm_batch_set_tiling(lbm_batch* b, int tiling) {
+  if (!b) return fail_msg(LBM_EINVAL, "null batch");
+  if (tiling != LBM_TILING_ROWS && tiling != LBM_TILING_FLAT) return fail_msg(LBM_EINVAL, "tiling must be LBM_TILING_ROWS or LBM_TILING_FLAT");
+  if (b->inplace && tiling != LBM_TILING_FLAT) return fail_msg(LBM_EINVAL, "in-place batches keep their own tiling (LBM_TILING_FLAT)");
+  if (b->inplace) return LBM_OK;
+  const int old = b->flat;
+  b->flat = tiling == LBM_TILING_FLAT ? 1 : 0;
+  const int rc = set_launch(b, b->nt, b->ctas_per_sm);
+  if (rc) b->flat = old;
+  return rc;
+}
+
+int lbm_batch_get_tiling(const lbm_batch* b, int* tiling) {
+  if (!b || !tiling) return fail_msg(LBM_EINVAL, "null argument");
+  *tiling = b->flat ? LBM_TILING_FLAT : LBM_TILING_ROWS;
+  return LBM_OK;
+}
+
 int lbm_batch_tune(lbm_batch* b, int steps, int* threads_per_cta, int* ctas_per_sm, float* ms_per_step) {
   if (!b) return fail_msg(LBM_EINVAL, "null batch");
   if (steps < 1) return fail_msg(LBM_EINVAL, "steps must be positive");
@@ -465,15 +485,18 @@ int lbm_batch_tune(lbm_batch* b, int steps, int* threads_per_cta, int* ctas_per_
   const int ks[6] = {0, 1, 2, 4, 8, 16};  // 0: one CTA per work item
   const int n_nt = b->inplace ? 1 : 3, n_k = b->inplace ? 1 : 6;
   const int* nt_list = b->inplace ? &nts[1] : nts;
+  const int n_tiling = b->inplace ? 1 : 2;  // flat, then rows
   float best = 1e30f;
-  int best_nt = b->nt, best_k = b->ctas_per_sm;
+  int best_nt = b->nt, best_k = b->ctas_per_sm, best_flat = b->flat;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   int rc = LBM_OK;
+  for (int f = 0; f < n_tiling && rc == LBM_OK; ++f)
   for (int a = 0; a < n_nt && rc == LBM_OK; ++a)
     for (int c = 0; c < n_k && rc == LBM_OK; ++c) {
       if (ks[c] > batch_max_ctas_per_sm(b->prec, nt_list[a])) continue;  // persistent CTAs must be resident
+      b->flat = b->inplace || f == 0 ? 1 : 0;
       if ((rc = set_launch(b, nt_list[a], ks[c]))) break;
       if ((rc = launch_once(b, b->cur, b->stream))) break;  // warm-up
       cudaEventRecord(e0, b->stream);
@@ -487,6 +510,7 @@ int lbm_batch_tune(lbm_batch* b, int steps, int* threads_per_cta, int* ctas_per_
         best = ms;
         best_nt = nt_list[a];
         best_k = ks[c];
+        best_flat = b->flat;
       }
     }
   cudaMemcpyAsync(live, save, pool_bytes, cudaMemcpyDeviceToDevice, b->stream);
@@ -495,6 +519,7 @@ int lbm_batch_tune(lbm_batch* b, int steps, int* threads_per_cta, int* ctas_per_
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
+  b->flat = best_flat;
   if ((rc = set_launch(b, best_nt, best_k))) return rc;
   if (threads_per_cta) *threads_per_cta = best_nt;
   if (ctas_per_sm) *ctas_per_sm = best_k;

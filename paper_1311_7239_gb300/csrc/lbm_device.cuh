@@ -35,6 +35,8 @@ struct PairConst {
   float cq;                    // -s_v / 4
   // medium coefficients of the uniform medium (see PairCoef) and phi a / 2
   float u_inv_phi, u_l0, u_l0sq, u_l1, u_nclin, u_ncnl, u_c2, u_nR, u_cf7, u_cf8, u_hx, u_hy;
+  // per-cell media (pair_coef_het): 0.1 (1 - s_e/2) rho0 s, rho0 s, a_x / 2
+  float k_c2, k_rs, hax;
 };
 
 // Everything a step kernel needs, passed by value.
@@ -365,6 +367,31 @@ __device__ __forceinline__ PairCoef pair_coef_uniform(const PairConst& K) {
   return c;
 }
 
+// The same for a pair of cells of a per-cell medium: porosity ph, permeability k and viscous rate
+// sv of the two cells (Eqs. 3-4, 13, 18, as coef_of); hx, hy receive phi a / 2.
+__device__ __forceinline__ PairCoef pair_coef_het(const StepParams& P, float2 ph, float2 k, float2 sv, float2& hx, float2& hy) {
+  const PairConst& K = P.pc;
+  PairCoef c;
+  c.inv_phi = make_float2(fast_rcp(ph.x), fast_rcp(ph.y));
+  const float2 clin = mul2(mul2(ph, f2(P.nu)), make_float2(fast_rcp(k.x), fast_rcp(k.y)));  // phi nu / K
+  const float2 cnl = P.forch ? make_float2(1.75f * rsqrtf(150.0f * ph.x * k.x), 1.75f * rsqrtf(150.0f * ph.y * k.y)) : f2(0.0f);
+  c.l0 = fma2(f2(0.25f), clin, f2(0.5f));
+  c.l0sq = mul2(c.l0, c.l0);
+  c.l1 = mul2(f2(0.5f), cnl);
+  c.nclin = neg2(clin);
+  c.ncnl = neg2(cnl);
+  const float2 rs_phi = mul2(f2(K.k_rs), c.inv_phi);
+  c.c2 = mul2(f2(K.k_c2), c.inv_phi);
+  c.cq = mul2(f2(-0.25f), sv);
+  c.nR = neg2(rs_phi);
+  const float2 hvr = mul2(fma2(f2(-0.5f), sv, f2(1.0f)), rs_phi);  // (1 - s_v/2) rho0 s / phi
+  c.cf7 = mul2(f2(0.5f), hvr);
+  c.cf8 = mul2(f2(0.25f), hvr);
+  hx = mul2(f2(K.hax), ph);
+  hy = mul2(f2(K.hay), ph);
+  return c;
+}
+
 // hx, hy: phi a / 2 of the two cells.  d: in, stored pre-collision deviations; out, post-collision.
 __device__ __forceinline__ void collide_pair(float2 d[8], const PairCoef& c, float2 hx, float2 hy, const PairConst& K, float2& ux,
                                              float2& uy) {
@@ -467,6 +494,29 @@ __device__ __forceinline__ float collide_d2q5(float g[5], float ux, float uy, co
   g[3] += (r3 - r1) + r4;
   g[4] += (r3 - r2) - r4;
   return T;
+}
+
+// The same for two cells at once on packed FP32 pairs; g holds the stored deviations s g (s: the
+// storage scale), u is in lattice units.  T = T0 + n0 / s is carried as s T = s T0 + n0.
+__device__ __forceinline__ void collide_d2q5_pair(float2 g[5], float2 ux, float2 uy, const StepParams& P) {
+  const float2 n0 = add2(add2(add2(g[0], g[1]), add2(g[2], g[3])), g[4]);
+  const float2 n1 = sub2(g[1], g[3]), n2 = sub2(g[2], g[4]);
+  const float2 side = add2(add2(g[1], g[2]), add2(g[3], g[4]));
+  const float2 n3 = fma2(f2(-4.0f), g[0], side);
+  const float2 n4 = sub2(add2(g[1], g[3]), add2(g[2], g[4]));
+  const float2 sT = add2(f2(P.scale * P.T0), n0);  // s T
+  const float2 q = mul2(sT, f2(P.inv_sigma));
+  // increments n+ - n (n0 conserved) times the diagonal of N^-1 (as collide_d2q5)
+  const float2 r1 = mul2(f2(-0.5f * P.zeta1), fma2(neg2(ux), q, n1));
+  const float2 r2 = mul2(f2(-0.5f * P.zeta1), fma2(neg2(uy), q, n2));
+  const float2 r3 = mul2(f2(-0.05f * P.zeta3), fma2(f2(-P.varpi), sT, n3));
+  const float2 r4 = mul2(f2(-0.25f * P.zeta4), n4);
+  const float2 a = add2(r3, r4), b = sub2(r3, r4);
+  g[0] = fma2(f2(-4.0f), r3, g[0]);
+  g[1] = add2(g[1], add2(r1, a));
+  g[2] = add2(g[2], add2(r2, b));
+  g[3] = add2(g[3], sub2(a, r1));
+  g[4] = add2(g[4], sub2(b, r2));
 }
 
 // D2Q5 velocities of Eq. B.3 (0 rest, 1..4 as D2Q8's first four)

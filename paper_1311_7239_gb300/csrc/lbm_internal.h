@@ -16,10 +16,10 @@ struct lbm_config;
 namespace lbm {
 int validate_config(const ::lbm_config* c);
 void params_from_config(const ::lbm_config& k, int prec, int pitch, int64_t plane, StepParams& P);
-int64_t batch_items(int nx, int ny, int bc_y, int nt);
+int64_t batch_items(int nx, int ny, int bc_y, int nt, int flat);
 int batch_max_ctas_per_sm(int prec, int nt);
 cudaError_t launch_step_batch(const StepParams* Pd, const int64_t* item_start, const int* item_lattice, int n, int64_t total, int prec,
-                              int nt, int grid, cudaStream_t s);
+                              int nt, int grid, int flat, cudaStream_t s);
 cudaError_t launch_step(const StepParams& P, int prec, bool het, bool thermal, cudaStream_t s);
 cudaError_t launch_step_inplace(const StepParams& P, int prec, bool het, bool thermal, cudaStream_t s);
 int64_t inplace_items(int nx, int ny, int bc_x, int bc_y);

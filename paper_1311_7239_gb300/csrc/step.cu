@@ -14,10 +14,10 @@
 
 namespace lbm {
 
-// Interior cells of a uniform medium with 16-bit storage, where the step is bound by instruction
-// issue rather than by HBM, are collided two at a time with the packed FP32 pairs (collide_pair);
-// FP32 storage and per-cell media keep the scalar collision, whose lower register count holds
-// more loads in flight.
+// Interior cells with 16-bit storage, where the step is bound by instruction issue rather than by
+// HBM, are collided two at a time with the packed FP32 pairs (collide_pair): without temperature
+// on any medium (step_item_words), with temperature on a uniform medium; FP32 storage keeps the
+// scalar collision, whose lower register count holds more loads in flight.
 template <int PREC, bool HET>
 constexpr bool kPacked = PREC != PREC_FP32 && !HET;
 
@@ -59,11 +59,14 @@ __device__ void frame_step(const StepParams& P, const Frame& F, int k) {
   }
 }
 
-// Main item of the packed collision without temperature: the populations stay in their stored
-// 16-bit form (two cells per 32-bit word) until each pair is collided, which halves the
-// registers that hold the gathered state.
-template <int PREC, int NT>
+// Main item of the packed collision with 16-bit storage: the populations stay in their stored
+// form (two cells per 32-bit word) until each pair is collided, which halves the registers that
+// hold the gathered state.  A per-cell medium is read as float4 vectors of the four cells, issued
+// ahead of the populations, and turned into pair coefficients per pair; with the temperature
+// (uniform medium) the D2Q5 populations are gathered and collided the same way.
+template <int PREC, bool HET, bool THERMAL, int NT>
 __device__ __forceinline__ void step_item_words(const StepParams& P, const Tiling& tl, int item) {
+  static_assert(!(HET && THERMAL), "the temperature step with a per-cell medium uses the scalar path");
   using S = Store<PREC>;
   using T = typename S::T;
   constexpr int C = kCellsPerThread;
@@ -79,6 +82,12 @@ __device__ __forceinline__ void step_item_words(const StepParams& P, const Tilin
   yp = yp >= P.ny ? 0 : yp;
   const int64_t pl = P.plane;
   const int64_t rm = (int64_t)ym * P.pitch, r0 = (int64_t)y * P.pitch, rp = (int64_t)yp * P.pitch;
+  float4 ph4, k4, sv4;
+  if (HET) {
+    ph4 = __ldg(reinterpret_cast<const float4*>(P.phi + r0 + xl));
+    k4 = __ldg(reinterpret_cast<const float4*>(P.K + r0 + xl));
+    sv4 = P.sv ? __ldg(reinterpret_cast<const float4*>(P.sv + r0 + xl)) : make_float4(P.s_v, P.s_v, P.s_v, P.s_v);
+  }
   // pull streaming, Eq. 15, as stored (s d): w[i] = pairs (c0, c1), (c2, c3) of population i
   uint32_t w[8][2];
   gather4w<PREC, 1>(src + 0 * pl + r0, xl, P.pitch, lane, w[0]);   // e1 = ( 1, 0)
@@ -89,6 +98,15 @@ __device__ __forceinline__ void step_item_words(const StepParams& P, const Tilin
   gather4w<PREC, -1>(src + 5 * pl + rm, xl, P.pitch, lane, w[5]);  // e6 = (-1, 1)
   gather4w<PREC, -1>(src + 6 * pl + rp, xl, P.pitch, lane, w[6]);  // e7 = (-1,-1)
   gather4w<PREC, 1>(src + 7 * pl + rp, xl, P.pitch, lane, w[7]);   // e8 = ( 1,-1)
+  uint32_t gw[5][2];
+  if (THERMAL) {  // Eq. B.2: g_i(x) = g+_i(x - e_i), D2Q5 (rest, e1..e4)
+    const T* __restrict__ gsrc = static_cast<const T*>(P.gsrc);
+    gather4w<PREC, 0>(gsrc + 0 * pl + r0, xl, P.pitch, lane, gw[0]);
+    gather4w<PREC, 1>(gsrc + 1 * pl + r0, xl, P.pitch, lane, gw[1]);
+    gather4w<PREC, 0>(gsrc + 2 * pl + rm, xl, P.pitch, lane, gw[2]);
+    gather4w<PREC, -1>(gsrc + 3 * pl + r0, xl, P.pitch, lane, gw[3]);
+    gather4w<PREC, 0>(gsrc + 4 * pl + rp, xl, P.pitch, lane, gw[4]);
+  }
   const bool wall_row = (P.bc_y == BC_WALL || P.bc_y == BC_NEE) && (y == 0 || y == P.ny - 1);
   if (!has_group || !idx_ok || wall_row || x0 == 0 || x0 + C >= P.nx) return;
   float check = 0.0f;
@@ -98,7 +116,26 @@ __device__ __forceinline__ void step_item_words(const StepParams& P, const Tilin
 #pragma unroll
     for (int i = 0; i < 8; ++i) dp[i] = S::w2f(w[i][h]);
     float2 ux, uy;
-    collide_pair(dp, pair_coef_uniform(P.pc), f2(P.pc.u_hx), f2(P.pc.u_hy), P.pc, ux, uy);
+    if (HET) {
+      float2 hx, hy;
+      const PairCoef c = pair_coef_het(P, h ? make_float2(ph4.z, ph4.w) : make_float2(ph4.x, ph4.y),
+                                       h ? make_float2(k4.z, k4.w) : make_float2(k4.x, k4.y),
+                                       h ? make_float2(sv4.z, sv4.w) : make_float2(sv4.x, sv4.y), hx, hy);
+      collide_pair(dp, c, hx, hy, P.pc, ux, uy);
+    } else if (THERMAL) {
+      float2 gp[5];
+#pragma unroll
+      for (int i = 0; i < 5; ++i) gp[i] = S::w2f(gw[i][h]);
+      // a = g beta (T - T0) j added to the body force (Boussinesq): phi a_y / 2 of the two cells
+      const float2 sTd = add2(add2(add2(gp[0], gp[1]), add2(gp[2], gp[3])), gp[4]);  // s (T - T0)
+      const float2 hy = mul2(f2(P.phi_u), fma2(f2(0.5f * P.g_beta * P.inv_scale), sTd, f2(P.pc.hay)));
+      collide_pair(dp, pair_coef_uniform(P.pc), f2(P.pc.u_hx), hy, P.pc, ux, uy);
+      collide_d2q5_pair(gp, ux, uy, P);
+#pragma unroll
+      for (int i = 0; i < 5; ++i) gw[i][h] = S::f2w(gp[i]);
+    } else {
+      collide_pair(dp, pair_coef_uniform(P.pc), f2(P.pc.u_hx), f2(P.pc.u_hy), P.pc, ux, uy);
+    }
     check += (fabsf(ux.x) + fabsf(uy.x)) + (fabsf(ux.y) + fabsf(uy.y));
 #pragma unroll
     for (int i = 0; i < 8; ++i) w[i][h] = S::f2w(dp[i]);
@@ -107,6 +144,11 @@ __device__ __forceinline__ void step_item_words(const StepParams& P, const Tilin
   T* __restrict__ dst = static_cast<T*>(P.dst);
 #pragma unroll
   for (int i = 0; i < 8; ++i) *reinterpret_cast<uint2*>(dst + i * pl + r0 + x0) = make_uint2(w[i][0], w[i][1]);
+  if (THERMAL) {
+    T* __restrict__ gdst = static_cast<T*>(P.gdst);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) *reinterpret_cast<uint2*>(gdst + i * pl + r0 + x0) = make_uint2(gw[i][0], gw[i][1]);
+  }
 }
 
 // Work item `item` of one lattice, for CTAs of NT threads: items [0, frame_blocks) do the frame,
@@ -122,8 +164,8 @@ __device__ __forceinline__ void step_item(const StepParams& P, const Tiling& tl,
     frame_step<PREC, HET, THERMAL>(P, F, item * NT + (int)threadIdx.x);
     return;
   }
-  if constexpr (kPacked<PREC, HET> && !THERMAL) {
-    step_item_words<PREC, NT>(P, tl, item);
+  if constexpr (PREC != PREC_FP32 && !(HET && THERMAL)) {
+    step_item_words<PREC, HET, THERMAL, NT>(P, tl, item);
     return;
   }
   int x0, y;
@@ -241,18 +283,19 @@ __device__ __forceinline__ void step_item(const StepParams& P, const Tiling& tl,
   }
 }
 
-// One time step of one lattice: one CTA per work item.  Register caps (measured): 8 CTAs (32
-// warps) per SM for the flow alone (64 registers), with every storage precision; 6 and 5 with
-// the temperature populations (80 and 96).
+// One time step of one lattice: one CTA per work item (flat tiling).  Register caps (measured): 8
+// CTAs (32 warps) per SM for the flow alone (64 registers), with every storage precision; 6 with
+// the temperature populations (80 registers; the 16-bit uniform-medium form runs 8 % faster than
+// at 96), 5 (96) for the scalar 16-bit temperature step of a per-cell medium.
 template <int PREC, bool HET, bool THERMAL>
-__global__ void __launch_bounds__(kStepThreads, THERMAL ? (PREC == PREC_FP32 ? 6 : 5) : 8) k_step(const StepParams P, Tiling tl) {
+__global__ void __launch_bounds__(kStepThreads, THERMAL ? (PREC != PREC_FP32 && HET ? 5 : 6) : 8) k_step(const StepParams P, Tiling tl) {
   step_item<PREC, HET, THERMAL, kStepThreads>(P, tl, blockIdx.x);
 }
 
 template <int PREC, bool HET, bool THERMAL>
 static cudaError_t launch_step_t(const StepParams& P, cudaStream_t s) {
-  const Tiling tl = tiling_of(P.nx, P.ny, P.bc_y, kStepThreads);
-  const long long blocks = (long long)tl.frame_blocks + main_items(tl, P.ny);
+  const Tiling tl = tiling_of(P.nx, P.ny, P.bc_y, kStepThreads, true);
+  const long long blocks = (long long)tl.frame_blocks + main_items(tl, P.ny, kStepThreads);
   k_step<PREC, HET, THERMAL><<<(unsigned)blocks, kStepThreads, 0, s>>>(P, tl);
   return cudaGetLastError();
 }
@@ -291,23 +334,25 @@ __device__ __forceinline__ void load_params(StepParams& sP, const StepParams* __
 }
 
 // Register caps (measured on a 512-lattice ensemble): the streaming rate follows the number of
-// resident warps, so the per-item form is held to 64 registers (32 warps per SM, a few bytes of
-// spill) and the persistent form to 85 (24 warps); uncapped they take 72-108 registers and run
-// 1.2-1.5x slower.
+// resident warps, so the per-item form is held to 64 registers with FP32 storage (32 warps per SM,
+// a few bytes of spill) and to 80 with 16-bit storage (24 warps; its packed collision spills
+// 200 bytes at 64 and runs 13 % slower), the persistent form to 85 (24 warps); uncapped they take
+// 72-108 registers and run 1.2-1.5x slower.  flat: the lattices' tiling (tiling_of).
 template <int PREC, int NT>
-__global__ void __launch_bounds__(NT, 1024 / NT) k_step_batch_items(const StepParams* __restrict__ Pd, const int64_t* __restrict__ item_start,
-                                                         const int* __restrict__ item_lattice) {
+__global__ void __launch_bounds__(NT, (PREC == PREC_FP32 ? 1024 : 768) / NT) k_step_batch_items(const StepParams* __restrict__ Pd,
+                                                                                         const int64_t* __restrict__ item_start,
+                                                                                         const int* __restrict__ item_lattice, int flat) {
   __shared__ StepParams sP;
   const int d = item_lattice[blockIdx.x];
   load_params<NT>(sP, Pd, d);
   __syncthreads();
-  const Tiling tl = tiling_of(sP.nx, sP.ny, sP.bc_y, NT);
+  const Tiling tl = tiling_of(sP.nx, sP.ny, sP.bc_y, NT, flat != 0);
   step_item<PREC, true, false, NT>(sP, tl, (int)((int64_t)blockIdx.x - item_start[d]));
 }
 
 template <int PREC, int NT>
 __global__ void __launch_bounds__(NT, 768 / NT) k_step_batch(const StepParams* __restrict__ Pd, const int64_t* __restrict__ item_start, int n,
-                                                   int64_t total) {
+                                                   int64_t total, int flat) {
   __shared__ StepParams sP;
   const int64_t chunk = (total + gridDim.x - 1) / gridDim.x;
   const int64_t begin = (int64_t)blockIdx.x * chunk;
@@ -322,7 +367,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_step_batch(const StepParams* _
   int64_t next = lo + 1 < n ? item_start[lo + 1] : total;
   load_params<NT>(sP, Pd, lo);
   __syncthreads();
-  Tiling tl = tiling_of(sP.nx, sP.ny, sP.bc_y, NT);
+  Tiling tl = tiling_of(sP.nx, sP.ny, sP.bc_y, NT, flat != 0);
   for (int64_t it = begin; it < end; ++it) {
     if (it >= next) {  // the range crosses into the next lattice(s): uniform over the CTA
       while (it >= next) {
@@ -333,7 +378,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_step_batch(const StepParams* _
       __syncthreads();  // every thread is done with the previous parameters
       load_params<NT>(sP, Pd, lo);
       __syncthreads();
-      tl = tiling_of(sP.nx, sP.ny, sP.bc_y, NT);
+      tl = tiling_of(sP.nx, sP.ny, sP.bc_y, NT, flat != 0);
     }
     step_item<PREC, true, false, NT>(sP, tl, (int)(it - first));
   }
@@ -343,27 +388,27 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_step_batch(const StepParams* _
 
 namespace lbm {
 
-int64_t batch_items(int nx, int ny, int bc_y, int nt) {
-  const Tiling tl = tiling_of(nx, ny, bc_y, nt);
-  return (int64_t)tl.frame_blocks + main_items(tl, ny);
+int64_t batch_items(int nx, int ny, int bc_y, int nt, int flat) {
+  const Tiling tl = tiling_of(nx, ny, bc_y, nt, flat != 0);
+  return (int64_t)tl.frame_blocks + main_items(tl, ny, nt);
 }
 
 template <int PREC, int NT>
 static void launch_batch_t(const StepParams* Pd, const int64_t* item_start, const int* item_lattice, int n, int64_t total, int grid,
-                           cudaStream_t s) {
+                           int flat, cudaStream_t s) {
   if (item_lattice)
-    k_step_batch_items<PREC, NT><<<(unsigned)total, NT, 0, s>>>(Pd, item_start, item_lattice);
+    k_step_batch_items<PREC, NT><<<(unsigned)total, NT, 0, s>>>(Pd, item_start, item_lattice, flat);
   else
-    k_step_batch<PREC, NT><<<grid, NT, 0, s>>>(Pd, item_start, n, total);
+    k_step_batch<PREC, NT><<<grid, NT, 0, s>>>(Pd, item_start, n, total, flat);
 }
 
 template <int PREC>
 static cudaError_t launch_batch_p(const StepParams* Pd, const int64_t* item_start, const int* item_lattice, int n, int64_t total,
-                                  int nt, int grid, cudaStream_t s) {
+                                  int nt, int grid, int flat, cudaStream_t s) {
   switch (nt) {
-    case 64: launch_batch_t<PREC, 64>(Pd, item_start, item_lattice, n, total, grid, s); break;
-    case 256: launch_batch_t<PREC, 256>(Pd, item_start, item_lattice, n, total, grid, s); break;
-    default: launch_batch_t<PREC, 128>(Pd, item_start, item_lattice, n, total, grid, s); break;
+    case 64: launch_batch_t<PREC, 64>(Pd, item_start, item_lattice, n, total, grid, flat, s); break;
+    case 256: launch_batch_t<PREC, 256>(Pd, item_start, item_lattice, n, total, grid, flat, s); break;
+    default: launch_batch_t<PREC, 128>(Pd, item_start, item_lattice, n, total, grid, flat, s); break;
   }
   return cudaGetLastError();
 }
@@ -382,10 +427,10 @@ int batch_max_ctas_per_sm(int prec, int nt) {
 }
 
 cudaError_t launch_step_batch(const StepParams* Pd, const int64_t* item_start, const int* item_lattice, int n, int64_t total, int prec,
-                              int nt, int grid, cudaStream_t s) {
-  if (prec == PREC_FP32) return launch_batch_p<PREC_FP32>(Pd, item_start, item_lattice, n, total, nt, grid, s);
-  if (prec == PREC_FP16) return launch_batch_p<PREC_FP16>(Pd, item_start, item_lattice, n, total, nt, grid, s);
-  return launch_batch_p<PREC_BF16>(Pd, item_start, item_lattice, n, total, nt, grid, s);
+                              int nt, int grid, int flat, cudaStream_t s) {
+  if (prec == PREC_FP32) return launch_batch_p<PREC_FP32>(Pd, item_start, item_lattice, n, total, nt, grid, flat, s);
+  if (prec == PREC_FP16) return launch_batch_p<PREC_FP16>(Pd, item_start, item_lattice, n, total, nt, grid, flat, s);
+  return launch_batch_p<PREC_BF16>(Pd, item_start, item_lattice, n, total, nt, grid, flat, s);
 }
 
 }  // namespace lbm

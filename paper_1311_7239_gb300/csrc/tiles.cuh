@@ -104,10 +104,15 @@ __host__ __device__ inline Frame frame_of(int nx, int ny, int bc_y, int C) {
 }
 
 // Work items of one lattice for CTAs of nt threads: the frame items first, then the main items.
-// A row of G = ceil(nx / C) groups takes gx = ceil(G / nt) items when G > nt; shorter rows are
-// packed rows_per_item = nt / G to an item (thread t of the item: row t / G, group t % G).
+// Row-aligned tiling: a row of G = ceil(nx / C) groups takes gx = ceil(G / nt) items when G > nt;
+// shorter rows are packed rows_per_item = nt / G to an item (thread t of the item: row t / G,
+// group t % G).  Flat tiling: the ny G groups in row-major order, nt consecutive groups per item,
+// so that an item may span the end of one row and the start of the next; only the lattice's last
+// item is ragged.  (Within a warp the one-cell shifts then also cross a row end, between the last
+// group of a row and the first of the next: both are frame groups, whose main-path results are
+// not stored.)
 struct Tiling {
-  int frame_blocks, gx, rows_per_item, groups;
+  int frame_blocks, gx, rows_per_item, groups, flat;
 };
 
 // Row and column of frame cell k (frame group k / C, cell k % C of the group).
@@ -127,8 +132,9 @@ __device__ __forceinline__ bool frame_cell(const Frame& F, int ny, int k, int& x
   return true;
 }
 
-__host__ __device__ inline Tiling tiling_of(int nx, int ny, int bc_y, int nt) {
+__host__ __device__ inline Tiling tiling_of(int nx, int ny, int bc_y, int nt, bool flat = false) {
   Tiling t;
+  t.flat = flat ? 1 : 0;
   t.groups = (nx + kCellsPerThread - 1) / kCellsPerThread;
   const Frame F = frame_of(nx, ny, bc_y, kCellsPerThread);
   t.frame_blocks = (int)(((int64_t)F.count * kCellsPerThread + nt - 1) / nt);  // one thread per frame cell
@@ -142,13 +148,22 @@ __host__ __device__ inline Tiling tiling_of(int nx, int ny, int bc_y, int nt) {
   return t;
 }
 
-__host__ __device__ inline int64_t main_items(const Tiling& t, int ny) {
+__host__ __device__ inline int64_t main_items(const Tiling& t, int ny, int nt) {
+  if (t.flat) return ((int64_t)ny * t.groups + nt - 1) / nt;
   return t.rows_per_item > 1 ? (int64_t)((ny + t.rows_per_item - 1) / t.rows_per_item) : (int64_t)t.gx * ny;
 }
 
 // Row and first cell of thread `tid` in main item b; false for a thread with no group (it still
 // takes part in the loads and shuffles, on a clamped row, and stores nothing).
 __device__ __forceinline__ bool main_group(const Tiling& t, int ny, int nt, int b, int tid, int& x0, int& y) {
+  if (t.flat) {
+    const int64_t g = (int64_t)b * nt + tid;
+    y = (int)(g / t.groups);
+    x0 = (int)(g - (int64_t)y * t.groups) * kCellsPerThread;
+    const bool ok = y < ny;
+    if (!ok) y = ny - 1;
+    return ok;
+  }
   if (t.rows_per_item > 1) {
     const int r = tid / t.groups;
     y = b * t.rows_per_item + r;

@@ -20,6 +20,7 @@ FP32, FP16_DEV, BF16_DEV = 0, 1, 2
 PERIODIC, WALL, PRESSURE, NEE = 0, 1, 2, 3
 STREAM_AB, STREAM_INPLACE = 0, 1
 OPT_NO_RESIDUAL_RECORD = 1
+TILING_ROWS, TILING_FLAT = 0, 1
 LEFT, RIGHT, BOTTOM, TOP = 0, 1, 2, 3
 CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy
 LOSS_OUTLET_FLUX, LOSS_VELOCITY_MISFIT = 0, 1
@@ -107,6 +108,8 @@ SIGNATURES = {
     "lbm_batch_step_each": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "lbm_batch_set_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "lbm_batch_get_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "lbm_batch_set_tiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "lbm_batch_get_tiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "lbm_batch_tune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_float)]),
     "lbm_batch_macros": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _f32p, _f32p, _f32p]),
@@ -401,14 +404,22 @@ class Batch:
         _check(lib().lbm_batch_get_launch(self._h, ctypes.byref(a), ctypes.byref(b)), "lbm_batch_get_launch")
         return a.value, b.value
 
+    def set_tiling(self, tiling):
+        _check(lib().lbm_batch_set_tiling(self._h, int(tiling)), "lbm_batch_set_tiling")
+
+    def get_tiling(self):
+        t = ctypes.c_int()
+        _check(lib().lbm_batch_get_tiling(self._h, ctypes.byref(t)), "lbm_batch_get_tiling")
+        return t.value
+
     def tune(self, steps=20):
         a, b, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
         _check(lib().lbm_batch_tune(self._h, int(steps), ctypes.byref(a), ctypes.byref(b), ctypes.byref(ms)), "lbm_batch_tune")
         return a.value, b.value, ms.value
 
     def tune_cached(self, path=None, steps=20):
-        """Launch shape from a JSON cache on disk (keyed by GPU, storage precision, lattice count and
-        total cells rounded to a power of two); a miss runs ``tune`` and records the result."""
+        """Launch shape and tiling from a JSON cache on disk (keyed by GPU, storage precision, lattice
+        count and total cells rounded to a power of two); a miss runs ``tune`` and records the result."""
         import json
 
         import torch
@@ -423,10 +434,11 @@ class Batch:
             cache = {}
         if key in cache:
             nt, k = cache[key]["threads_per_cta"], cache[key]["ctas_per_sm"]
+            self.set_tiling(cache[key].get("tiling", TILING_FLAT))
             self.set_launch(nt, k)
             return nt, k, cache[key]["ms_per_step"], True
         nt, k, ms = self.tune(steps)
-        cache[key] = {"threads_per_cta": nt, "ctas_per_sm": k, "ms_per_step": ms}
+        cache[key] = {"threads_per_cta": nt, "ctas_per_sm": k, "tiling": self.get_tiling(), "ms_per_step": ms}
         os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
         tmp = path + ".tmp"
         with open(tmp, "w") as fh:

@@ -12,6 +12,7 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built liblbm.so")
     config.addinivalue_line("markers", "slow: long-running CPU check (minutes)")
+    config.addinivalue_line("markers", "gpu_long: GPU run of several minutes, only with -m gpu_long (not part of -m gpu)")
 
 
 # Relative L2 errors against the FP64 oracle measured by the GPU tests; written as JSON to the path

@@ -43,15 +43,18 @@ def test_batch_equals_single_lattices_bitwise(lbm, prec):
     cfgs, media = ensemble.ensemble(lbm, n=7, seed=3, lo=8, hi=300, precision=prec)
     steps = 45
     want = _singles(lbm, cfgs, media, steps)
-    for shape in [(128, 4), (64, 8), (256, 2), (128, 32), (128, 0), (64, 0)]:
-        with ensemble.build(lbm, cfgs, media) as b:
-            b.set_launch(*shape)
-            b.step(steps)  # a graph of 32 + 13 launches
-            b.sync()
-            for d in range(len(cfgs)):
-                got = b.get_populations(d).cpu().numpy()
-                assert np.array_equal(got, want[d]), (shape, d)
-            assert b.info()["steps"] == steps
+    for tiling in (lbm.TILING_FLAT, lbm.TILING_ROWS):
+        for shape in [(128, 4), (64, 8), (256, 2), (128, 32), (128, 0), (64, 0)]:
+            with ensemble.build(lbm, cfgs, media) as b:
+                b.set_tiling(tiling)
+                b.set_launch(*shape)
+                assert b.get_tiling() == tiling
+                b.step(steps)  # a graph of 32 + 13 launches
+                b.sync()
+                for d in range(len(cfgs)):
+                    got = b.get_populations(d).cpu().numpy()
+                    assert np.array_equal(got, want[d]), (tiling, shape, d)
+                assert b.info()["steps"] == steps
 
 
 def test_step_each_and_tune_leave_results_unchanged(lbm):
@@ -59,7 +62,7 @@ def test_step_each_and_tune_leave_results_unchanged(lbm):
     with ensemble.build(lbm, cfgs, media) as a, ensemble.build(lbm, cfgs, media) as b:
         nt, k, ms = a.tune(steps=3)
         assert nt in (64, 128, 256) and 0 <= k <= 16 and ms > 0
-        assert a.get_launch() == (nt, k)
+        assert a.get_launch() == (nt, k) and a.get_tiling() in (lbm.TILING_ROWS, lbm.TILING_FLAT)
         a.step(40)
         b.step_each(40)
         for d in range(len(cfgs)):

@@ -50,10 +50,12 @@ for (nx, ny), (bx, by), prec in itertools.product([(2, 3), (3, 2), (5, 7), (33, 
             runs += 1
 cfgs, media = workloads.ensemble(lbm, n=9, seed=3, lo=8, hi=300)
 with workloads.build(lbm, cfgs, media) as b:
-    for shape in [(64, 0), (128, 0), (128, 2), (256, 1)]:
-        b.set_launch(*shape)
-        b.step(11)
-        b.sync()
+    for tiling in (lbm.TILING_FLAT, lbm.TILING_ROWS):
+        b.set_tiling(tiling)
+        for shape in [(64, 0), (128, 0), (128, 2), (256, 1)]:
+            b.set_launch(*shape)
+            b.step(11)
+            b.sync()
 for prec in (0, 1):
     cfgs, media = workloads.ensemble(lbm, n=9, seed=3, lo=8, hi=300, precision=prec)
     for c in cfgs:

@@ -84,8 +84,8 @@ def test_table1_nusselt(lbm, Da, Ra, phi, walls):
 
 # Rows whose grid in the paper puts tau_v of Eq. 26 within 0.015 of 1/2 at Ma = 0.1, run on a finer
 # grid or, for Da = 1e-6, Ra = 1e8, at Ma = 0.3 (the bound the paper states) on a 400 grid:
-# (Da, Ra, phi, grid, Ma).  The Da = 1e-6, Ra = 1e9 rows would need grids of ~3600 at Ma = 0.1 or
-# ~1200 at Ma = 0.3 run for tens of millions of steps; they are not run.
+# (Da, Ra, phi, grid, Ma).  The Da = 1e-6, Ra = 1e9 rows need a 1200 grid at Ma = 0.3 run for up
+# to 24 million steps: tests/test_gpu_long_table1.py (marker gpu_long, not part of -m gpu).
 FINER = [(1e-4, 1e7, phi, 400, 0.1) for phi in (0.4, 0.6, 0.9)] + \
         [(1e-6, 1e7, phi, 250, 0.1) for phi in (0.4, 0.6, 0.9)] + \
         [(1e-6, 1e8, phi, 400, 0.3) for phi in (0.4, 0.6, 0.9)]
@@ -105,3 +105,4 @@ def test_table1_nusselt_finer_grid_or_mach(lbm, Da, Ra, phi, grid, Ma):
     print(f"{grid}^2 halfway walls, Ma={Ma}, Da={Da:g} Ra={Ra:g} phi={phi}: Nu_left={nu_l:.4f} Nu_right={nu_r:.4f} after {steps} "
           f"steps; Table 1 present {present}; rel. diff {abs(nu_l - present) / present:.3%}")
     assert abs(nu_l - present) <= max(0.02, spread) * present
+

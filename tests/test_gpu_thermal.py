@@ -4,8 +4,8 @@ natural-convection workload's size and tiling, in every storage precision and bo
 Two kinds of check:
 
 * One step, cell by cell, on a 1100 x 7 lattice with isothermal sides and adiabatic top and
-  bottom: a row spans three 512-cell work items (the last one ragged), which is the tiling of
-  every lattice wider than 512 cells, e.g. the 2048^2 natural-convection cavity.
+  bottom: a row is longer than one 512-cell work item, so items end inside rows and span row
+  ends, as on every lattice wider than 512 cells (e.g. the 2048^2 natural-convection cavity).
 * 32 steps (one replay of the 32-step CUDA graph that long runs replay) of the 2048^2
   natural-convection workload (eps = 0.6, Da = 1e-2, Ra = 1e5, Pr = 1, Ma = 0.1, T_h = 21,
   T_c = 1) from a seeded random pre-collision state, on sampled cells: after k steps a cell
@@ -96,8 +96,8 @@ def _check_close(got, want, rest, prec, tol_fp32, what):
 @pytest.mark.parametrize("streaming", [0, 1], ids=["ab", "inplace"])
 @pytest.mark.parametrize("prec", [0, 1, 2], ids=["fp32", "fp16", "bf16"])
 def test_thermal_one_step_rows_of_three_items(lbm, prec, streaming):
-    """One coupled step from a random state on 1100 x 7 (275 four-cell groups per row: three work
-    items of 128 threads, the last ragged), halfway walls, isothermal sides at 21 and 1, adiabatic
+    """One coupled step from a random state on 1100 x 7 (275 four-cell groups per row, work items
+    of 128 groups: items end inside rows and span row ends), halfway walls, isothermal sides at 21 and 1, adiabatic
     top and bottom, a buoyancy strong enough to change u by ~1e-3 per step, against the oracle's
     coupled step, element by element."""
     case = Case(1100, 7, nu=0.05, phi=0.6, K=3.0, bc_x="wall", bc_y="wall", precision=prec, streaming=streaming,
