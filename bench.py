@@ -336,8 +336,9 @@ def thermal_form(lbm, L, steps, warmup, local_rank):
 
 
 def heterogeneous_form(lbm, L, steps, warmup, local_rank):
-    """The bench cavity with a random medium (eps, K per cell: 72 B per update) and, in addition,
-    a per-cell viscosity ratio (J = 4 in the lower half: 76 B per update)."""
+    """The bench cavity with a random medium (eps, K per cell: 72 B per update), in addition a
+    per-cell viscosity ratio (J = 4 in the lower half: 76 B per update), and the random medium with
+    FP16 storage (40 B per update)."""
     import numpy as np
     import torch
 
@@ -348,9 +349,10 @@ def heterogeneous_form(lbm, L, steps, warmup, local_rank):
     eps, K = synth.heterogeneous_medium(L, L, H=L, seed=7, da_mean=1e-3, corr_len=32.0, eps_mean=0.4, eps_sd=0.05, eps_lo=0.2)
     J = np.where(np.arange(L)[:, None] < L // 2, 4.0, 1.0).astype(np.float32) * np.ones((L, L), np.float32)
     out = {}
-    for name, bpl, with_j in (("medium", 72, False), ("medium_and_J", 76, True)):
+    for name, prec, bpl, with_j in (("medium", "fp32", 72, False), ("medium_and_J", "fp32", 76, True),
+                                    ("medium_fp16", "fp16", 40, False)):
         stream = torch.cuda.Stream()
-        lat = make_lattice(lbm, L, "fp32", stream)
+        lat = make_lattice(lbm, L, prec, stream)
         lat.set_medium(torch.tensor(eps, dtype=torch.float32, device="cuda"), torch.tensor(K, dtype=torch.float32, device="cuda"))
         if with_j:
             lat.set_viscosity_ratio(torch.tensor(J, device="cuda"))
@@ -369,7 +371,8 @@ def heterogeneous_form(lbm, L, steps, warmup, local_rank):
         bw = bpl * L * L * steps / (ms * 1e-3) / 1e9
         out[name] = {"value": L * L * steps / (ms * 1e-3) / 1e6, "unit": "MLUPS", "achieved_gbs": bw, "roofline_frac": bw / peak,
                      "algorithmic_bytes_per_lu": bpl, "steps": steps, "clocks": clk.summary()}
-    return {"workload": f"lid-driven cavity {L}x{L}, random eps/K (and J = 4 in the lower half), FP32", **out}
+    return {"workload": f"lid-driven cavity {L}x{L}, random eps/K (and J = 4 in the lower half); FP32, and FP16 storage "
+                        f"(medium_fp16)", **out}
 
 
 def ensemble_form(lbm, steps, local_rank):
@@ -389,7 +392,8 @@ def ensemble_form(lbm, steps, local_rank):
         b = workloads.build(lbm, cfgs, media)
         cells = b.info()["cells"]
         device_bytes = b.info()["bytes"]
-        nt, k, _ = b.tune(steps=4)
+        nt, k, _ = b.tune(steps=8)
+        tiling = "flat" if b.get_tiling() == lbm.TILING_FLAT else "rows"
         b.step(32)
         b.sync()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -412,7 +416,8 @@ def ensemble_form(lbm, steps, local_rank):
         mlups = cells * steps / (ms_b * 1e-3) / 1e6
         res[key] = {"batched_MLUPS": mlups, "one_by_one_MLUPS": cells * each / (ms_e * 1e-3) / 1e6,
                     "batched_roofline_frac": mlups * 1e6 * bpl / 1e9 / peak, "algorithmic_bytes_per_lu": bpl,
-                    "launch": {"threads_per_cta": nt, "ctas_per_sm": k}, "steps": steps, "one_by_one_steps": each,
+                    "launch": {"threads_per_cta": nt, "ctas_per_sm": k, "tiling": tiling}, "steps": steps,
+                    "one_by_one_steps": each,
                     "device_bytes": device_bytes, "clocks": clk.summary()}
         torch.cuda.empty_cache()
     return {"workload": "512 heterogeneous porous cavities/channels, sides U{64..1024}, Re U[10,400], seed 42",

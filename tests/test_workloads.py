@@ -41,18 +41,23 @@ def test_ensemble_domains_of_the_bench_form():
 
 
 def test_ensemble_configs_recipe(lbm):
-    from paper_1311_7239_gb300 import workloads
+    from paper_1311_7239_gb300 import synth, workloads
 
     cfgs, media = workloads.ensemble(lbm, n=24, seed=42, lo=64, hi=256)
     cfgs2, media2 = workloads.ensemble(lbm, n=24, seed=42, lo=64, hi=256)
     assert all(bytes(a) == bytes(b) for a, b in zip(cfgs, cfgs2))            # deterministic
     assert all(np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) for a, b in zip(media, media2))
-    for c, (eps, K) in zip(cfgs, media):
+    doms = list(synth.ensemble_domains(24, 42, 64, 256))
+    for c, (eps, K), dom in zip(cfgs, media, doms):
         assert eps.shape == (c.ny, c.nx) and K.shape == (c.ny, c.nx)
         assert eps.min() >= 0.1 and eps.max() <= 0.9 and K.min() > 0
-        assert 0.5 + 3 * c.nu >= 0.56                                       # tau_v floor
         assert abs(c.p_rest - float(eps.mean())) < 1e-6                      # rest state phi p = mean(eps)
-        speed = c.u_wall[3][0] if c.bc_x == lbm.WALL else 0.02
+        if c.bc_x == lbm.WALL:                                              # cavity: lid speed U
+            speed = c.u_wall[3][0]
+        else:                                                               # channel: the centre speed its force gives
+            speed = _brinkman_centre_speed(c.ny, c.nu, c.phi, c.K, c.ax, n=800)
+        # Re = U H / nu of the domain's draw, unless the viscosity floor (tau_v >= 0.56) holds nu up
+        assert c.nu >= 0.02 - 1e-12 and (abs(c.nu - 0.02) < 1e-12 or abs(speed * c.ny / c.nu - dom["Re"]) < 0.02 * dom["Re"])
         assert speed / (math.sqrt(1 / 3) * math.sqrt(0.1)) <= 0.17          # |u| / (c_s sqrt(eps_min))
 
 
