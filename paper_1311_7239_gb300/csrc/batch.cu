@@ -62,6 +62,10 @@ struct lbm_batch {
   int64_t total_items = 0;
   int nt = 128, ctas_per_sm = 4, grid = 0, sms = 0;
   int flat = 1;  // tiling of the A-B batched kernel (LBM_TILING_FLAT / LBM_TILING_ROWS)
+  // A-B batches whose lattices share rho0, s_e, s_q and the storage scale: per-lattice records of the
+  // fields that differ (one array per buffer parity) for the per-item kernel
+  bool shared_consts = false;
+  BatchRec* rec[2] = {nullptr, nullptr};
   int cur = 0;
   int64_t steps = 0;
   int64_t cells = 0;
@@ -97,6 +101,7 @@ void release(lbm_batch* b) {
   for (int k = 0; k < 2; ++k) {
     cudaFree(b->pool[k]);
     cudaFree(b->dp[k]);
+    cudaFree(b->rec[k]);
   }
   cudaFree(b->phi);
   cudaFree(b->K);
@@ -160,14 +165,19 @@ int set_launch(lbm_batch* b, int nt, int ctas_per_sm) {
   return LBM_OK;
 }
 
+// One batched step from buffer parity `cur` on stream s, in the form the launch shape selects.
+cudaError_t launch_batch(const lbm_batch* b, int cur, cudaStream_t s) {
+  if (b->inplace)
+    return launch_step_batch_inplace(b->dp[cur], b->item_start, b->item_lattice, b->total_items, b->prec, cur, s);
+  if (b->shared_consts && b->ctas_per_sm == 0)
+    return launch_step_batch_shared(b->hp[0][0], b->rec[cur], b->dp[cur], b->item_start, b->item_lattice, b->total_items, b->prec,
+                                    b->nt, b->flat, s);
+  return launch_step_batch(b->dp[cur], b->item_start, b->ctas_per_sm == 0 ? b->item_lattice : nullptr, b->n, b->total_items, b->prec,
+                           b->nt, b->grid, b->flat, s);
+}
+
 int launch_once(lbm_batch* b, int cur, cudaStream_t s) {
-  if (b->inplace) {
-    LBM_BCUDA(launch_step_batch_inplace(b->dp[cur], b->item_start, b->item_lattice, b->total_items, b->prec, cur, s), "batched step kernel");
-    return LBM_OK;
-  }
-  LBM_BCUDA(launch_step_batch(b->dp[cur], b->item_start, b->ctas_per_sm == 0 ? b->item_lattice : nullptr, b->n, b->total_items, b->prec,
-                              b->nt, b->grid, b->flat, s),
-            "batched step kernel");
+  LBM_BCUDA(launch_batch(b, cur, s), "batched step kernel");
   return LBM_OK;
 }
 
@@ -175,11 +185,7 @@ int capture(lbm_batch* b, int cur) {
   if (!b->capture_stream) LBM_BCUDA(cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking), "cudaStreamCreate");
   LBM_BCUDA(cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
   cudaError_t le = cudaSuccess;
-  for (int k = 0; k < kBatchGraphSteps && le == cudaSuccess; ++k)
-    le = b->inplace ? launch_step_batch_inplace(b->dp[cur ^ (k & 1)], b->item_start, b->item_lattice, b->total_items, b->prec,
-                                                cur ^ (k & 1), b->capture_stream)
-                    : launch_step_batch(b->dp[cur ^ (k & 1)], b->item_start, b->ctas_per_sm == 0 ? b->item_lattice : nullptr, b->n,
-                                        b->total_items, b->prec, b->nt, b->grid, b->flat, b->capture_stream);
+  for (int k = 0; k < kBatchGraphSteps && le == cudaSuccess; ++k) le = launch_batch(b, cur ^ (k & 1), b->capture_stream);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(b->capture_stream, &g);
   if (le != cudaSuccess || e != cudaSuccess) {
@@ -340,6 +346,27 @@ int lbm_batch_create(const lbm_config* cfgs, int n, lbm_batch** out) {
   if (e != cudaSuccess) {
     release(b);
     return fail_msg(LBM_ECUDA, "batch parameter upload");
+  }
+  // the per-lattice records of A-B batches whose lattices share the collision constants
+  bool shared = !b->inplace;
+  for (int d = 1; d < n && shared; ++d)
+    shared = cfgs[d].rho0 == cfgs[0].rho0 && cfgs[d].s_e == cfgs[0].s_e && cfgs[d].s_q == cfgs[0].s_q &&
+             b->hp[0][d].scale == b->hp[0][0].scale;
+  if (shared) {
+    std::vector<BatchRec> r(n);
+    for (int k = 0; k < 2 && rc == LBM_OK && e == cudaSuccess; ++k) {
+      for (int d = 0; d < n; ++d) {
+        const StepParams& P = b->hp[k][d];
+        r[d] = BatchRec{P.src, P.dst, P.phi, P.K, P.uw, P.plane, P.nx, P.ny, P.pitch, P.bc_x, P.bc_y, P.forch, P.nu, P.s_v, P.ax, P.ay};
+      }
+      rc = balloc(b, reinterpret_cast<void**>(&b->rec[k]), n * sizeof(BatchRec), "cudaMalloc(lattice records)");
+      if (rc == LBM_OK) e = cudaMemcpy(b->rec[k], r.data(), n * sizeof(BatchRec), cudaMemcpyHostToDevice);
+    }
+    if (rc != LBM_OK || e != cudaSuccess) {
+      release(b);
+      return rc != LBM_OK ? rc : fail_msg(LBM_ECUDA, "batch record upload");
+    }
+    b->shared_consts = true;
   }
   if ((rc = set_launch(b, b->inplace ? 128 : 64, 0)) || (rc = lbm_batch_init_equilibrium(b, -1, 1.0, 0.0, 0.0, 0))) {
     release(b);

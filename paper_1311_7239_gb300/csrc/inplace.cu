@@ -282,10 +282,11 @@ __device__ __forceinline__ void ip_block(const StepParams& P, int frame_blocks, 
   }
 }
 
-// Register caps: 8 CTAs of 128 threads per SM for the flow (64 registers, as the A-B step), 5 with
-// the temperature populations (96; at 80 the FP32 thermal step spills).
+// Register caps: 8 CTAs of 128 threads per SM for the FP32 flow (64 registers, as the A-B step), 7
+// with 16-bit storage (72 registers: 4096^2 FP16 169.1 -> 173.5 GLUPS, 160.9 at 80), 5 with the
+// temperature populations (96; at 80 the FP32 thermal step spills).
 template <int PREC, bool HET, bool THERMAL, int PAR, bool REC>
-__global__ void __launch_bounds__(kIpThreads, THERMAL ? 5 : 8) k_step_ip(const StepParams P, int frame_blocks, int gx) {
+__global__ void __launch_bounds__(kIpThreads, THERMAL ? 5 : (PREC == PREC_FP32 ? 8 : 7)) k_step_ip(const StepParams P, int frame_blocks, int gx) {
   ip_block<PREC, HET, THERMAL, PAR, REC>(P, frame_blocks, gx, (int)blockIdx.x);
 }
 

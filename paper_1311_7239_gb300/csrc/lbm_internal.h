@@ -16,7 +16,23 @@ struct lbm_config;
 namespace lbm {
 int validate_config(const ::lbm_config* c);
 void params_from_config(const ::lbm_config& k, int prec, int pitch, int64_t plane, StepParams& P);
+// The fields that differ between the lattices of a batch whose lattices share rho0, s_e, s_q and
+// the storage scale (the batched per-item step then takes everything else from one lattice's
+// parameters passed by value, in the kernel's constant bank, instead of staging the whole set).
+struct BatchRec {
+  const void* src;
+  void* dst;
+  const float* phi;
+  const float* K;
+  const float* uw;
+  int64_t plane;
+  int nx, ny, pitch, bc_x, bc_y, forch;
+  float nu, s_v, ax, ay;
+};
+
 int64_t batch_items(int nx, int ny, int bc_y, int nt, int flat);
+cudaError_t launch_step_batch_shared(const StepParams& U, const BatchRec* R, const StepParams* Pd, const int64_t* item_start,
+                                     const int* item_lattice, int64_t total, int prec, int nt, int flat, cudaStream_t s);
 int batch_max_ctas_per_sm(int prec, int nt);
 cudaError_t launch_step_batch(const StepParams* Pd, const int64_t* item_start, const int* item_lattice, int n, int64_t total, int prec,
                               int nt, int grid, int flat, cudaStream_t s);
