@@ -354,11 +354,11 @@ __global__ void __launch_bounds__(NT, (PREC == PREC_FP32 ? 1024 : 768) / NT) k_s
 // parameters, by value: the kernel's constant bank) supplies those and the collision constants, the
 // record of the item's lattice the fields that differ, so a main item starts its gathers without
 // staging the parameter set in shared memory and keeps the constants out of the registers.  Frame
-// items, which use every parameter, stage the lattice's set as the general form.  At 64 registers
-// (32 warps per SM) the FP16 ensemble runs 117.7 GLUPS against 112.9 at 80 and 102.4 for the
-// staged form.
+// items, which use every parameter, stage the lattice's set as the general form.  Register caps
+// (512-lattice ensemble): FP16 at 72 registers 122.1 GLUPS (117.7 at 64, 112.9 at 80; the staged
+// form 102.4), BF16 and FP32 at 64 (BF16 113.4-114.7 at 64-80).
 template <int PREC, int NT>
-__global__ void __launch_bounds__(NT, 1024 / NT)
+__global__ void __launch_bounds__(NT, (PREC == PREC_FP16 ? 896 : 1024) / NT)
     k_step_batch_items_shared(const StepParams U, const BatchRec* __restrict__ R, const StepParams* __restrict__ Pd,
                               const int64_t* __restrict__ item_start, const int* __restrict__ item_lattice, int flat) {
   const int d = item_lattice[blockIdx.x];
