@@ -4,13 +4,15 @@ loss of the final state with respect to the per-cell log-permeability and porosi
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``); shares no code with the CUDA library.
 
 The forward map is the oracle's own step (Eq. 6 as collision Eq. 14 + streaming Eq. 15, then the
-pressure columns), f(t+1) = N(S(C(f(t); theta)); theta), from f(0) = N(f_eq(p0, u0; phi)) (the
-initial condition of Sec. 3.1).  The reverse sweep stores every state and applies, per step,
-  lambda <- J_N^T lambda,  lambda <- S^T lambda,  lambda <- J_C^T lambda,
-accumulating dL/dtheta from the theta-dependence of N and C and, at the end, of f(0).
+boundary nodes), f(t+1) = B(S(C(f(t); theta)); theta), from f(0) = B(f_eq(p0, u0; phi)) (the
+initial condition of Sec. 3.1), where B = W o N: N the pressure columns, then W the wall nodes of
+the sides with non-equilibrium extrapolation (Sec. 3's wall treatment).  The reverse sweep stores
+every state and applies, per step,
+  lambda <- J_W^T lambda,  lambda <- J_N^T lambda,  lambda <- S^T lambda,  lambda <- J_C^T lambda,
+accumulating dL/dtheta from the theta-dependence of W, N and C and, at the end, of f(0).
 
 Independent route: every Jacobian of a nonlinear per-cell map (the collision C, the pressure
-columns N, the initial equilibrium, the loss) is taken by the complex-step derivative
+columns N, the wall nodes W, the initial equilibrium, the loss) is taken by the complex-step derivative
 Im F(x + i h e_k) / h with h = 1e-30, which is exact to rounding and needs no hand derivation.
 Only the streaming map S is linear; its transpose is written out as the reversed link table.
 At |v| = 0 the magnitude has no derivative; the oracle's |v| is defined to have zero derivative
@@ -43,9 +45,9 @@ def stream_transpose(lam, flow: fl.Flow):
     for i in range(8):
         tx = xs + fl.E[i, 0]
         ty = ys + fl.E[i, 1]
-        if flow.bc_x in ("periodic", "pressure"):
+        if flow.bc_x in ("periodic", "pressure", "nee"):
             tx = tx % nx
-        if flow.bc_y == "periodic":
+        if flow.bc_y in ("periodic", "nee"):
             ty = ty % ny
         inside = (tx >= 0) & (tx < nx) & (ty >= 0) & (ty < ny)
         out[i][inside] = lam[i, ty[inside], tx[inside]]
@@ -108,6 +110,45 @@ def pressure_vjp(fs, lam, flow: fl.Flow, logK, phi):
     return out, glogk, gphi
 
 
+def _walls(f, flow, logK, phi):
+    return fl.wall_nodes(f, flow, phi=phi, K=np.exp(logK))
+
+
+def wall_vjp(fs, lam, flow: fl.Flow, logK, phi):
+    """VJP of the wall-node map W(fs): each wall node b is overwritten by a function of the state at
+    its inner neighbour nb and of phi at b and theta at nb.  Several wall nodes may share one nb
+    (a corner and its two neighbours along the walls), so the contributions are summed into nb."""
+    yb, xb, yn, xn, _ = fl.wall_node_list(flow)
+    out = lam.copy()
+    glogk = np.zeros((flow.ny, flow.nx))
+    gphi = np.zeros((flow.ny, flow.nx))
+    if yb.size == 0:
+        return out, glogk, gphi
+    bmask = np.zeros((flow.ny, flow.nx), dtype=bool)
+    bmask[yb, xb] = True
+    nmask = np.zeros((flow.ny, flow.nx), dtype=bool)
+    nmask[yn, xn] = True
+    # W reads the input at nb only: a node that is both a wall node and some wall node's nb would
+    # make the per-mask attribution below ambiguous (lattices of fewer than three nodes across)
+    assert not (bmask & nmask).any()
+    out[:, yb, xb] = 0.0
+    lam_b = np.where(bmask[None], lam, 0.0)
+    for j in range(8):  # d W_b / d fs_j(nb(b)), summed into nb
+        fc = fs.astype(np.complex128)
+        fc[j] = fc[j] + 1j * H * nmask
+        dW = np.imag(_walls(fc, flow, logK, phi)) / H
+        np.add.at(out[j], (yn, xn), np.sum(dW * lam_b, axis=0)[yb, xb])
+    for mask in (bmask, nmask):
+        for which in ("logK", "phi"):
+            lk = logK + (1j * H * mask if which == "logK" else 0)
+            ph = phi + (1j * H * mask if which == "phi" else 0)
+            dW = np.imag(_walls(fs.astype(np.complex128), flow, lk, ph)) / H
+            contrib = np.sum(dW * lam_b, axis=0)[yb, xb]  # d/dtheta at b or at nb(b), held by b
+            where = (yb, xb) if mask is bmask else (yn, xn)
+            np.add.at(glogk if which == "logK" else gphi, where, contrib)
+    return out, glogk, gphi
+
+
 def _shift_to_neighbour(a, nx):
     """Move values of columns 0 and nx-1 onto columns 1 and nx-2 (where the derivative belongs)."""
     out = np.zeros_like(a)
@@ -153,23 +194,51 @@ def _per_cell_loss_imag(fc, flow, kind, target, logK, phi):
     return np.imag(0.5 * ((ux - tx) ** 2 + (uy - ty) ** 2))
 
 
-def initial_state(flow: fl.Flow, logK, phi, p0=1.0, u0=(0.0, 0.0), phi_p_uniform=False):
-    """f(0) of Sec. 3.1 as a function of theta (equilibrium, then the pressure columns)."""
+def _has_walls(flow):
+    return "nee" in (flow.bc_x, flow.bc_y)
+
+
+def _equilibrium_state(flow: fl.Flow, phi, p0, u0, phi_p_uniform):
+    """f_eq(p0, u0; phi) of every cell (Eq. 22), before the boundary nodes."""
     ny, nx = flow.ny, flow.nx
     p = (p0 / phi) if phi_p_uniform else p0 + 0.0 * phi
     ux = np.full((ny, nx), float(u0[0])) + 0.0 * phi
     uy = np.full((ny, nx), float(u0[1])) + 0.0 * phi
-    f = fl.equilibrium(p, ux, uy, phi, flow.rho0)
+    return fl.equilibrium(p, ux, uy, phi, flow.rho0)
+
+
+def _boundary(f, flow, logK, phi):
+    """B = W o N: the pressure columns, then the wall nodes."""
     if flow.bc_x == "pressure":
-        f = fl.pressure_columns(f, flow, phi=phi, K=np.exp(logK))
+        f = _pressure(f, flow, logK, phi)
+    if _has_walls(flow):
+        f = _walls(f, flow, logK, phi)
     return f
 
 
-def step(f, flow, logK, phi):
-    out = fl.stream(_collide(f, flow, logK, phi), flow)
+def boundary_vjp(fs, lam, flow, logK, phi):
+    """(J_B^T lam, dB/dlogK^T lam, dB/dphi^T lam) at B's input fs: W's VJP at N(fs), then N's."""
+    glogk = np.zeros((flow.ny, flow.nx))
+    gphi = np.zeros((flow.ny, flow.nx))
+    if _has_walls(flow):
+        fN = _pressure(fs, flow, logK, phi) if flow.bc_x == "pressure" else fs
+        lam, a, b = wall_vjp(fN, lam, flow, logK, phi)
+        glogk += a
+        gphi += b
     if flow.bc_x == "pressure":
-        out = _pressure(out, flow, logK, phi)
-    return out
+        lam, a, b = pressure_vjp(fs, lam, flow, logK, phi)
+        glogk += a
+        gphi += b
+    return lam, glogk, gphi
+
+
+def initial_state(flow: fl.Flow, logK, phi, p0=1.0, u0=(0.0, 0.0), phi_p_uniform=False):
+    """f(0) of Sec. 3.1 as a function of theta (equilibrium, then the boundary nodes)."""
+    return _boundary(_equilibrium_state(flow, phi, p0, u0, phi_p_uniform), flow, logK, phi)
+
+
+def step(f, flow, logK, phi):
+    return _boundary(fl.stream(_collide(f, flow, logK, phi), flow), flow, logK, phi)
 
 
 def gradient(flow: fl.Flow, T: int, kind="flux", target=None, p0=1.0, u0=(0.0, 0.0), phi_p_uniform=False):
@@ -184,34 +253,19 @@ def gradient(flow: fl.Flow, T: int, kind="flux", target=None, p0=1.0, u0=(0.0, 0
     for t in range(T - 1, -1, -1):
         f = states[t]
         fs = fl.stream(_collide(f, flow, logK, phi), flow)
-        if flow.bc_x == "pressure":
-            lam, a, b = pressure_vjp(fs, lam, flow, logK, phi)
-            glogk += a
-            gphi += b
+        lam, a, b = boundary_vjp(fs, lam, flow, logK, phi)
+        glogk += a
+        gphi += b
         lam = stream_transpose(lam, flow)
         lam, a, b = collide_vjp(f, lam, flow, logK, phi)
         glogk += a
         gphi += b
-    # the initial state depends on theta (phi in the equilibrium, and the pressure columns)
-    if flow.bc_x != "pressure":
-        # f(0) of a cell depends on that cell's phi only (the equilibrium of Eq. 22)
-        d0 = np.imag(initial_state(flow, logK, phi + 1j * H, p0, u0, phi_p_uniform)) / H
-        gphi += np.sum(d0 * lam, axis=0)
-    else:
-        # the pressure columns couple each boundary cell to its neighbour
-        g_lk, g_ph = _initial_vjp_pressure(flow, lam, logK, phi, p0, u0, phi_p_uniform)
-        glogk += g_lk
-        gphi += g_ph
+    # the initial state f(0) = B(f_eq(theta)): the boundary nodes couple each boundary cell to its
+    # inner neighbour, then the equilibrium of a cell depends on that cell's phi only (Eq. 22)
+    f_eq = _equilibrium_state(flow, phi, p0, u0, phi_p_uniform)
+    lam, a, b = boundary_vjp(f_eq, lam, flow, logK, phi)
+    glogk += a
+    gphi += b
+    d0 = np.imag(_equilibrium_state(flow, phi + 1j * H, p0, u0, phi_p_uniform)) / H
+    gphi += np.sum(d0 * lam, axis=0)
     return L, glogk, gphi
-
-
-def _initial_vjp_pressure(flow, lam, logK, phi, p0, u0, phi_p_uniform):
-    """theta-gradient of <lam, f(0)(theta)> when f(0) includes the pressure columns: the
-    equilibrium part is per cell, then N couples boundary and neighbour columns."""
-    nx = flow.nx
-    f_eq = initial_state(fl.Flow(**{**flow.__dict__, "bc_x": "periodic"}), logK, phi, p0, u0, phi_p_uniform)
-    lam_eq, glogk, gphi = pressure_vjp(f_eq, lam, flow, logK, phi)
-    dphi_eq = np.imag(initial_state(fl.Flow(**{**flow.__dict__, "bc_x": "periodic"}), logK, phi + 1j * H, p0, u0,
-                                    phi_p_uniform)) / H
-    gphi = gphi + np.sum(dphi_eq * lam_eq, axis=0)
-    return glogk, gphi

@@ -23,6 +23,12 @@ CASES = {
     "cavity-lid-misfit": dict(nx=7, ny=6, bc_x="wall", bc_y="wall", walls={"top": (0.08, 0.0)}),
     "channel-force-flux": dict(nx=8, ny=5, bc_x="periodic", bc_y="wall", ax=2e-4),
     "pressure-flux": dict(nx=9, ny=5, bc_x="pressure", bc_y="wall", p_in=1.004, p_out=0.996),
+    # extrapolated wall nodes (Sec. 3's wall treatment) on every side, on the y sides of a
+    # force-driven channel, and with pressure columns
+    "nee-cavity-lid-misfit": dict(nx=7, ny=6, bc_x="nee", bc_y="nee", walls={"top": (0.08, 0.0)}),
+    "nee-channel-force-flux": dict(nx=8, ny=5, bc_x="periodic", bc_y="nee", ax=2e-4),
+    "nee-pressure-flux": dict(nx=9, ny=5, bc_x="pressure", bc_y="nee", p_in=1.004, p_out=0.996),
+    "nee-sides-force-misfit": dict(nx=6, ny=7, bc_x="nee", bc_y="wall", ax=2e-4, walls={"left": (0.0, 0.03)}),
 }
 
 
@@ -87,3 +93,48 @@ def test_one_step_jacobian_transpose_dot_product():
     l2 = adj.stream_transpose(l1, flow)
     JTlam, _, _ = adj.collide_vjp(f, l2, flow, logK, phi)
     assert abs(np.sum(lam * Jv) - np.sum(JTlam * v)) < 1e-10 * np.abs(np.sum(lam * Jv))
+
+
+@pytest.mark.parametrize("name", ["nee-cavity-lid-misfit", "nee-pressure-flux"])
+def test_one_step_jacobian_transpose_dot_product_wall_nodes(name):
+    """The same identity through the wall-node map W (and the pressure columns before it), whose
+    corner nodes share their inner neighbour with the wall nodes beside them."""
+    flow = _flow(**CASES[name])
+    logK, phi = np.log(flow.K), flow.phi
+    f = adj.initial_state(flow, logK, phi)
+    for _ in range(5):
+        f = adj.step(f, flow, logK, phi)
+    v = rng.standard_normal(f.shape)
+    lam = rng.standard_normal(f.shape)
+    Jv = np.imag(adj.step(f + 1e-30j * v, flow, logK, phi)) / 1e-30
+    fs = fl.stream(adj._collide(f, flow, logK, phi), flow)
+    l1, _, _ = adj.boundary_vjp(fs, lam, flow, logK, phi)
+    l2 = adj.stream_transpose(l1, flow)
+    JTlam, _, _ = adj.collide_vjp(f, l2, flow, logK, phi)
+    assert abs(np.sum(lam * Jv) - np.sum(JTlam * v)) < 1e-10 * np.abs(np.sum(lam * Jv))
+
+
+def test_wall_vjp_against_single_cell_complex_steps():
+    """wall_vjp perturbs all inner neighbours at once and scatters the result; here each entry of the
+    VJP is recomputed by perturbing one cell's input (or theta) alone: d/dx <lam, W(fs)>.  With wall
+    nodes on all four sides the inner corner node (1, 1) is the nb of three wall nodes (the corner
+    (0, 0) and its neighbours (0, 1) and (1, 0)), so a scatter that dropped a shared contribution,
+    or a wall node that kept its own adjoint, fails."""
+    flow = _flow(**CASES["nee-cavity-lid-misfit"])
+    logK, phi = np.log(flow.K), flow.phi
+    fs = fl.stream(adj._collide(adj.initial_state(flow, logK, phi), flow, logK, phi), flow)
+    lam = rng.standard_normal(fs.shape)
+    got, glk, gph = adj.wall_vjp(fs, lam, flow, logK, phi)
+    ny, nx = flow.ny, flow.nx
+    for (y, x) in [(1, 1), (1, nx - 2), (ny - 2, 1), (ny - 2, nx - 2), (2, 1), (1, 3), (3, 3), (0, 0), (0, 2), (2, 0)]:
+        for j in range(8):
+            fc = fs.astype(np.complex128)
+            fc[j, y, x] += 1e-30j
+            want = np.sum(lam * np.imag(fl.wall_nodes(fc, flow)) / 1e-30)
+            assert abs(got[j, y, x] - want) <= 1e-13 * (1 + abs(want)), ((y, x), j, got[j, y, x], want)
+        for which, g in (("logK", glk), ("phi", gph)):
+            lk = logK.astype(np.complex128)
+            ph = phi.astype(np.complex128)
+            (lk if which == "logK" else ph)[y, x] += 1e-30j
+            want = np.sum(lam * np.imag(fl.wall_nodes(fs.astype(np.complex128), flow, phi=ph, K=np.exp(lk))) / 1e-30)
+            assert abs(g[y, x] - want) <= 1e-13 * (1 + abs(want)), ((y, x), which, g[y, x], want)
