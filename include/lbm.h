@@ -59,7 +59,7 @@ extern "C" {
                          * paper's scheme, Sec. 3): f_b = f_eq(p_nb, u_w) + f_nb - f_eq(p_nb, u_nb), nb
                          * the node inward along the normal; walls at distance nx - 1 / ny - 1; a
                          * temperature wall node takes g_eq(T_w or T_nb, u_w) + g_nb - g_eq(T_nb, u_nb);
-                         * not differentiable by lbm_adjoint; needs nx, ny >= 3 */
+                         * needs nx, ny >= 3 (lbm_adjoint: >= 4 across an extrapolated side pair) */
 
 /* population streaming (lbm_config.streaming) */
 #define LBM_STREAM_AB 0u      /* two population buffers: the step pulls from one into the other */
@@ -212,9 +212,10 @@ LBM_API int lbm_residual_noalloc(const float* ux, const float* uy, const float* 
 #define LBM_LOSS_OUTLET_FLUX 0     /* L = sum_y u_x(nx-1, y) of the final state */
 #define LBM_LOSS_VELOCITY_MISFIT 1 /* L = 1/2 sum |u - u*|^2 over all cells of the final state */
 
-/* Discrete adjoint of T flow steps (collision Eq. 14, streaming Eq. 15, pressure columns) from the
- * current initial state (call right after lbm_init_equilibrium; ESTATE otherwise, and for thermal
- * contexts): runs the T steps -- the context ends at step T, as after lbm_step(ctx, T) -- and
+/* Discrete adjoint of T flow steps (collision Eq. 14, streaming Eq. 15, pressure columns and
+ * extrapolated wall nodes) from the current initial state (call right after lbm_init_equilibrium;
+ * ESTATE otherwise, and for thermal or in-place contexts; EINVAL for an LBM_NEE side pair fewer than
+ * 4 nodes apart): runs the T steps -- the context ends at step T, as after lbm_step(ctx, T) -- and
  * returns the loss and its gradient with respect to the per-cell log K and eps (phi) fields,
  * including their effect on the initial equilibrium (Eq. 22).  Memory: checkpoints of the
  * post-collision state every ceil(sqrt(T)) steps, one segment of ceil(sqrt(T)) states, two FP32

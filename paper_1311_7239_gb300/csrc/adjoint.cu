@@ -4,7 +4,9 @@
 //
 // Forward map in pre-collision variables: z(t+1) = N(P(C(z(t); theta)); theta), z(0) = N(f_eq(theta)),
 // with C the collision (Eq. 14 as d+ = d + M^-1 k, k = m+ - m), P the pull streaming with its wall
-// rules (Eq. 15) and N the pressure columns (non-equilibrium extrapolation).  The adjoint state
+// rules (Eq. 15) and N the boundary nodes: the pressure columns, then the wall nodes of the sides
+// with non-equilibrium extrapolation (Sec. 3's wall treatment), both f_b = f_eq(p_b, u_b; phi_b) +
+// f_nb - f_eq(p_nb, u_nb; phi_nb) from the inner neighbour nb.  The adjoint state
 // nu(t) = dL/dz(t) obeys nu(t) = J_C(z(t))^T P^T J_N^T nu(t+1); every piece is differentiated
 // here by hand in reverse mode:
 //   - P^T is the reversed link table (a gather of nu from x + e_i, or from the opposite slot
@@ -12,7 +14,8 @@
 //   - J_C^T mu = mu + M^T kbar, kbar = (dk/dm)^T w, w = M^-T mu, through Eq. 11-14 (m_eq, S),
 //     Eq. 3 (F), Eq. 20 (phi p) and the root of Eqs. 18-19 (u, |u|).  At |v| = 0 the derivative
 //     of |v| is taken as 0 (the one-sided limit of the smooth part of Eq. 18).
-//   - J_N^T moves the adjoint of each pressure-column cell onto its neighbour column.
+//   - J_N^T moves the adjoint of each wall node (k_adj_wall), then of each pressure-column cell
+//     (k_adj_nee), onto its inner neighbour.
 // theta enters through phi (Eq. 3, 11, 16, 19, 20 and F_phi of Eq. 4) and K (Eq. 3, 19); with
 // c_lin = phi nu / K and c_nl = phi F_phi / sqrt(K) = 1.75 / sqrt(150 phi K):
 //   dc_lin/dl = -c_lin, dc_lin/dphi = c_lin / phi, dc_nl/dl = -c_nl / 2, dc_nl/dphi = -c_nl / (2 phi).
@@ -180,15 +183,11 @@ __device__ void collide_vjp(const float z[8], const Coef& c, float ax, float ay,
   theta_bar(c, clin_b, cnl_b, ipb, phib, g_l, g_phi);
 }
 
-// pre-collision state of a cell gathered from a post-collision buffer (pressure columns included)
+// pre-collision state of a cell gathered from a post-collision buffer (wall nodes and pressure
+// columns included)
 template <int PREC, bool HET>
 __device__ __forceinline__ void gather_z(const StepParams& P, const void* buf, int x, int y, float z[8]) {
-  using T = typename Store<PREC>::T;
-  const T* src = static_cast<const T*>(buf);
-  if (P.bc_x == BC_PRESSURE && (x == 0 || x == P.nx - 1))
-    pressure_column<PREC, HET>(P, src, x, y, z);
-  else
-    pull_cell<PREC>(P, src, x, y, z);
+  gather_cell<PREC, HET>(P, static_cast<const typename Store<PREC>::T*>(buf), x, y, z);
 }
 
 // --------------------------------------------------------------------------------------------
@@ -331,6 +330,109 @@ __global__ void k_adj_nee(const StepParams P, const void* buf, float* __restrict
   }
 }
 
+// J_W^T in place on nu: the wall nodes of the extrapolated sides.  A wall node b is overwritten by
+//   W_b,i = f_eq,i(phi_b p_nb, u_w; phi_b) + z_nb,i - f_eq,i(phi_nb p_nb, u_nb; phi_nb),
+// a function of the pre-boundary state z_nb of its inner neighbour, of phi_b and of theta at nb; so
+// its adjoint is cleared and J^T lambda_b is added to nb.  A corner's nb is the diagonal node, which
+// is also the nb of the wall nodes beside the corner: one group of eight lanes (lane i holding
+// population i) per nb takes all the wall nodes that extrapolate from it, in a fixed order, so the
+// sums are race-free and deterministic.  Groups: the nb of the bottom and top walls (row 1 / ny-2,
+// with the corners and, when the x sides are extrapolated too, the side nodes of rows 1 and ny-2),
+// then the nb of the left and right walls in the remaining rows.  Needs nx >= 4 on extrapolated
+// x sides and ny >= 4 on extrapolated y sides (no nb on two sides at once, no nb that is a wall node).
+struct WallGroups {
+  int gy, gx, row0;  // groups per y side (bottom, top), per x side (left, right), first row of the x groups
+};
+
+__host__ __device__ inline WallGroups wall_groups(const StepParams& P) {
+  WallGroups g;
+  g.gy = P.bc_y == BC_NEE ? (P.bc_x == BC_PERIODIC ? P.nx : P.nx - 2) : 0;
+  g.row0 = P.bc_y == BC_NEE ? 2 : 0;
+  g.gx = P.bc_x == BC_NEE ? (P.bc_y == BC_NEE ? P.ny - 4 : P.ny) : 0;
+  return g;
+}
+
+template <int PREC, bool HET>
+__global__ void k_adj_wall(const StepParams P, const void* buf, WallGroups G, float* __restrict__ nu, float* __restrict__ g_l,
+                           float* __restrict__ g_phi) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int grp = t >> 3;
+  const int i = t & 7;
+  if (grp >= 2 * (G.gy + G.gx)) return;  // whole lane groups leave together
+  const unsigned gm = 0xffu << (threadIdx.x & 24);
+  // the nb (xt, yt) of this group and the wall nodes (bx, by) on walls bw that extrapolate from it
+  int xt, yt, n = 0;
+  int bx[3], by[3], bw[3];
+  if (grp < 2 * G.gy) {
+    const int top = grp >= G.gy, g = grp - (top ? G.gy : 0);
+    xt = P.bc_x == BC_PERIODIC ? g : g + 1;
+    yt = top ? P.ny - 2 : 1;
+    const int yw = top ? P.ny - 1 : 0, w = top ? 3 : 2;
+    bx[n] = xt; by[n] = yw; bw[n++] = w;
+    if (P.bc_x != BC_PERIODIC && xt == 1) { bx[n] = 0; by[n] = yw; bw[n++] = w; }
+    if (P.bc_x != BC_PERIODIC && xt == P.nx - 2) { bx[n] = P.nx - 1; by[n] = yw; bw[n++] = w; }
+    if (P.bc_x == BC_NEE && xt == 1) { bx[n] = 0; by[n] = yt; bw[n++] = 0; }
+    if (P.bc_x == BC_NEE && xt == P.nx - 2) { bx[n] = P.nx - 1; by[n] = yt; bw[n++] = 1; }
+  } else {
+    grp -= 2 * G.gy;
+    const int right = grp >= G.gx;
+    yt = G.row0 + grp - (right ? G.gx : 0);
+    xt = right ? P.nx - 2 : 1;
+    bx[n] = right ? P.nx - 1 : 0; by[n] = yt; bw[n++] = right ? 1 : 0;
+  }
+  using T = typename Store<PREC>::T;
+  const float ex = (float)ex_of(i), ey = (float)ey_of(i), wi = w_of(i);
+  const float rho0 = P.rho0;
+  // forward quantities at nb: u_nb (Eqs. 18-19), phi_nb p_nb (Eq. 20)
+  const float zi = pull_one<PREC>(P, static_cast<const T*>(buf), xt, yt, i);
+  const Coef cn = coef_at<HET>(P, xt, yt);
+  const float jx = group8_sum(ex * zi, gm), jy = group8_sum(ey * zi, gm), m1 = group8_sum(zi, gm);
+  float ux, uy, umag;
+  velocity_from_j(jx, jy, cn, P.ax, P.ay, P.inv_rho0, ux, uy, umag);
+  const float usq = ux * ux + uy * uy;
+  const float Pn = P.p_rest + 0.6f * m1 - 0.4f * rho0 * usq * cn.inv_phi;  // phi_nb p_nb
+  const float eun = ex * ux + ey * uy;
+  // adjoints at nb, summed over the wall nodes: z_nb,i, phi_nb p_nb, 1/phi_nb, u_nb
+  float zbar = 0.0f, Pn_b = 0.0f, ipn_b = 0.0f, ubx = 0.0f, uby = 0.0f;
+  for (int k = 0; k < n; ++k) {
+    const int64_t ob = (int64_t)by[k] * P.pitch + bx[k];
+    const float lam = nu[i * P.plane + ob];
+    nu[i * P.plane + ob] = 0.0f;
+    const Coef cb = coef_at<HET>(P, bx[k], by[k]);
+    const float uwx = __ldg(P.uw + 2 * bw[k]), uwy = __ldg(P.uw + 2 * bw[k] + 1);
+    const float euw = ex * uwx + ey * uwy;
+    const float wl = wi * lam;
+    const float W = group8_sum(wl, gm);
+    const float WAw = group8_sum(wl * (4.5f * euw * euw - 1.5f * (uwx * uwx + uwy * uwy)), gm);
+    const float WAn = group8_sum(wl * (4.5f * eun * eun - 1.5f * usq), gm);
+    const float gux = group8_sum(wl * (3.0f * ex + (9.0f * eun * ex - 3.0f * ux) * cn.inv_phi), gm);
+    const float guy = group8_sum(wl * (3.0f * ey + (9.0f * eun * ey - 3.0f * uy) * cn.inv_phi), gm);
+    // phi_b p_nb = (1 + r) phi_nb p_nb with r = phi_b / phi_nb - 1
+    const float r = cb.phi * cn.inv_phi - 1.0f;
+    zbar += lam;
+    Pn_b += 3.0f * r * W;
+    const float r_b = 3.0f * W * Pn;
+    ipn_b += r_b * cb.phi - rho0 * WAn;
+    ubx += -rho0 * gux;
+    uby += -rho0 * guy;
+    if (i == 0) g_phi[ob] += r_b * cn.inv_phi - cb.inv_phi * cb.inv_phi * rho0 * WAw;  // phi_b through r and 1/phi_b
+  }
+  // phi_nb p_nb (deviation) = 0.6 m1 - 0.4 rho0 |u|^2 / phi_nb
+  const float mb1 = 0.6f * Pn_b;
+  ubx += -0.8f * rho0 * ux * cn.inv_phi * Pn_b;
+  uby += -0.8f * rho0 * uy * cn.inv_phi * Pn_b;
+  ipn_b += -0.4f * rho0 * usq * Pn_b;
+  const VelBar vb = velocity_vjp(jx, jy, cn, P.ax, P.ay, P.inv_rho0, ubx, uby, 0.0f);
+  const int64_t on = (int64_t)yt * P.pitch + xt;
+  nu[i * P.plane + on] += zbar + mb1 + ex * vb.jx + ey * vb.jy;
+  if (i == 0) {
+    float gl = 0.0f, gp = 0.0f;
+    theta_bar(cn, vb.clin, vb.cnl, ipn_b, vb.phi, gl, gp);
+    g_l[on] += gl;
+    g_phi[on] += gp;
+  }
+}
+
 // nu(t) = J_C(z(t))^T P^T nu~(t+1), gradient += (dC/dtheta)^T P^T nu~(t+1); z(t) gathered from
 // buf = b(t).  Generic form for one cell (frame cells): every boundary rule.
 template <int PREC, bool HET>
@@ -459,7 +561,7 @@ __device__ __forceinline__ void adj_item(const StepParams& P, const void* buf, c
   gather2<PREC_FP32, 1>(nu_in + 5 * pl + rp, xl, P.pitch, lane, 1.0f, mu[5]);   // e6 = (-1, 1)
   gather2<PREC_FP32, 1>(nu_in + 6 * pl + rm, xl, P.pitch, lane, 1.0f, mu[6]);   // e7 = (-1,-1)
   gather2<PREC_FP32, -1>(nu_in + 7 * pl + rm, xl, P.pitch, lane, 1.0f, mu[7]);  // e8 = ( 1,-1)
-  const bool wall_row = P.bc_y == BC_WALL && (y == 0 || y == P.ny - 1);
+  const bool wall_row = (P.bc_y == BC_WALL || P.bc_y == BC_NEE) && (y == 0 || y == P.ny - 1);
   if (!has_pair || !idx_ok || wall_row || x0 < kCellsPerThread || x0 >= tl.frame_x1) return;
   float gl[2], gp[2];
 #pragma unroll
@@ -555,6 +657,18 @@ cudaError_t launch_adj_nee(const StepParams& P, int prec, bool het, const void* 
 #define CALL_NEE(PR, H) k_adj_nee<PR, H><<<blocks, 128, 0, s>>>(P, buf, nu, g_l, g_phi)
   LBM_ADJ_DISPATCH(prec, het, CALL_NEE);
 #undef CALL_NEE
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_wall(const StepParams& P, int prec, bool het, const void* buf, float* nu, float* g_l, float* g_phi,
+                            cudaStream_t s) {
+  const WallGroups G = wall_groups(P);
+  const int threads = 8 * 2 * (G.gy + G.gx);
+  if (threads == 0) return cudaSuccess;
+  const int blocks = (threads + 127) / 128;
+#define CALL_WALL(PR, H) k_adj_wall<PR, H><<<blocks, 128, 0, s>>>(P, buf, G, nu, g_l, g_phi)
+  LBM_ADJ_DISPATCH(prec, het, CALL_WALL);
+#undef CALL_WALL
   return cudaGetLastError();
 }
 

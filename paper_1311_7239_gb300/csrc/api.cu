@@ -890,8 +890,8 @@ int lbm_adjoint(lbm_ctx* c, int T, int loss_kind, const float* target_ux, const 
   if (loss_kind == LBM_LOSS_VELOCITY_MISFIT && (!target_ux || !target_uy)) return fail(LBM_EINVAL, "misfit loss needs a target");
   if (thermal_of(c)) return fail(LBM_ESTATE, "the adjoint covers the isothermal flow step only");
   if (c->inplace) return fail(LBM_ESTATE, "the adjoint needs A-B streaming (its checkpoints are A-B states)");
-  if (c->cfg.bc_x == LBM_NEE || c->cfg.bc_y == LBM_NEE)
-    return fail(LBM_ESTATE, "the adjoint covers halfway walls, periodic sides and pressure columns, not extrapolated wall nodes");
+  if ((c->cfg.bc_x == LBM_NEE && c->cfg.nx < 4) || (c->cfg.bc_y == LBM_NEE && c->cfg.ny < 4))
+    return fail(LBM_EINVAL, "the adjoint through extrapolated wall nodes needs at least 4 nodes across each such side pair");
   if (c->steps != 0 || c->history != 0)
     return fail(LBM_ESTATE, "lbm_adjoint differentiates from the initial state: call lbm_init_equilibrium first");
   const int64_t n = (int64_t)c->cfg.nx * c->cfg.ny;
@@ -945,6 +945,9 @@ int lbm_adjoint(lbm_ctx* c, int T, int loss_kind, const float* target_ux, const 
   const int nb = residual_blocks((int)c->cfg.nx, (int)c->cfg.ny);
   double* loss_dev = c->red + 2 * kResidualMaxBlocks;
   LBM_CUDA(launch_adj_seed(P, c->prec, c->het, nu[0], hl, hp, loss_kind, tux, tuy, c->red, nb, loss_dev, c->stream), "adjoint seed");
+  const bool walls = c->cfg.bc_x == LBM_NEE || c->cfg.bc_y == LBM_NEE;
+  // J_N^T of the boundary nodes N = (wall nodes) o (pressure columns): wall nodes first
+  if (walls) LBM_CUDA(launch_adj_wall(P, c->prec, c->het, c->f[c->cur], nu[0], hl, hp, c->stream), "adjoint wall nodes");
   if (pressure) LBM_CUDA(launch_adj_nee(P, c->prec, c->het, c->f[c->cur], nu[0], hl, hp, c->stream), "adjoint pressure columns");
   int cur_nu = 0, unfolded = 1;
   constexpr int kAdjFold = 64;  // at most this many per-step terms in an FP32 partial sum
@@ -961,6 +964,7 @@ int lbm_adjoint(lbm_ctx* c, int T, int loss_kind, const float* target_ux, const 
       const void* buf = seg[t - t0];
       LBM_CUDA(launch_adj_step(P, c->prec, c->het, buf, nu[cur_nu], nu[cur_nu ^ 1], hl, hp, c->stream), "adjoint step");
       cur_nu ^= 1;
+      if (walls) LBM_CUDA(launch_adj_wall(P, c->prec, c->het, buf, nu[cur_nu], hl, hp, c->stream), "adjoint wall nodes");
       if (pressure) LBM_CUDA(launch_adj_nee(P, c->prec, c->het, buf, nu[cur_nu], hl, hp, c->stream), "adjoint pressure columns");
       if (++unfolded == kAdjFold) {
         LBM_CUDA(launch_adj_fold(hl, hp, gl, gp, c->plane, c->stream), "gradient fold");

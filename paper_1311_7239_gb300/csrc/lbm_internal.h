@@ -60,6 +60,8 @@ cudaError_t launch_nusselt(const StepParams& P, int prec, int side, double* out,
 
 cudaError_t launch_adj_seed(const StepParams& P, int prec, bool het, float* nu_out, float* g_l, float* g_phi, int kind,
                             const float* tux, const float* tuy, double* partial, int nblocks, double* loss_out, cudaStream_t s);
+cudaError_t launch_adj_wall(const StepParams& P, int prec, bool het, const void* buf, float* nu, float* g_l, float* g_phi,
+                            cudaStream_t s);
 cudaError_t launch_adj_nee(const StepParams& P, int prec, bool het, const void* buf, float* nu, float* g_l, float* g_phi,
                            cudaStream_t s);
 cudaError_t launch_adj_step(const StepParams& P, int prec, bool het, const void* buf, const float* nu_in, float* nu_out, float* g_l,

@@ -65,6 +65,17 @@ CASES = {
     # rows longer than one work item (150 cell pairs > 128 threads): the split-row tiling
     "long-row-pressure-channel": (Case(300, 8, nu=0.1, phi=0.35, K=0.05 * 8 * 8, het=True, eps_sd=0.03, corr=8.0, bc_x="pressure",
                                        bc_y="wall", p_in=1.001, p_out=0.999), 12, "flux", True),
+    # extrapolated wall nodes (Sec. 3's wall treatment): on all four sides, where each inner corner
+    # node is the nb of three wall nodes; on the y sides of pressure-driven and force-driven
+    # channels; and on split rows
+    "nee-lid-cavity-misfit": (Case(24, 20, nu=0.06, phi=0.5, K=4.0, het=True, eps_sd=0.05, corr=4.0, bc_x="nee", bc_y="nee",
+                                   walls={"top": (0.08, 0.0)}), 40, "misfit", False),
+    "nee-pressure-channel-flux": (Case(64, 32, nu=0.1, phi=0.35, K=0.05 * 32 * 32, het=True, eps_sd=0.03, corr=8.0,
+                                       bc_x="pressure", bc_y="nee", p_in=1.003, p_out=0.997), 60, "flux", True),
+    "nee-forced-channel-flux": (Case(20, 16, nu=0.08, phi=0.4, K=6.0, het=True, eps_sd=0.05, corr=4.0, ax=3e-4, bc_y="nee"), 30,
+                                "flux", False),
+    "nee-long-row-cavity-misfit": (Case(300, 8, nu=0.1, phi=0.5, K=4.0, het=True, eps_sd=0.05, corr=4.0, bc_x="nee", bc_y="nee",
+                                        walls={"top": (0.05, 0.0), "left": (0.0, 0.02)}), 12, "misfit", False),
 }
 
 
