@@ -67,9 +67,11 @@ extern "C" {
                                * slots it read, each slot receiving the opposite population; populations
                                * leaving through a wall are parked in one ghost row below and above and one
                                * ghost column right of the lattice).  Same arithmetic and results as
-                               * LBM_STREAM_AB with half the population memory.  Sides: LBM_PERIODIC and
-                               * LBM_WALL only (the extrapolated sides read a neighbour's state while it is
-                               * being overwritten); not for lbm_adjoint or batches.  The last step of each
+                               * LBM_STREAM_AB with half the population memory.  All sides; with LBM_NEE or
+                               * LBM_PRESSURE sides each step first computes the boundary nodes' states
+                               * (one small extra launch; 4 (8 or 13) (nx + ny) bytes kept), since a
+                               * boundary node reads a neighbour that the step overwrites.  Not for
+                               * lbm_adjoint; batches: LBM_PERIODIC and LBM_WALL sides only.  The last step of each
                                * lbm_step call records the velocity of its collisions, u(t-1) for
                                * lbm_residual (8 B per cell kept and written once per call), unless
                                * LBM_OPT_NO_RESIDUAL_RECORD is set.  Limit:

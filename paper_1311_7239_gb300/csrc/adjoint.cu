@@ -380,6 +380,7 @@ __global__ void k_adj_wall(const StepParams P, const void* buf, WallGroups G, fl
     xt = right ? P.nx - 2 : 1;
     bx[n] = right ? P.nx - 1 : 0; by[n] = yt; bw[n++] = right ? 1 : 0;
   }
+  if (!dbg_check(P, xt >= 0 && xt < P.nx && yt >= 0 && yt < P.ny)) return;  // uniform over the lane group
   using T = typename Store<PREC>::T;
   const float ex = (float)ex_of(i), ey = (float)ey_of(i), wi = w_of(i);
   const float rho0 = P.rho0;
@@ -395,6 +396,7 @@ __global__ void k_adj_wall(const StepParams P, const void* buf, WallGroups G, fl
   // adjoints at nb, summed over the wall nodes: z_nb,i, phi_nb p_nb, 1/phi_nb, u_nb
   float zbar = 0.0f, Pn_b = 0.0f, ipn_b = 0.0f, ubx = 0.0f, uby = 0.0f;
   for (int k = 0; k < n; ++k) {
+    if (!dbg_check(P, bx[k] >= 0 && bx[k] < P.nx && by[k] >= 0 && by[k] < P.ny)) continue;
     const int64_t ob = (int64_t)by[k] * P.pitch + bx[k];
     const float lam = nu[i * P.plane + ob];
     nu[i * P.plane + ob] = 0.0f;

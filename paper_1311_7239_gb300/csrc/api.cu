@@ -135,6 +135,7 @@ struct lbm_ctx {
   bool inplace = false;          // one buffer (f[0], g[0]) with rows -1..ny and a ghost column; see ip_off
   size_t fbytes = 0, gbytes = 0; // bytes of one flow / temperature population buffer
   float* uprev = nullptr;        // in-place: u before the last step of the last lbm_step call, [2][ny][nx]
+  float* edge = nullptr;         // in-place with extrapolated sides: boundary-node states of the coming step
   float* phi = nullptr;
   float* K = nullptr;
   float* sv = nullptr;  // per-cell viscous rate (heterogeneous mode), when a viscosity-ratio field is set
@@ -293,6 +294,7 @@ StepParams params_for(const lbm_ctx* c, bool forward_dst = true) {
   P.phi = c->het ? c->phi : nullptr;
   P.K = c->het ? c->K : nullptr;
   P.sv = c->het ? c->sv : nullptr;
+  P.edge = c->inplace ? c->edge : nullptr;
   (void)forward_dst;
   return P;
 }
@@ -328,8 +330,6 @@ int validate_config(const lbm_config* c) {
   if (c->dev_scale_log2 < -30 || c->dev_scale_log2 > 30) return fail(LBM_EINVAL, "dev_scale_log2 out of [-30, 30]");
   if (c->streaming > LBM_STREAM_INPLACE) return fail(LBM_EINVAL, "unknown streaming mode %u", c->streaming);
   if (c->options & ~LBM_OPT_NO_RESIDUAL_RECORD) return fail(LBM_EINVAL, "unknown option bits %#x", c->options);
-  if (c->streaming == LBM_STREAM_INPLACE && (c->bc_x > LBM_WALL || c->bc_y > LBM_WALL))
-    return fail(LBM_EINVAL, "in-place streaming supports periodic and halfway-wall sides only");
   if (c->thermal) {
     if (!(c->tau_T > 0.5) || !(c->sigma > 0)) return fail(LBM_EINVAL, "tau_T must exceed 1/2 and sigma be positive");
     if (!(c->zeta3 > 0 && c->zeta3 < 2) || !(c->zeta4 > 0 && c->zeta4 < 2)) return fail(LBM_EINVAL, "zeta3, zeta4 in (0, 2)");
@@ -367,6 +367,7 @@ void release(lbm_ctx* c) {
   cudaFree(c->K);
   cudaFree(c->sv);
   cudaFree(c->uprev);
+  cudaFree(c->edge);
   cudaFree(c->err);
   cudaFree(c->walls);
   cudaFree(c->probe);
@@ -454,6 +455,9 @@ int lbm_create(const lbm_config* cfg, lbm_ctx** out) {
   }
   if (rc == LBM_OK && c->inplace && !(cfg->options & LBM_OPT_NO_RESIDUAL_RECORD))
     rc = dev_alloc(c, reinterpret_cast<void**>(&c->uprev), 2 * (size_t)cfg->nx * cfg->ny * sizeof(float), "cudaMalloc(previous velocity)");
+  if (rc == LBM_OK && c->inplace && (cfg->bc_x == LBM_PRESSURE || cfg->bc_x == LBM_NEE || cfg->bc_y == LBM_NEE))
+    rc = dev_alloc(c, reinterpret_cast<void**>(&c->edge), (cfg->thermal ? 13 : 8) * 2 * ((size_t)cfg->nx + cfg->ny) * sizeof(float),
+                   "cudaMalloc(boundary-node states)");
   if (rc == LBM_OK) rc = dev_alloc(c, reinterpret_cast<void**>(&c->err), sizeof(unsigned int), "cudaMalloc(error word)");
   if (rc == LBM_OK)
     rc = dev_alloc(c, reinterpret_cast<void**>(&c->red), (2 * kResidualMaxBlocks + 2) * sizeof(double), "cudaMalloc(reduction)");

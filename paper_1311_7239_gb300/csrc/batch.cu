@@ -242,6 +242,8 @@ int lbm_batch_create(const lbm_config* cfgs, int n, lbm_batch** out) {
     if (rc) return rc;
     if (cfgs[d].thermal) return fail_msg(LBM_EINVAL, "lbm_batch_create: batches hold isothermal lattices only");
     if (cfgs[d].streaming != cfgs[0].streaming) return fail_msg(LBM_EINVAL, "lbm_batch_create: all lattices need one streaming form");
+    if (cfgs[d].streaming == LBM_STREAM_INPLACE && (cfgs[d].bc_x > LBM_WALL || cfgs[d].bc_y > LBM_WALL))
+      return fail_msg(LBM_EINVAL, "lbm_batch_create: in-place batches take periodic and halfway-wall sides only");
     if (cfgs[d].precision != cfgs[0].precision) return fail_msg(LBM_EINVAL, "lbm_batch_create: all lattices need one precision");
   }
   lbm_batch* b = new (std::nothrow) lbm_batch();

@@ -29,18 +29,112 @@ __device__ __forceinline__ void record_u(const StepParams& P, int x, int y, floa
   P.urec[(int64_t)P.nx * P.ny + o] = uy;
 }
 
-// one cell with the generic slot rules: pulls with bounce-back, collision, stores into the slots
-// of the next parity (ghost slots for populations that leave through a wall)
+// Extrapolated sides (wall nodes and pressure columns): a boundary node's pre-collision state is
+// a function of its inner neighbour's, which that neighbour's own update overwrites in the same
+// pass.  So k_edge_ip computes the states of all boundary nodes of the coming step first (the
+// rules of gather_cell / gather_cell_thermal on the unchanged buffer) into FP32 planes
+// [8 (+5)][2 (nx + ny)], and the step reads them from there; the node's own slots are written as
+// any cell's.  Plane index of a boundary node: bottom row x, top row nx + x, left column (rows
+// 1..ny-2) 2 nx + y, right column 2 nx + ny + y.
+__device__ __forceinline__ int edge_index(const StepParams& P, int x, int y) {
+  if (y == 0) return x;
+  if (y == P.ny - 1) return P.nx + x;
+  return 2 * P.nx + (x == 0 ? y : P.ny + y);
+}
+
+__device__ __forceinline__ bool boundary_node(const StepParams& P, int x, int y) {
+  int xn, yn, w;
+  return nee_node(P, x, y, xn, yn, w) || (P.bc_x == BC_PRESSURE && (x == 0 || x == P.nx - 1));
+}
+
+// Eight lanes per boundary node, lane i pulling population i (and temperature population i < 5) of
+// the node's inner neighbour, so that the scattered loads of a node are in flight together; the
+// pulled state is then shared within the lane group and every lane applies the node's rule to the
+// whole state (the functions gather_cell uses, so the result is bitwise that of the A-B form) and
+// stores its own population.
+template <int PREC, bool HET, bool THERMAL>
+__global__ void k_edge_ip(const StepParams P) {
+  using T = typename Store<PREC>::T;
+  const int n = 2 * (P.nx + P.ny);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = t >> 3, lane = t & 7;
+  if (k >= n) return;  // whole lane groups leave together (as below: x, y and the rule depend on k only)
+  int x, y;
+  if (k < 2 * P.nx) {
+    if (k >= P.nx && P.ny == 1) return;  // one row: the bottom range has it
+    y = k < P.nx ? 0 : P.ny - 1;
+    x = k < P.nx ? k : k - P.nx;
+  } else {
+    const int r = k - 2 * P.nx;
+    x = r < P.ny ? 0 : P.nx - 1;
+    y = r < P.ny ? r : r - P.ny;
+    if (y == 0 || y == P.ny - 1) return;  // the rows' ranges have the corners
+  }
+  int xn, yn, w;
+  const bool wall = nee_node(P, x, y, xn, yn, w);
+  if (!wall) {
+    if (!(P.bc_x == BC_PRESSURE && (x == 0 || x == P.nx - 1))) return;
+    xn = x == 0 ? 1 : P.nx - 2;
+    yn = y;
+  }
+  const unsigned gm = 0xffu << (threadIdx.x & 24);
+  const int base = threadIdx.x & 24;
+  const float zi = pull_one<PREC>(P, static_cast<const T*>(P.src), xn, yn, lane);
+  // temperature: a wall node extrapolates from nb, a pressure column keeps its own pulled state
+  const float gi = (THERMAL && lane < 5) ? pull_one_g<PREC>(P, static_cast<const T*>(P.gsrc), wall ? xn : x, wall ? yn : y, lane) : 0.0f;
+  float dn[8], gn[5], d[8], g[5];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) dn[j] = __shfl_sync(gm, zi, base + j);
+  if (THERMAL) {
+#pragma unroll
+    for (int j = 0; j < 5; ++j) gn[j] = __shfl_sync(gm, gi, base + j);
+  }
+  if (wall) {
+    if (THERMAL) {
+      thermal_wall_node_from<HET>(P, dn, gn, x, y, xn, yn, w, d, g);
+    } else {
+      float ux, uy;
+      wall_node_from<HET>(P, dn, x, y, xn, yn, w, P.ay, d, ux, uy);
+    }
+  } else {
+    pressure_column_from<HET>(P, dn, x, y, d);
+    if (THERMAL) {
+#pragma unroll
+      for (int j = 0; j < 5; ++j) g[j] = gn[j];
+    }
+  }
+  float dv = d[0], gv = THERMAL ? g[0] : 0.0f;
+#pragma unroll
+  for (int j = 1; j < 8; ++j) dv = lane == j ? d[j] : dv;
+  if (THERMAL) {
+#pragma unroll
+    for (int j = 1; j < 5; ++j) gv = lane == j ? g[j] : gv;
+  }
+  P.edge[lane * n + k] = dv;
+  if (THERMAL && lane < 5) P.edge[(8 + lane) * n + k] = gv;
+}
+
+// one cell with the generic slot rules: pulls with bounce-back (or, for a boundary node of an
+// extrapolated side, the state k_edge_ip computed), collision, stores into the slots of the next
+// parity (ghost slots for populations that leave through a wall)
 template <int PREC, bool HET, bool THERMAL, bool REC>
 __device__ __noinline__ void ip_cell(const StepParams& P, typename Store<PREC>::T* A, typename Store<PREC>::T* G, int x, int y) {
   using S = Store<PREC>;
   float d[8], g[5];
-  pull_cell<PREC>(P, A, x, y, d);
-  float ay = P.ay;
-  if (THERMAL) {
-    pull_cell_g<PREC>(P, G, x, y, g);
-    ay += P.g_beta * (g[0] + g[1] + g[2] + g[3] + g[4]);  // a = g beta (T - T0) j
+  if (P.edge && boundary_node(P, x, y)) {
+    const int n = 2 * (P.nx + P.ny), e = edge_index(P, x, y);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) d[i] = P.edge[i * n + e];
+    if (THERMAL) {
+#pragma unroll
+      for (int i = 0; i < 5; ++i) g[i] = P.edge[(8 + i) * n + e];
+    }
+  } else {
+    pull_cell<PREC>(P, A, x, y, d);
+    if (THERMAL) pull_cell_g<PREC>(P, G, x, y, g);
   }
+  float ay = P.ay;
+  if (THERMAL) ay += P.g_beta * (g[0] + g[1] + g[2] + g[3] + g[4]);  // a = g beta (T - T0) j
   const Coef cf = coef_at<HET>(P, x, y);
   float ux, uy, phip;
   collide_d2q8(d, cf, P.ax, ay, P, ux, uy, phip);
@@ -98,9 +192,9 @@ __device__ __forceinline__ constexpr int plane_of(int i) {
 }
 
 // Cells of the frame, the groups with a cell on a wall or on the last column (see k_step_ip):
-// whole wall rows (y = 0 and ny - 1 when the y sides are walls), and in the other rows the cells
-// x < L (the first group, when the x sides are walls) and x >= R (the groups that reach column
-// nx - 1 through their right neighbours).
+// whole wall rows (y = 0 and ny - 1 when the y sides are not periodic), and in the other rows the
+// cells x < L (the first group, when the x sides are not periodic) and x >= R (the groups that
+// reach column nx - 1 through their right neighbours).
 struct IpFrame {
   int L, R, E, wall_rows;
   int64_t total;
@@ -108,11 +202,11 @@ struct IpFrame {
 
 __host__ __device__ __forceinline__ IpFrame ip_frame_of(int nx, int ny, int bc_x, int bc_y) {
   IpFrame F;
-  F.L = bc_x == BC_WALL ? (nx < 4 ? nx : 4) : 0;
+  F.L = bc_x != BC_PERIODIC ? (nx < 4 ? nx : 4) : 0;
   const int x0e = nx <= 4 ? 0 : (nx - 1) / 4 * 4;  // first group start with x0 + 4 >= nx
   F.R = x0e > F.L ? x0e : F.L;
   F.E = F.L + (nx - F.R);
-  F.wall_rows = bc_y == BC_WALL ? 2 : 0;
+  F.wall_rows = bc_y != BC_PERIODIC ? 2 : 0;
   F.total = (int64_t)F.wall_rows * nx + (int64_t)(ny - F.wall_rows) * F.E;
   return F;
 }
@@ -159,7 +253,7 @@ __device__ __forceinline__ void ip_block(const StepParams& P, int frame_blocks, 
   const int y = b / gx;
   const int x0 = ((b - y * gx) * kIpThreads + (int)threadIdx.x) * C;
   if (x0 >= P.nx || !dbg_check(P, y < P.ny)) return;
-  const bool edge = (P.bc_x == BC_WALL && x0 == 0) || x0 + C >= P.nx || (P.bc_y == BC_WALL && (y == 0 || y == P.ny - 1));
+  const bool edge = (P.bc_x != BC_PERIODIC && x0 == 0) || x0 + C >= P.nx || (P.bc_y != BC_PERIODIC && (y == 0 || y == P.ny - 1));
   if (edge) return;  // a frame group
   // rows y - 1 and y + 1 (periodic wrap; wall rows are frame rows)
   const int ym = y == 0 ? P.ny - 1 : y - 1;
@@ -318,6 +412,10 @@ static cudaError_t launch_ip_t(const StepParams& P, cudaStream_t s) {
   const int groups = (P.nx + kIpCells - 1) / kIpCells;
   const int gx = (groups + kIpThreads - 1) / kIpThreads;
   const long long blocks = (long long)frame_blocks + (long long)gx * P.ny;
+  if (P.edge) {  // the boundary nodes' states, before the step overwrites their neighbours' slots
+    const int64_t threads = 8 * 2 * ((int64_t)P.nx + P.ny);
+    k_edge_ip<PREC, HET, THERMAL><<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(P);
+  }
   // the variant that records u runs once per lbm_step call
   if (P.urec) {
     if (P.parity)

@@ -68,6 +68,7 @@ struct StepParams {
   int Tdir[4];        // 1 = wall temperature prescribed, 0 = adiabatic
   unsigned int* err;  // bit 0: non-finite velocity
   float* urec;        // in-place step: if set, the velocity of every cell's collision, dense [2][ny][nx]
+  float* edge;        // in-place step with extrapolated sides: pre-collision states of the boundary nodes (see k_edge_ip)
   PairConst pc;
 };
 
@@ -545,8 +546,9 @@ __device__ __forceinline__ int wall_of(int sx, int sy, int ny) {
 // wall are parked in ghost slots (rows -1 and ny, column nx; never updated as cells) until the
 // same cell reads them back as its bounce-back (Eq. 15 at a wall).  Ghost rows -1 and ny are rows of
 // the planes; the ghost column lives after the last plane, q columns of ny + 2 slots (so that a
-// lattice width that is a multiple of the row pitch needs no wider rows).  Only periodic and
-// halfway-wall sides are supported.
+// lattice width that is a multiple of the row pitch needs no wider rows).  Extrapolated sides (wall
+// nodes, pressure columns) keep the slot rules of a halfway wall; their boundary nodes' states are
+// computed before each step (k_edge_ip), since they read a neighbour that the step overwrites.
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ bool ip_positive(int i) { return i == 0 || i == 1 || i == 4 || i == 7; }
 
@@ -674,12 +676,11 @@ __device__ __forceinline__ void pull_cell_g(const StepParams& P, const typename 
 
 // Non-equilibrium extrapolation of a pressure column: replaces d of the cell (xb, y) by
 // f_eq(p_b, u_nb; phi_b) + f_nb - f_eq(p_nb, u_nb; phi_nb) with nb = (xb +- 1, y), in deviations.
-template <int PREC, bool HET>
-__device__ __forceinline__ void pressure_column(const StepParams& P, const typename Store<PREC>::T* src, int xb, int y, float d[8]) {
+// (dn: the pulled state of nb)
+template <bool HET>
+__device__ __forceinline__ void pressure_column_from(const StepParams& P, const float dn[8], int xb, int y, float d[8]) {
   const int xn = xb == 0 ? 1 : P.nx - 2;
   const float pb = xb == 0 ? P.p_in : P.p_out;
-  float dn[8];
-  pull_cell<PREC>(P, src, xn, y, dn);
   const Coef cn = coef_at<HET>(P, xn, y);
   const Coef cb = coef_at<HET>(P, xb, y);
   const Macro mn = macro_d2q8(dn, cn, P.ax, P.ay, P.rho0);
@@ -688,6 +689,13 @@ __device__ __forceinline__ void pressure_column(const StepParams& P, const typen
   feq_dev_d2q8(mn.phip_dev, mn.ux, mn.uy, cn.inv_phi, P.rho0, en);
 #pragma unroll
   for (int i = 0; i < 8; ++i) d[i] = eb[i] + dn[i] - en[i];
+}
+
+template <int PREC, bool HET>
+__device__ __forceinline__ void pressure_column(const StepParams& P, const typename Store<PREC>::T* src, int xb, int y, float d[8]) {
+  float dn[8];
+  pull_cell<PREC>(P, src, xb == 0 ? 1 : P.nx - 2, y, dn);
+  pressure_column_from<HET>(P, dn, xb, y, d);
 }
 
 // Wall node of a side with non-equilibrium extrapolation (BC_NEE, the paper's wall treatment of
@@ -712,12 +720,10 @@ __device__ __forceinline__ bool nee_node(const StepParams& P, int x, int y, int&
 
 // d of a wall node: f_eq(p_nb, u_w; phi_b) + f_nb - f_eq(p_nb, u_nb; phi_nb) (pressure extrapolated
 // with zero normal gradient), in deviations; ay_nb is a_y at nb (with its buoyancy in a thermal
-// context), u_nb is returned.
-template <int PREC, bool HET>
-__device__ __forceinline__ void wall_node(const StepParams& P, const typename Store<PREC>::T* src, int x, int y, int xn, int yn,
-                                          int w, float ay_nb, float d[8], float& ux_nb, float& uy_nb) {
-  float dn[8];
-  pull_cell<PREC>(P, src, xn, yn, dn);
+// context), u_nb is returned; dn is the pulled state of nb.
+template <bool HET>
+__device__ __forceinline__ void wall_node_from(const StepParams& P, const float dn[8], int x, int y, int xn, int yn, int w, float ay_nb,
+                                               float d[8], float& ux_nb, float& uy_nb) {
   const Coef cn = coef_at<HET>(P, xn, yn);
   const Coef cb = coef_at<HET>(P, x, y);
   const Macro mn = macro_d2q8(dn, cn, P.ax, ay_nb, P.rho0);
@@ -732,6 +738,14 @@ __device__ __forceinline__ void wall_node(const StepParams& P, const typename St
   feq_dev_d2q8(mn.phip_dev, mn.ux, mn.uy, cn.inv_phi, P.rho0, en);
 #pragma unroll
   for (int i = 0; i < 8; ++i) d[i] = eb[i] + dn[i] - en[i];
+}
+
+template <int PREC, bool HET>
+__device__ __forceinline__ void wall_node(const StepParams& P, const typename Store<PREC>::T* src, int x, int y, int xn, int yn,
+                                          int w, float ay_nb, float d[8], float& ux_nb, float& uy_nb) {
+  float dn[8];
+  pull_cell<PREC>(P, src, xn, yn, dn);
+  wall_node_from<HET>(P, dn, x, y, xn, yn, w, ay_nb, d, ux_nb, uy_nb);
 }
 
 // Pre-collision state of any cell: the pull of Eq. 15 with its wall rules, or the extrapolated
@@ -772,6 +786,22 @@ __device__ __forceinline__ double temperature_at(const StepParams& P, const type
   return (double)P.T0 + ((double)g[0] + g[1] + g[2] + g[3] + g[4]);
 }
 
+// Flow and temperature state of a wall node of a thermal context from the pulled states dn, gn of
+// its nb (see gather_cell_thermal).
+template <bool HET>
+__device__ __forceinline__ void thermal_wall_node_from(const StepParams& P, const float dn[8], const float gn[5], int x, int y, int xn,
+                                                       int yn, int w, float d[8], float g[5]) {
+  const float Tn = gn[0] + gn[1] + gn[2] + gn[3] + gn[4];  // T_nb - T0
+  float uxn, uyn;
+  wall_node_from<HET>(P, dn, x, y, xn, yn, w, P.ay + P.g_beta * Tn, d, uxn, uyn);
+  const float Tb = P.Tdir[w] ? P.Tw[w] - P.T0 : Tn;
+  float eb[5], en[5];
+  geq_dev(P, P.T0 + Tb, __ldg(P.uw + 2 * w), __ldg(P.uw + 2 * w + 1), eb);
+  geq_dev(P, P.T0 + Tn, uxn, uyn, en);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) g[i] = eb[i] + gn[i] - en[i];
+}
+
 // Pre-collision flow (d) and temperature (g, deviations from T0/5) state of a cell of a thermal
 // context.  On a wall node of an extrapolated side, g = g_eq(T_b, u_w) + g_nb - g_eq(T_nb, u_nb)
 // with T_b the wall temperature (isothermal wall) or T_nb (adiabatic wall), and the flow part
@@ -781,17 +811,10 @@ __device__ __forceinline__ void gather_cell_thermal(const StepParams& P, const t
                                                     const typename Store<PREC>::T* gsrc, int x, int y, float d[8], float g[5]) {
   int xn, yn, w;
   if (nee_node(P, x, y, xn, yn, w)) {
-    float gn[5];
+    float dn[8], gn[5];
+    pull_cell<PREC>(P, src, xn, yn, dn);
     pull_cell_g<PREC>(P, gsrc, xn, yn, gn);
-    const float Tn = gn[0] + gn[1] + gn[2] + gn[3] + gn[4];  // T_nb - T0
-    float uxn, uyn;
-    wall_node<PREC, HET>(P, src, x, y, xn, yn, w, P.ay + P.g_beta * Tn, d, uxn, uyn);
-    const float Tb = P.Tdir[w] ? P.Tw[w] - P.T0 : Tn;
-    float eb[5], en[5];
-    geq_dev(P, P.T0 + Tb, __ldg(P.uw + 2 * w), __ldg(P.uw + 2 * w + 1), eb);
-    geq_dev(P, P.T0 + Tn, uxn, uyn, en);
-#pragma unroll
-    for (int i = 0; i < 5; ++i) g[i] = eb[i] + gn[i] - en[i];
+    thermal_wall_node_from<HET>(P, dn, gn, x, y, xn, yn, w, d, g);
   } else {
     gather_cell<PREC, HET>(P, src, x, y, d);
     pull_cell_g<PREC>(P, gsrc, x, y, g);

@@ -71,14 +71,15 @@ def test_create_rejects_bad_configs_without_a_device(L, field, value, code):
 
 
 @pytest.mark.parametrize("bc_x,bc_y", [(2, 1), (3, 1), (1, 3), (0, 3)])
-def test_inplace_streaming_rejects_extrapolated_sides_without_a_device(L, bc_x, bc_y):
-    """In-place streaming takes periodic and halfway-wall sides only: pressure columns and wall nodes
-    read a neighbour's state while it is overwritten."""
+def test_inplace_batch_rejects_extrapolated_sides_without_a_device(L, bc_x, bc_y):
+    """A single lattice takes pressure columns and wall nodes with in-place streaming (their states
+    are computed before each step); an in-place batch takes periodic and halfway-wall sides only."""
     from paper_1311_7239_gb300 import lbm
 
-    cfg = lbm.default_config(bc_x=bc_x, bc_y=bc_y, streaming=lbm.STREAM_INPLACE)
+    cfgs = (lbm.Config * 2)(lbm.default_config(streaming=lbm.STREAM_INPLACE),
+                            lbm.default_config(bc_x=bc_x, bc_y=bc_y, streaming=lbm.STREAM_INPLACE))
     h = ctypes.c_void_p()
-    assert L.lbm_create(ctypes.byref(cfg), ctypes.byref(h)) == lbm.EINVAL
+    assert L.lbm_batch_create(cfgs, 2, ctypes.byref(h)) == lbm.EINVAL
     assert not h.value and b"in-place" in L.lbm_last_error()
 
 

@@ -47,6 +47,17 @@ MULTI_STEP_CASES = {
     "tiny-2x3": Case(2, 3, bc_x="periodic", bc_y="wall", walls=CAV, streaming=IP),
     "tiny-3x2-walls": Case(3, 2, bc_x="wall", bc_y="wall", walls=CAV, streaming=IP),
     "tiny-5x2-periodic": Case(5, 2, bc_x="periodic", bc_y="periodic", ax=1e-4, streaming=IP),
+    # extrapolated sides: pressure columns and wall nodes (their states are computed before the step)
+    "pressure-het": Case(41, 13, bc_x="pressure", bc_y="wall", het=True, p_in=1.01, p_out=0.99, streaming=IP),
+    "nee-cavity-moving-walls-het": Case(37, 21, bc_x="nee", bc_y="nee", het=True, streaming=IP,
+                                        walls={"top": (0.1, 0.0), "bottom": (0.0, 0.01), "left": (0.0, 0.02), "right": (0.0, -0.03)}),
+    "nee-channel-lid": Case(33, 17, bc_x="periodic", bc_y="nee", walls={"top": (0.05, 0.0)}, ax=1e-4, streaming=IP),
+    "nee-walls-pressure-het": Case(41, 13, bc_x="pressure", bc_y="nee", het=True, p_in=1.01, p_out=0.99, streaming=IP),
+    "nee-x-halfway-y": Case(20, 9, bc_x="nee", bc_y="wall", walls={"left": (0.0, 0.05), "top": (0.03, 0.0)}, streaming=IP),
+    "nee-x-periodic-y": Case(20, 9, bc_x="nee", bc_y="periodic", walls={"right": (0.0, -0.04)}, ay=1e-4, streaming=IP),
+    "nee-ragged-3-blocks": Case(1100, 6, bc_x="nee", bc_y="nee", walls=CAV, phi=0.7, K=5.0, streaming=IP),
+    "nee-tiny-3x3": Case(3, 3, bc_x="nee", bc_y="nee", walls=CAV, streaming=IP),
+    "pressure-tiny-3x2": Case(3, 2, bc_x="pressure", bc_y="periodic", p_in=1.01, p_out=0.99, streaming=IP),
 }
 
 
@@ -119,6 +130,23 @@ def _reduced_precision_cavity(lbm, prec):
     return _trajectory(lbm, case, 800)
 
 
+@pytest.mark.parametrize("prec,bound", [(0, 1e-5), (1, 1e-3)])
+def test_nee_cavity_and_pressure_channel_trajectories(lbm, accuracy, prec, bound):
+    """In-place streaming with extrapolated sides over many steps (both parities, graph replays):
+    the lid-driven cavity with wall nodes on all sides and the pressure-driven heterogeneous
+    channel with wall nodes above and below, against the oracle's trajectories."""
+    L = 64
+    cav = Case(L, L, nu=0.1 * L / 100, phi=0.4, K=1e-3 * L * L, bc_x="nee", bc_y="nee", walls=CAV, precision=prec, streaming=IP)
+    ch = Case(96, 48, nu=0.1, phi=0.35, K=1e-3 * 48 * 48, het=True, eps_sd=0.03, corr=12.0, bc_x="pressure", bc_y="nee",
+              p_in=1.002, p_out=0.998, precision=prec, streaming=IP)
+    name = {0: "fp32", 1: "fp16"}[prec]
+    for label, case, steps in (("lid-driven porous cavity 64x64 with extrapolated wall nodes, in-place streaming", cav, 500),
+                               ("pressure-driven heterogeneous channel 96x48 with extrapolated wall nodes, in-place streaming", ch, 400)):
+        e_u, e_p = _trajectory(lbm, case, steps)
+        accuracy.append({"case": label, "precision": name, "steps": steps, "rel_l2_u": e_u, "rel_l2_p": e_p, "bound": bound})
+        assert e_u <= bound and e_p <= bound, (label, e_u, e_p)
+
+
 def test_reduced_precision_cavity(lbm, accuracy):
     """FP16 storage with in-place streaming, within the 1e-3 target."""
     e_u, e_p = _reduced_precision_cavity(lbm, 1)
@@ -165,16 +193,19 @@ def test_natural_convection_trajectory_and_nusselt(lbm, accuracy, prec, bound):
     assert abs(nu_l - nu_o) <= 10 * bound * abs(nu_o), (nu_l, nu_o)
 
 
-def test_thermal_one_step_matches_oracle_elementwise(lbm):
-    """One and two coupled steps from a random state with isothermal and adiabatic halfway walls
-    and a moving lid (the anti-bounce-back slots of both parities)."""
-    case = Case(23, 17, nu=0.05, phi=0.6, K=3.0, bc_x="wall", bc_y="wall", walls={"top": (0.04, 0.0)}, streaming=IP,
+@pytest.mark.parametrize("bc", ["wall", "nee"])
+def test_thermal_one_step_matches_oracle_elementwise(lbm, bc):
+    """One and two coupled steps from a random state with isothermal and adiabatic walls (halfway,
+    or extrapolated wall nodes) and a moving lid (the anti-bounce-back slots of both parities)."""
+    case = Case(23, 17, nu=0.05, phi=0.6, K=3.0, bc_x=bc, bc_y=bc, walls={"top": (0.04, 0.0)}, streaming=IP,
                 thermal=dict(tau_T=0.8, g_beta=2e-4, T0=11.0, T_left=21.0, T_right=1.0))
     flow, tp = case.flow(), case.thermal_params()
     rng = np.random.default_rng(21)
     f = random_state(flow, seed=9)
     T = 11.0 + 5.0 * rng.standard_normal((flow.ny, flow.nx))
     g = th.equilibrium(T, *(0.03 * rng.standard_normal((2, flow.ny, flow.nx))), tp) + 0.01 * rng.standard_normal((5, flow.ny, flow.nx))
+    if bc == "nee":
+        f, g = th.boundary_nodes(f, g, flow, tp)
     f = f.astype(np.float32).astype(np.float64)
     g = g.astype(np.float32).astype(np.float64)
     with case.lattice(lbm) as lat:
@@ -188,10 +219,19 @@ def test_thermal_one_step_matches_oracle_elementwise(lbm):
         lat.sync()
 
 
-def test_same_result_as_ab_streaming(lbm):
+SIDES = {
+    "halfway-walls": dict(bc_x="wall", bc_y="wall", walls=CAV),
+    "nee-walls": dict(bc_x="nee", bc_y="nee", walls={"top": (0.1, 0.0), "left": (0.0, 0.02)}),
+    "pressure-nee": dict(bc_x="pressure", bc_y="nee", p_in=1.002, p_out=0.998),
+    "pressure-halfway": dict(bc_x="pressure", bc_y="wall", p_in=1.002, p_out=0.998, walls=CAV),
+}
+
+
+@pytest.mark.parametrize("sides", list(SIDES))
+def test_same_result_as_ab_streaming(lbm, sides):
     """In-place and A-B forms of the same run (FP32, per-cell medium, moving walls, 101 steps: three
     graph replays and five single steps) agree to FP32 rounding; the probe and the residual too."""
-    case = Case(150, 70, nu=0.05, phi=0.5, K=3.0, bc_x="wall", bc_y="wall", walls=CAV, het=True)
+    case = Case(150, 70, nu=0.05, phi=0.5, K=3.0, het=True, **SIDES[sides])
     with case.lattice(lbm) as a, dataclasses.replace(case, streaming=IP).lattice(lbm) as b:
         a.step(101)
         b.step(101)
@@ -272,9 +312,13 @@ def test_memory_and_rejections(lbm):
         assert e.value.code == lbm.ESTATE
     assert ma - mc >= 0.99 * one, (ma, mc)
     assert ma - mb >= 0.99 * one - 8 * n, (ma, mb)
+    # extrapolated sides: a single lattice takes them (with a few bytes per boundary node for their
+    # states), an in-place batch does not
     for bx, by in (("nee", "wall"), ("wall", "nee"), ("pressure", "wall")):
+        with Case(32, 16, bc_x=bx, bc_y=by, streaming=IP).lattice(lbm) as lat:
+            lat.step(3)
         with pytest.raises(lbm.LbmError) as e:
-            Case(32, 16, bc_x=bx, bc_y=by, streaming=IP).lattice(lbm)
+            lbm.Batch([Case(32, 16, bc_x=bx, bc_y=by, streaming=IP).config(lbm)])
         assert e.value.code == lbm.EINVAL
     with Case(32, 16, bc_x="periodic", bc_y="wall", streaming=IP).lattice(lbm) as lat:
         with pytest.raises(lbm.LbmError) as e:
