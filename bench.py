@@ -394,6 +394,7 @@ def ensemble_form(lbm, steps, local_rank):
         device_bytes = b.info()["bytes"]
         nt, k, _ = b.tune(steps=8)
         tiling = "flat" if b.get_tiling() == lbm.TILING_FLAT else "rows"
+        ipc = b.get_items_per_cta()
         b.step(32)
         b.sync()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -416,7 +417,8 @@ def ensemble_form(lbm, steps, local_rank):
         mlups = cells * steps / (ms_b * 1e-3) / 1e6
         res[key] = {"batched_MLUPS": mlups, "one_by_one_MLUPS": cells * each / (ms_e * 1e-3) / 1e6,
                     "batched_roofline_frac": mlups * 1e6 * bpl / 1e9 / peak, "algorithmic_bytes_per_lu": bpl,
-                    "launch": {"threads_per_cta": nt, "ctas_per_sm": k, "tiling": tiling}, "steps": steps,
+                    "launch": {"threads_per_cta": nt, "ctas_per_sm": k, "items_per_cta": ipc, "tiling": tiling},
+                    "steps": steps,
                     "one_by_one_steps": each,
                     "device_bytes": device_bytes, "clocks": clk.summary()}
         torch.cuda.empty_cache()

@@ -275,6 +275,13 @@ LBM_API int lbm_batch_step_each(lbm_batch* b, int n);
  * In-place batches take (128, 0) only (EINVAL otherwise). */
 LBM_API int lbm_batch_set_launch(lbm_batch* b, int threads_per_cta, int ctas_per_sm);
 LBM_API int lbm_batch_get_launch(const lbm_batch* b, int* threads_per_cta, int* ctas_per_sm);
+/* Work items per CTA when ctas_per_sm = 0: 1 (the default) = one CTA per work item; 2, 4 or 8 = CTAs
+ * of that many consecutive work items of the concatenated list (4 x items_per_cta cells per thread;
+ * ceil(items / items_per_cta) CTAs walking their ranges as the persistent form does, the lattice
+ * table not needed).  In-place batches take 1 only (EINVAL otherwise).  The work-item tables are
+ * rebuilt. */
+LBM_API int lbm_batch_set_items_per_cta(lbm_batch* b, int items_per_cta);
+LBM_API int lbm_batch_get_items_per_cta(const lbm_batch* b, int* items_per_cta);
 /* Tiling of each lattice into work items of one CTA (A-B batches; in-place batches keep their own
  * tiling and accept LBM_TILING_FLAT only, EINVAL otherwise):
  *   LBM_TILING_ROWS  rows of work items: a row of G four-cell groups takes ceil(G / threads) items,
@@ -286,9 +293,10 @@ LBM_API int lbm_batch_get_launch(const lbm_batch* b, int* threads_per_cta, int* 
 #define LBM_TILING_FLAT 1
 LBM_API int lbm_batch_set_tiling(lbm_batch* b, int tiling);
 LBM_API int lbm_batch_get_tiling(const lbm_batch* b, int* tiling);
-/* Time `steps` steps for every launch shape and tiling on a copy of the current state, keep the
- * fastest, restore the state; outputs may be NULL (the chosen tiling: lbm_batch_get_tiling).
- * Waits for the stream. */
+/* Time `steps` steps for every launch shape (threads per CTA 64 / 128 / 256; one CTA per work item,
+ * CTAs of 2 or 4 work items, persistent grids of 1..16 CTAs per SM) and tiling on a copy of the
+ * current state, keep the fastest, restore the state; outputs may be NULL (the chosen tiling and
+ * work items per CTA: lbm_batch_get_tiling, lbm_batch_get_items_per_cta).  Waits for the stream. */
 LBM_API int lbm_batch_tune(lbm_batch* b, int steps, int* threads_per_cta, int* ctas_per_sm, float* ms_per_step);
 /* Read-outs of lattice d (float32 [ny_d][nx_d] / [8][ny_d][nx_d], host or device). */
 LBM_API int lbm_batch_macros(lbm_batch* b, int d, float* p, float* ux, float* uy);

@@ -61,6 +61,7 @@ struct lbm_batch {
   int64_t item_lattice_cap = 0;
   int64_t total_items = 0;
   int nt = 128, ctas_per_sm = 4, grid = 0, sms = 0;
+  int items_per_cta = 1;  // ctas_per_sm = 0: consecutive work items per CTA (4 x items_per_cta cells per thread)
   int flat = 1;  // tiling of the A-B batched kernel (LBM_TILING_FLAT / LBM_TILING_ROWS)
   // A-B batches whose lattices share rho0, s_e, s_q and the storage scale: per-lattice records of the
   // fields that differ (one array per buffer parity) for the per-item kernel
@@ -134,6 +135,13 @@ int set_launch(lbm_batch* b, int nt, int ctas_per_sm) {
   b->total_items = total;
   b->nt = nt;
   drop_graphs(b);
+  if (ctas_per_sm == 0 && b->items_per_cta > 1) {  // CTAs of items_per_cta consecutive items (the range walk)
+    const int64_t g = (total + b->items_per_cta - 1) / b->items_per_cta;
+    if (g > 0x7fffffffLL) return fail_msg(LBM_EINVAL, "too many work items for the grid");
+    b->ctas_per_sm = 0;
+    b->grid = (int)g;
+    return LBM_OK;
+  }
   if (ctas_per_sm == 0) {  // one CTA per work item
     if (total > 0x7fffffffLL) return fail_msg(LBM_EINVAL, "too many work items for one CTA per item");
     if (b->item_lattice_cap < total) {
@@ -169,11 +177,13 @@ int set_launch(lbm_batch* b, int nt, int ctas_per_sm) {
 cudaError_t launch_batch(const lbm_batch* b, int cur, cudaStream_t s) {
   if (b->inplace)
     return launch_step_batch_inplace(b->dp[cur], b->item_start, b->item_lattice, b->total_items, b->prec, cur, s);
-  if (b->shared_consts && b->ctas_per_sm == 0)
+  const bool per_item = b->ctas_per_sm == 0 && b->items_per_cta == 1;
+  if (b->shared_consts && per_item)
     return launch_step_batch_shared(b->hp[0][0], b->rec[cur], b->dp[cur], b->item_start, b->item_lattice, b->total_items, b->prec,
                                     b->nt, b->flat, s);
-  return launch_step_batch(b->dp[cur], b->item_start, b->ctas_per_sm == 0 ? b->item_lattice : nullptr, b->n, b->total_items, b->prec,
-                           b->nt, b->grid, b->flat, s);
+  // otherwise the range walk: a persistent grid, or ceil(items / items_per_cta) CTAs
+  return launch_step_batch(b->dp[cur], b->item_start, per_item ? b->item_lattice : nullptr, b->n, b->total_items, b->prec, b->nt,
+                           b->grid, b->flat, s);
 }
 
 int launch_once(lbm_batch* b, int cur, cudaStream_t s) {
@@ -485,6 +495,24 @@ int lbm_batch_get_launch(const lbm_batch* b, int* threads_per_cta, int* ctas_per
   return LBM_OK;
 }
 
+int lbm_batch_set_items_per_cta(lbm_batch* b, int items_per_cta) {
+  if (!b) return fail_msg(LBM_EINVAL, "null batch");
+  if (items_per_cta != 1 && items_per_cta != 2 && items_per_cta != 4 && items_per_cta != 8)
+    return fail_msg(LBM_EINVAL, "work items per CTA must be 1, 2, 4 or 8");
+  if (b->inplace && items_per_cta != 1) return fail_msg(LBM_EINVAL, "in-place batches run one work item per CTA");
+  const int old = b->items_per_cta;
+  b->items_per_cta = items_per_cta;
+  const int rc = set_launch(b, b->nt, b->ctas_per_sm);
+  if (rc) b->items_per_cta = old;
+  return rc;
+}
+
+int lbm_batch_get_items_per_cta(const lbm_batch* b, int* items_per_cta) {
+  if (!b || !items_per_cta) return fail_msg(LBM_EINVAL, "null argument");
+  *items_per_cta = b->items_per_cta;
+  return LBM_OK;
+}
+
 int lbm_batch_set_tiling(lbm_batch* b, int tiling) {
   if (!b) return fail_msg(LBM_EINVAL, "null batch");
   if (tiling != LBM_TILING_ROWS && tiling != LBM_TILING_FLAT) return fail_msg(LBM_EINVAL, "tiling must be LBM_TILING_ROWS or LBM_TILING_FLAT");
@@ -513,12 +541,15 @@ int lbm_batch_tune(lbm_batch* b, int steps, int* threads_per_cta, int* ctas_per_
   void* live = b->pool[b->inplace ? 0 : b->cur];
   cudaMemcpyAsync(save, live, pool_bytes, cudaMemcpyDeviceToDevice, b->stream);
   const int nts[3] = {64, 128, 256};
-  const int ks[6] = {0, 1, 2, 4, 8, 16};  // 0: one CTA per work item
-  const int n_nt = b->inplace ? 1 : 3, n_k = b->inplace ? 1 : 6;
+  // (CTAs per SM, work items per CTA): one CTA per item, CTAs of 2 and 4 consecutive items (8 and
+  // 16 cells per thread), persistent grids of SMs x k CTAs
+  const int ks[8] = {0, 0, 0, 1, 2, 4, 8, 16};
+  const int ipc[8] = {1, 2, 4, 1, 1, 1, 1, 1};
+  const int n_nt = b->inplace ? 1 : 3, n_k = b->inplace ? 1 : 8;
   const int* nt_list = b->inplace ? &nts[1] : nts;
   const int n_tiling = b->inplace ? 1 : 2;  // flat, then rows
   float best = 1e30f;
-  int best_nt = b->nt, best_k = b->ctas_per_sm, best_flat = b->flat;
+  int best_nt = b->nt, best_k = b->ctas_per_sm, best_flat = b->flat, best_ipc = b->items_per_cta;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -528,6 +559,7 @@ int lbm_batch_tune(lbm_batch* b, int steps, int* threads_per_cta, int* ctas_per_
     for (int c = 0; c < n_k && rc == LBM_OK; ++c) {
       if (ks[c] > batch_max_ctas_per_sm(b->prec, nt_list[a])) continue;  // persistent CTAs must be resident
       b->flat = b->inplace || f == 0 ? 1 : 0;
+      b->items_per_cta = ipc[c];
       if ((rc = set_launch(b, nt_list[a], ks[c]))) break;
       if ((rc = launch_once(b, b->cur, b->stream))) break;  // warm-up
       cudaEventRecord(e0, b->stream);
@@ -542,6 +574,7 @@ int lbm_batch_tune(lbm_batch* b, int steps, int* threads_per_cta, int* ctas_per_
         best_nt = nt_list[a];
         best_k = ks[c];
         best_flat = b->flat;
+        best_ipc = ipc[c];
       }
     }
   cudaMemcpyAsync(live, save, pool_bytes, cudaMemcpyDeviceToDevice, b->stream);
@@ -551,6 +584,7 @@ int lbm_batch_tune(lbm_batch* b, int steps, int* threads_per_cta, int* ctas_per_
   cudaEventDestroy(e1);
   if (rc) return rc;
   b->flat = best_flat;
+  b->items_per_cta = best_ipc;
   if ((rc = set_launch(b, best_nt, best_k))) return rc;
   if (threads_per_cta) *threads_per_cta = best_nt;
   if (ctas_per_sm) *ctas_per_sm = best_k;

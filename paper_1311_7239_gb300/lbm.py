@@ -108,6 +108,8 @@ SIGNATURES = {
     "lbm_batch_step_each": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "lbm_batch_set_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "lbm_batch_get_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "lbm_batch_set_items_per_cta": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "lbm_batch_get_items_per_cta": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "lbm_batch_set_tiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "lbm_batch_get_tiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "lbm_batch_tune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -404,6 +406,16 @@ class Batch:
         _check(lib().lbm_batch_get_launch(self._h, ctypes.byref(a), ctypes.byref(b)), "lbm_batch_get_launch")
         return a.value, b.value
 
+    def set_items_per_cta(self, items_per_cta):
+        """Work items per CTA of the one-CTA form (ctas_per_sm = 0): 1, 2, 4 or 8 (4 x that many
+        cells per thread)."""
+        _check(lib().lbm_batch_set_items_per_cta(self._h, int(items_per_cta)), "lbm_batch_set_items_per_cta")
+
+    def get_items_per_cta(self):
+        k = ctypes.c_int()
+        _check(lib().lbm_batch_get_items_per_cta(self._h, ctypes.byref(k)), "lbm_batch_get_items_per_cta")
+        return k.value
+
     def set_tiling(self, tiling):
         _check(lib().lbm_batch_set_tiling(self._h, int(tiling)), "lbm_batch_set_tiling")
 
@@ -418,8 +430,9 @@ class Batch:
         return a.value, b.value, ms.value
 
     def tune_cached(self, path=None, steps=20):
-        """Launch shape and tiling from a JSON cache on disk (keyed by GPU, storage precision, lattice
-        count and total cells rounded to a power of two); a miss runs ``tune`` and records the result."""
+        """Launch shape, work items per CTA and tiling from a JSON cache on disk (keyed by GPU, storage
+        precision, lattice count and total cells rounded to a power of two); a miss runs ``tune`` and
+        records the result."""
         import json
 
         import torch
@@ -435,10 +448,12 @@ class Batch:
         if key in cache:
             nt, k = cache[key]["threads_per_cta"], cache[key]["ctas_per_sm"]
             self.set_tiling(cache[key].get("tiling", TILING_FLAT))
+            self.set_items_per_cta(cache[key].get("items_per_cta", 1))
             self.set_launch(nt, k)
             return nt, k, cache[key]["ms_per_step"], True
         nt, k, ms = self.tune(steps)
-        cache[key] = {"threads_per_cta": nt, "ctas_per_sm": k, "tiling": self.get_tiling(), "ms_per_step": ms}
+        cache[key] = {"threads_per_cta": nt, "ctas_per_sm": k, "tiling": self.get_tiling(), "items_per_cta": self.get_items_per_cta(),
+                      "ms_per_step": ms}
         os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
         tmp = path + ".tmp"
         with open(tmp, "w") as fh:

@@ -43,12 +43,16 @@ def test_batch_equals_single_lattices_bitwise(lbm, prec):
     cfgs, media = ensemble.ensemble(lbm, n=7, seed=3, lo=8, hi=300, precision=prec)
     steps = 45
     want = _singles(lbm, cfgs, media, steps)
+    # (threads per CTA, CTAs per SM, work items per CTA): persistent grids, one CTA per item, CTAs of
+    # 2, 4 and 8 consecutive items
     for tiling in (lbm.TILING_FLAT, lbm.TILING_ROWS):
-        for shape in [(128, 4), (64, 8), (256, 2), (128, 32), (128, 0), (64, 0)]:
+        for shape in [(128, 4, 1), (64, 8, 1), (256, 2, 1), (128, 32, 1), (128, 0, 1), (64, 0, 1), (128, 0, 2), (64, 0, 4),
+                      (256, 0, 8)]:
             with ensemble.build(lbm, cfgs, media) as b:
                 b.set_tiling(tiling)
-                b.set_launch(*shape)
-                assert b.get_tiling() == tiling
+                b.set_items_per_cta(shape[2])
+                b.set_launch(*shape[:2])
+                assert b.get_tiling() == tiling and b.get_items_per_cta() == shape[2]
                 b.step(steps)  # a graph of 32 + 13 launches
                 b.sync()
                 for d in range(len(cfgs)):
@@ -63,6 +67,7 @@ def test_step_each_and_tune_leave_results_unchanged(lbm):
         nt, k, ms = a.tune(steps=3)
         assert nt in (64, 128, 256) and 0 <= k <= 16 and ms > 0
         assert a.get_launch() == (nt, k) and a.get_tiling() in (lbm.TILING_ROWS, lbm.TILING_FLAT)
+        assert a.get_items_per_cta() in (1, 2, 4) and (k == 0 or a.get_items_per_cta() == 1)
         a.step(40)
         b.step_each(40)
         for d in range(len(cfgs)):
