@@ -250,7 +250,8 @@ LBM_API int lbm_nusselt(lbm_ctx* ctx, int side, double* nu);
 /* ---------------------------------------------------------------------------------------------
  * Batched ensembles: n independent isothermal lattices, each with its own lbm_config (size,
  * boundaries, parameters, medium; one storage precision for all), advanced together by one
- * persistent launch per time step over the concatenated work items of all lattices, with
+ * launch per time step over the concatenated work items of all lattices (one CTA per item, CTAs
+ * of a few items, or a persistent grid: lbm_batch_set_launch, lbm_batch_tune), with
  * runs of 32 steps replayed as a captured CUDA graph.  The batch runs on cfgs[0].stream (NULL:
  * a stream of its own).  Every lattice keeps per-cell medium fields (8 B per cell).  All lattices
  * use one streaming form: LBM_STREAM_AB (two population pools), or LBM_STREAM_INPLACE (one pool,

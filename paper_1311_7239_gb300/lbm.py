@@ -195,8 +195,8 @@ class Lattice:
     Outputs of the read-out methods are torch tensors on the context's device unless ``out``
     arrays are given.  By default the context runs on torch's current CUDA stream.  Keyword
     arguments are ``lbm_config`` fields, e.g. ``streaming=STREAM_INPLACE`` for one population
-    buffer updated in place (periodic and halfway-wall sides; ``options=OPT_NO_RESIDUAL_RECORD``
-    also drops the residual's velocity record).
+    buffer updated in place (every side kind; ``options=OPT_NO_RESIDUAL_RECORD`` also drops the
+    residual's velocity record).
     """
 
     def __init__(self, cfg: Config | None = None, **kw):
