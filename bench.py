@@ -222,21 +222,24 @@ def run_reference(args, rank, world):
     return 0
 
 
-def make_lattice(lbm, L, prec, stream, streaming=0):
+def make_lattice(lbm, L, prec, stream, streaming=0, walls="halfway"):
+    """The benchmark cavity: halfway bounce-back walls, or the paper's wall nodes with
+    non-equilibrium extrapolation (walls="nee")."""
     prm = cavity_params(L)
-    cfg = lbm.default_config(nx=L, ny=L, bc_x=lbm.WALL, bc_y=lbm.WALL, nu=prm["nu"], phi=prm["phi"], K=prm["K"],
+    bc = lbm.NEE if walls == "nee" else lbm.WALL
+    cfg = lbm.default_config(nx=L, ny=L, bc_x=bc, bc_y=bc, nu=prm["nu"], phi=prm["phi"], K=prm["K"],
                              u_wall=[(0, 0), (0, 0), (0, 0), (prm["lid"], 0)], precision=PREC[prec], p_rest=prm["phi"],
                              dev_scale_log2=10, streaming=streaming)
     cfg.stream = stream.cuda_stream
     return lbm.Lattice(cfg)
 
 
-def timed_steps(lbm, L, prec, steps, warmup, local_rank, dist=None, streaming=0):
+def timed_steps(lbm, L, prec, steps, warmup, local_rank, dist=None, streaming=0, walls="halfway"):
     """(ms for `steps` steps, clock summary, lattice) with CUDA events on the lattice's stream."""
     import torch
 
     stream = torch.cuda.Stream()
-    lat = make_lattice(lbm, L, prec, stream, streaming)
+    lat = make_lattice(lbm, L, prec, stream, streaming, walls)
     lat.step(warmup)
     lat.sync()
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -303,6 +306,26 @@ def inplace_form(lbm, L, steps, warmup, local_rank):
                      "algorithmic_bytes_per_lu": BYTES_PER_LU[prec], "steps": steps, "device_bytes": mem,
                      "device_bytes_ab": mem_ab, "clocks": clk}
     return {"workload": f"lid-driven porous cavity {L}x{L}, eps=0.4, Da=1e-3, Re=100, lid=0.1, in-place streaming", **out}
+
+
+def wall_nodes_form(lbm, L, steps, warmup, local_rank):
+    """The benchmark cavity with the paper's wall treatment (wall nodes with non-equilibrium
+    extrapolation on all four sides) instead of halfway bounce-back, A-B and in-place streaming;
+    in-place steps first compute the boundary nodes' states (one small extra launch per step)."""
+    import torch
+
+    out = {}
+    peak, _ = peaks()
+    for prec in ("fp32", "fp16"):
+        for streaming in (0, 1):
+            ms, clk, lat = timed_steps(lbm, L, prec, steps, warmup, local_rank, streaming=streaming, walls="nee")
+            lat.close()
+            torch.cuda.empty_cache()
+            bw = BYTES_PER_LU[prec] * L * L * steps / (ms * 1e-3) / 1e9
+            out[f"{prec}_{'inplace' if streaming else 'ab'}"] = {
+                "value": L * L * steps / (ms * 1e-3) / 1e6, "unit": "MLUPS", "achieved_gbs": bw, "roofline_frac": bw / peak,
+                "algorithmic_bytes_per_lu": BYTES_PER_LU[prec], "steps": steps, "clocks": clk}
+    return {"workload": f"lid-driven porous cavity {L}x{L}, eps=0.4, Da=1e-3, Re=100, lid=0.1, extrapolated wall nodes", **out}
 
 
 def thermal_form(lbm, L, steps, warmup, local_rank):
@@ -485,7 +508,7 @@ def run_gpu(args, rank, world, local_rank):
     prm = cavity_params(L)
     prec = args.precision
     streaming = 1 if args.streaming == "inplace" else 0
-    ms, clocks, lat = timed_steps(lbm, L, prec, args.steps, args.warmup, local_rank, dist, streaming)
+    ms, clocks, lat = timed_steps(lbm, L, prec, args.steps, args.warmup, local_rank, dist, streaming, args.walls)
     if dist:
         ms = max_over_ranks(ms, dist, "cuda")
         dist.barrier()
@@ -547,14 +570,15 @@ def run_gpu(args, rank, world, local_rank):
         return 0
     bpl = BYTES_PER_LU[prec]
     achieved = bpl * cells / (ms * 1e-3 / args.steps) / 1e9
-    kernel_key = f"k_step_{prec}_uniform_{L}" if not streaming else f"k_step_ip_{prec}_uniform_{L}"
+    kernel_key = (f"k_step_{prec}_uniform_{L}" if not streaming else f"k_step_ip_{prec}_uniform_{L}") + ("_nee" if args.walls == "nee" else "")
     traffic = traffic_for(kernel_key)
     line = {
         "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "fp16": "f32 (f16 storage)", "bf16": "f32 (bf16 storage)"}[prec], "data": "synthetic",
         "config": {"workload": f"lid-driven porous cavity {L}x{L}, eps=0.4, Da=1e-3, Re=100, lid=0.1, "
-                               f"{prec} deviation storage, {'in-place' if streaming else 'A-B pull'} streaming",
+                               f"{prec} deviation storage, {'in-place' if streaming else 'A-B pull'} streaming"
+                               + (", extrapolated wall nodes" if args.walls == "nee" else ""),
                    "nx": L, "ny": L, "precision": prec,
                    "l2": f"inputs larger than L2 ({1 if streaming else 2} population buffer(s) of {bpl // 2 * cells / 1e6:.0f} MB)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -572,6 +596,7 @@ def run_gpu(args, rank, world, local_rank):
         line["forms"]["thermal"] = thermal_form(lbm, 2048, max(64, args.steps // 4), args.warmup, local_rank)
         line["forms"]["heterogeneous"] = heterogeneous_form(lbm, args.size, max(64, args.steps // 4), args.warmup, local_rank)
         line["forms"]["inplace"] = inplace_form(lbm, args.size, max(64, args.steps // 4), args.warmup, local_rank)
+        line["forms"]["wall_nodes"] = wall_nodes_form(lbm, args.size, max(64, args.steps // 4), args.warmup, local_rank)
         line["forms"]["adjoint"] = adjoint_form(lbm, T=args.adjoint_steps)
         if not args.no_ensemble:
             line["forms"]["ensemble"] = ensemble_form(lbm, args.ensemble_steps, local_rank)
@@ -630,8 +655,8 @@ def run_case(args, local_rank):
     elif args.case in ("fp16", "thermal", "inplace"):  # 2048^2 cavity FP16 storage / natural convection (--precision) /
         stream = torch.cuda.Stream()                     # cavity with in-place streaming (--precision)
         if args.case in ("fp16", "inplace"):
-            cfg = make_lattice(lbm, 2048, "fp16" if args.case == "fp16" else args.precision, stream,
-                               1 if args.case == "inplace" else 0).cfg
+            cfg = make_lattice(lbm, 2048 if args.walls == "halfway" else args.size, "fp16" if args.case == "fp16" else args.precision,
+                               stream, 1 if args.case == "inplace" else 0, args.walls).cfg
         else:
             cfg = workloads.natural_convection(lbm, L=2048, precision=PREC[args.precision])
             cfg.stream = stream.cuda_stream
@@ -656,7 +681,7 @@ def run_sweep(args, local_rank):
             steps = max(64, int(args.steps * (4096 / L) ** 2))
             steps = min(steps, 64000) // 32 * 32
             ms, clk, lat = timed_steps(lbm, L, prec, steps, args.warmup, local_rank,
-                                       streaming=1 if args.streaming == "inplace" else 0)
+                                       streaming=1 if args.streaming == "inplace" else 0, walls=args.walls)
             lat.close()
             cells = L * L
             bw = BYTES_PER_LU[prec] * cells * steps / (ms * 1e-3) / 1e9
@@ -679,6 +704,8 @@ def main():
     ap.add_argument("--size", type=int, default=4096)
     ap.add_argument("--streaming", default="ab", choices=["ab", "inplace"],
                     help="population streaming of the main line and the sweep (A-B buffers or in-place)")
+    ap.add_argument("--walls", default="halfway", choices=["halfway", "nee"],
+                    help="cavity walls: halfway bounce-back, or wall nodes with non-equilibrium extrapolation")
     ap.add_argument("--no-cpu", action="store_true", help="skip the timed CPU oracle baseline")
     ap.add_argument("--no-forms", action="store_true", help="skip the other storage precisions")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 512-lattice ensemble form")
