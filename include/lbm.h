@@ -220,11 +220,13 @@ LBM_API int lbm_residual_noalloc(const float* ux, const float* uy, const float* 
  * 4 nodes apart): runs the T steps -- the context ends at step T, as after lbm_step(ctx, T) -- and
  * returns the loss and its gradient with respect to the per-cell log K and eps (phi) fields,
  * including their effect on the initial equilibrium (Eq. 22).  Memory: checkpoints of the
- * post-collision state every ceil(sqrt(T)) steps, one segment of ceil(sqrt(T)) states, two FP32
- * adjoint states and the gradient sums (FP32 partial sums over at most 64 steps, folded into FP64
- * totals) form a workspace that stays allocated after the call, so that repeated calls (an
- * optimisation loop) allocate nothing; it is counted by lbm_memory_bytes and freed by
- * lbm_release_workspace or lbm_destroy.  The forward work is about 2 T steps.
+ * post-collision state every ceil(sqrt(T)) steps, two segments of ceil(sqrt(T)) states (the
+ * states of one segment are recomputed, on a second stream of lower priority, while the adjoint
+ * steps of the next run on a stream of higher priority), two FP32 adjoint states and the gradient
+ * sums (FP32 partial sums over at most 64 steps, folded into FP64 totals) form a workspace that
+ * stays allocated after the call, so that repeated calls (an optimisation loop) allocate nothing;
+ * it is counted by lbm_memory_bytes and freed by lbm_release_workspace or lbm_destroy.  The
+ * forward work is about 2 T steps.
  *   target_ux, target_uy: float32 [ny][nx] (misfit loss only; host or device).
  *   grad_logK, grad_eps: double [ny][nx] outputs (host or device; NULL skips); loss: double.
  * Waits for the stream. */

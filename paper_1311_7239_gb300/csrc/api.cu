@@ -158,6 +158,10 @@ struct lbm_ctx {
   // CUDA graphs of kGraphSteps steps starting from buffer 0 or 1 (captured on first use)
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   cudaStream_t capture_stream = nullptr;
+  // adjoint reverse sweep: the adjoint steps on a high-priority stream, the recomputation of the
+  // next segment's states on a low-priority one (created on first use)
+  cudaStream_t adj_hi = nullptr, adj_lo = nullptr;
+  cudaEvent_t adj_ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // start, ready[2], freed[2], done
 };
 
 namespace {
@@ -359,6 +363,10 @@ void release(lbm_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   drop_graphs(c);
   if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+  if (c->adj_hi) cudaStreamDestroy(c->adj_hi);
+  if (c->adj_lo) cudaStreamDestroy(c->adj_lo);
+  for (cudaEvent_t e : c->adj_ev)
+    if (e) cudaEventDestroy(e);
   for (int b = 0; b < 2; ++b) {
     cudaFree(c->f[b]);
     cudaFree(c->g[b]);
@@ -905,7 +913,7 @@ int lbm_adjoint(lbm_ctx* c, int T, int loss_kind, const float* target_ux, const 
   while ((int64_t)ck * ck < T) ++ck;  // checkpoint interval ceil(sqrt(T))
   const int nck = (T + ck - 1) / ck;
   // workspace slots (kept between calls): 0-1 adjoint state, 2-3 FP64 gradient totals, 4-5 FP32
-  // gradient partial sums, then nck checkpoints and ck segment states
+  // gradient partial sums, then nck checkpoints and two sets of ck segment states
   LBM_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
   int rc = LBM_OK;
   float* nu[2];
@@ -918,12 +926,25 @@ int lbm_adjoint(lbm_ctx* c, int T, int loss_kind, const float* target_ux, const 
   float* hl = gp ? static_cast<float*>(ws_slot(c, 4, hbytes, &rc, "cudaMalloc(gradient partial sums)")) : nullptr;
   float* hp = hl ? static_cast<float*>(ws_slot(c, 5, hbytes, &rc, "cudaMalloc(gradient partial sums)")) : nullptr;
   if (!hp) return rc;
-  std::vector<void*> ckpt(nck), seg(ck);
+  // two sets of segment states: the adjoint steps of one segment read one set while the states of
+  // the segment before it are recomputed into the other
+  std::vector<void*> ckpt(nck), seg[2] = {std::vector<void*>(ck), std::vector<void*>(ck)};
   for (int k = 0; k < nck; ++k)
     if (!(ckpt[k] = ws_slot(c, 6 + k, fbytes, &rc, "cudaMalloc(checkpoints)"))) return rc;
-  for (int j = 0; j < ck; ++j)
-    if (!(seg[j] = ws_slot(c, 6 + nck + j, fbytes, &rc, "cudaMalloc(segment states)"))) return rc;
-  ws_trim(c, 6 + nck + ck);
+  for (int h = 0; h < 2; ++h)
+    for (int j = 0; j < ck; ++j)
+      if (!(seg[h][j] = ws_slot(c, 6 + nck + h * ck + j, fbytes, &rc, "cudaMalloc(segment states)"))) return rc;
+  ws_trim(c, 6 + nck + 2 * ck);
+  if (!c->adj_hi) {
+    int least = 0, greatest = 0;
+    LBM_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest), "cudaDeviceGetStreamPriorityRange");
+    LBM_CUDA(cudaStreamCreateWithPriority(&c->adj_hi, cudaStreamNonBlocking, greatest), "cudaStreamCreate");
+    LBM_CUDA(cudaStreamCreateWithPriority(&c->adj_lo, cudaStreamNonBlocking, least), "cudaStreamCreate");
+    for (cudaEvent_t& e : c->adj_ev) LBM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
+  }
+  cudaStream_t hi = c->adj_hi, lo = c->adj_lo;
+  cudaEvent_t ev_start = c->adj_ev[0], ev_done = c->adj_ev[5];
+  cudaEvent_t ready[2] = {c->adj_ev[1], c->adj_ev[2]}, freed[2] = {c->adj_ev[3], c->adj_ev[4]};
   for (int b = 0; b < 2; ++b) LBM_CUDA(cudaMemsetAsync(nu[b], 0, nubytes, c->stream), "cudaMemset");
   const float *tux = nullptr, *tuy = nullptr;
   if (loss_kind == LBM_LOSS_VELOCITY_MISFIT) {
@@ -955,27 +976,58 @@ int lbm_adjoint(lbm_ctx* c, int T, int loss_kind, const float* target_ux, const 
   if (pressure) LBM_CUDA(launch_adj_nee(P, c->prec, c->het, c->f[c->cur], nu[0], hl, hp, c->stream), "adjoint pressure columns");
   int cur_nu = 0, unfolded = 1;
   constexpr int kAdjFold = 64;  // at most this many per-step terms in an FP32 partial sum
-  for (int k = nck - 1; k >= 0; --k) {
+  // Reverse sweep over the segments, last first.  The states of segment k - 1 are recomputed from
+  // its checkpoint on the low-priority stream while the adjoint steps of segment k run on the
+  // high-priority one (whose small boundary-transpose launches and tails leave the SMs partly
+  // idle); set k & 1 holds segment k's states, and the recomputation into a set waits until the
+  // adjoint steps that read it (segment k + 2) are done.
+  LBM_CUDA(cudaEventRecord(ev_start, c->stream), "cudaEventRecord");
+  LBM_CUDA(cudaStreamWaitEvent(hi, ev_start, 0), "cudaStreamWaitEvent");
+  LBM_CUDA(cudaStreamWaitEvent(lo, ev_start, 0), "cudaStreamWaitEvent");
+  for (int h = 0; h < 2; ++h) LBM_CUDA(cudaEventRecord(freed[h], hi), "cudaEventRecord");
+  auto recompute = [&](int k) -> int {
     const int t0 = k * ck, t1 = (t0 + ck < T) ? t0 + ck : T;
-    LBM_CUDA(cudaMemcpyAsync(seg[0], ckpt[k], fbytes, cudaMemcpyDeviceToDevice, c->stream), "checkpoint restore");
+    std::vector<void*>& S = seg[k & 1];
+    LBM_CUDA(cudaStreamWaitEvent(lo, freed[k & 1], 0), "cudaStreamWaitEvent");
+    LBM_CUDA(cudaMemcpyAsync(S[0], ckpt[k], fbytes, cudaMemcpyDeviceToDevice, lo), "checkpoint restore");
     for (int j = 1; j < t1 - t0; ++j) {
       StepParams F = P;
-      F.src = seg[j - 1];
-      F.dst = seg[j];
-      LBM_CUDA(launch_step(F, c->prec, c->het, false, c->stream), "recompute step");
+      F.src = S[j - 1];
+      F.dst = S[j];
+      LBM_CUDA(launch_step(F, c->prec, c->het, false, lo), "recompute step");
     }
+    LBM_CUDA(cudaEventRecord(ready[k & 1], lo), "cudaEventRecord");
+    return LBM_OK;
+  };
+  auto sweep = [&]() -> int {
+  int rc2 = recompute(nck - 1);
+  if (rc2) return rc2;
+  for (int k = nck - 1; k >= 0; --k) {
+    const int t0 = k * ck, t1 = (t0 + ck < T) ? t0 + ck : T;
+    if (k > 0 && (rc2 = recompute(k - 1))) return rc2;
+    LBM_CUDA(cudaStreamWaitEvent(hi, ready[k & 1], 0), "cudaStreamWaitEvent");
     for (int t = t1 - 1; t >= t0; --t) {
-      const void* buf = seg[t - t0];
-      LBM_CUDA(launch_adj_step(P, c->prec, c->het, buf, nu[cur_nu], nu[cur_nu ^ 1], hl, hp, c->stream), "adjoint step");
+      const void* buf = seg[k & 1][t - t0];
+      LBM_CUDA(launch_adj_step(P, c->prec, c->het, buf, nu[cur_nu], nu[cur_nu ^ 1], hl, hp, hi), "adjoint step");
       cur_nu ^= 1;
-      if (walls) LBM_CUDA(launch_adj_wall(P, c->prec, c->het, buf, nu[cur_nu], hl, hp, c->stream), "adjoint wall nodes");
-      if (pressure) LBM_CUDA(launch_adj_nee(P, c->prec, c->het, buf, nu[cur_nu], hl, hp, c->stream), "adjoint pressure columns");
+      if (walls) LBM_CUDA(launch_adj_wall(P, c->prec, c->het, buf, nu[cur_nu], hl, hp, hi), "adjoint wall nodes");
+      if (pressure) LBM_CUDA(launch_adj_nee(P, c->prec, c->het, buf, nu[cur_nu], hl, hp, hi), "adjoint pressure columns");
       if (++unfolded == kAdjFold) {
-        LBM_CUDA(launch_adj_fold(hl, hp, gl, gp, c->plane, c->stream), "gradient fold");
+        LBM_CUDA(launch_adj_fold(hl, hp, gl, gp, c->plane, hi), "gradient fold");
         unfolded = 0;
       }
     }
+    LBM_CUDA(cudaEventRecord(freed[k & 1], hi), "cudaEventRecord");
   }
+  return LBM_OK;
+  };
+  if ((rc = sweep())) {  // nothing of the sweep may still run when the workspace changes hands
+    cudaStreamSynchronize(hi);
+    cudaStreamSynchronize(lo);
+    return rc;
+  }
+  LBM_CUDA(cudaEventRecord(ev_done, hi), "cudaEventRecord");
+  LBM_CUDA(cudaStreamWaitEvent(c->stream, ev_done, 0), "cudaStreamWaitEvent");
   LBM_CUDA(launch_adj_init(P, c->het, nu[cur_nu], hp, (float)c->init_p0, (float)c->init_ux, (float)c->init_uy, c->init_phip, c->stream),
            "adjoint initial state");
   LBM_CUDA(launch_adj_fold(hl, hp, gl, gp, c->plane, c->stream), "gradient fold");
