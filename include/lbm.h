@@ -172,6 +172,12 @@ LBM_API int lbm_set_walls(lbm_ctx* ctx, const float* u_wall);
 /* (p, ux, uy, T) of one cell of the current state into out[4] (T = 0 without a temperature
  * field), by the same rules as lbm_macros.  Host outputs wait for the stream. */
 LBM_API int lbm_probe(lbm_ctx* ctx, int x, int y, float* out);
+/* lbm_probe without the wait: the read of the cell is enqueued on the stream and the call returns;
+ * out[4] holds the values once the stream has passed this point (lbm_sync, or an event the caller
+ * records on the stream after the call and waits for).  Host out should be page-locked (pinned):
+ * the copy into pageable memory is staged by the driver and may wait.  A loop that steps, probes
+ * and reads the previous step's probe keeps the GPU busy while the host reads. */
+LBM_API int lbm_probe_async(lbm_ctx* ctx, int x, int y, float* out);
 
 /* Macroscopic fields of the current state (pre-collision populations f(x, t)): pressure p
  * (Eq. 20), velocity u (Eqs. 18-19) and, if thermal, temperature T = sum g.  Outputs are

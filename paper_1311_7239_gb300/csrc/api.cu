@@ -207,6 +207,17 @@ int pointer_kind(const lbm_ctx* c, const void* p) {
   return 0;
 }
 
+// Device address of page-locked host memory mapped into the device's address space (pinned memory
+// under unified addressing), else nullptr: kernels may write there directly.
+float* mapped_host(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? static_cast<float*>(a.devicePointer) : nullptr;
+}
+
 int ensure_stage(lbm_ctx* c, size_t bytes) {
   if (c->stage_bytes >= bytes) return LBM_OK;
   if (c->stage) {
@@ -730,11 +741,27 @@ int lbm_probe(lbm_ctx* c, int x, int y, float* out) {
   const int kind = pointer_kind(c, out);
   if (kind < 0) return fail(LBM_EINVAL, "probe output in memory of another GPU");
   StepParams P = params_for(c);
-  LBM_CUDA(launch_probe(P, c->prec, c->het, thermal_of(c), x, y, kind ? out : c->probe, c->stream), "probe kernel");
+  float* mapped = kind ? nullptr : mapped_host(out);  // pinned host memory: written by the kernel
+  LBM_CUDA(launch_probe(P, c->prec, c->het, thermal_of(c), x, y, kind ? out : (mapped ? mapped : c->probe), c->stream), "probe kernel");
   if (kind == 0) {
-    LBM_CUDA(cudaMemcpyAsync(out, c->probe, 4 * sizeof(float), cudaMemcpyDeviceToHost, c->stream), "copy of probe");
+    if (!mapped) LBM_CUDA(cudaMemcpyAsync(out, c->probe, 4 * sizeof(float), cudaMemcpyDeviceToHost, c->stream), "copy of probe");
     LBM_CUDA(cudaStreamSynchronize(c->stream), "stream synchronize");
   }
+  return LBM_OK;
+}
+
+int lbm_probe_async(lbm_ctx* c, int x, int y, float* out) {
+  if (!c || !out) return fail(LBM_EINVAL, "null argument");
+  if (x < 0 || y < 0 || x >= (int)c->cfg.nx || y >= (int)c->cfg.ny) return fail(LBM_EINVAL, "probe cell outside the lattice");
+  const int kind = pointer_kind(c, out);
+  if (kind < 0) return fail(LBM_EINVAL, "probe output in memory of another GPU");
+  StepParams P = params_for(c);
+  // pinned host memory: the kernel writes it directly; pageable: through the device slot and a copy
+  // (the next probe kernel on the stream runs after this copy has read the slot)
+  float* mapped = kind ? nullptr : mapped_host(out);
+  LBM_CUDA(launch_probe(P, c->prec, c->het, thermal_of(c), x, y, kind ? out : (mapped ? mapped : c->probe), c->stream), "probe kernel");
+  if (kind == 0 && !mapped)
+    LBM_CUDA(cudaMemcpyAsync(out, c->probe, 4 * sizeof(float), cudaMemcpyDeviceToHost, c->stream), "copy of probe");
   return LBM_OK;
 }
 

@@ -83,6 +83,7 @@ SIGNATURES = {
     "lbm_step": (ctypes.c_int, [_c_ctx, ctypes.c_int]),
     "lbm_set_walls": (ctypes.c_int, [_c_ctx, _f32p]),
     "lbm_probe": (ctypes.c_int, [_c_ctx, ctypes.c_int, ctypes.c_int, _f32p]),
+    "lbm_probe_async": (ctypes.c_int, [_c_ctx, ctypes.c_int, ctypes.c_int, _f32p]),
     "lbm_macros": (ctypes.c_int, [_c_ctx, _f32p, _f32p, _f32p, _f32p]),
     "lbm_get_populations": (ctypes.c_int, [_c_ctx, _f32p, _f32p]),
     "lbm_set_populations": (ctypes.c_int, [_c_ctx, _f32p, _f32p]),
@@ -284,6 +285,13 @@ class Lattice:
 
         out = np.empty(4, np.float32) if out is None else out
         _check(lib().lbm_probe(self._h, int(x), int(y), _ptr(out, True)), "lbm_probe")
+        return out
+
+    def probe_async(self, x, y, out):
+        """Enqueue the read of (p, ux, uy, T) of cell (x, y) into out (float32 [4]: pinned host or
+        device tensor) on the context's stream without waiting; out is valid once the stream has
+        passed this point (``sync``, or an event recorded after the call)."""
+        _check(lib().lbm_probe_async(self._h, int(x), int(y), _ptr(out, True)), "lbm_probe_async")
         return out
 
     def _new(self, *shape):

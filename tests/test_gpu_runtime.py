@@ -118,3 +118,32 @@ def test_bench_cavity_stays_bounded_for_50k_steps(lbm, prec):
         lat.sync()
         assert lat.step_count() == 50000
     assert umax <= 0.1 and 0 < r1 < 1e-2 and 0 < r2 < 1e-2, (umax, r1, r2)
+
+
+def test_probe_async_matches_probe_in_a_pipelined_loop(lbm):
+    """lbm_probe_async into pinned host memory (two buffers, an event per step) gives, one step
+    later, what lbm_probe gives after each step; the same into device memory."""
+    import torch
+
+    case = Case(64, 40, nu=0.05, phi=0.5, K=3.0, bc_x="wall", bc_y="wall", walls={"top": (0.1, 0.0)}, het=True)
+    stream = torch.cuda.current_stream()
+    with case.lattice(lbm) as a, case.lattice(lbm) as b:
+        bufs = [torch.zeros(4, dtype=torch.float32).pin_memory() for _ in range(2)]
+        evs = [torch.cuda.Event() for _ in range(2)]
+        want, got = [], []
+        for k in range(12):
+            a.step(1)
+            want.append(a.probe(31, 20).copy())
+            b.step(1)
+            b.probe_async(31, 20, bufs[k & 1])
+            evs[k & 1].record(stream)
+            if k:
+                evs[(k - 1) & 1].synchronize()
+                got.append(bufs[(k - 1) & 1].numpy().copy())
+        evs[11 & 1].synchronize()
+        got.append(bufs[11 & 1].numpy().copy())
+        assert all(np.array_equal(g, w) for g, w in zip(got, want))
+        dev = torch.zeros(4, dtype=torch.float32, device="cuda")
+        b.probe_async(31, 20, dev)
+        b.sync()
+        assert np.array_equal(dev.cpu().numpy(), a.probe(31, 20))
