@@ -210,6 +210,7 @@ int pointer_kind(const lbm_ctx* c, const void* p) {
 // Device address of page-locked host memory mapped into the device's address space (pinned memory
 // under unified addressing), else nullptr: kernels may write there directly.
 float* mapped_host(const void* p) {
+  if (!p) return nullptr;
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
@@ -727,9 +728,15 @@ int lbm_set_walls(lbm_ctx* c, const float* u_wall) {
   if (!c || !u_wall) return fail(LBM_EINVAL, "null argument");
   const int kind = pointer_kind(c, u_wall);
   if (kind < 0) return fail(LBM_EINVAL, "wall velocities in memory of another GPU");
-  LBM_CUDA(cudaMemcpyAsync(c->walls, u_wall, 8 * sizeof(float), kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                           c->stream),
-           "copy of wall velocities");
+  // page-locked host memory: read by a one-warp kernel (a launch on the stream, no copy-engine
+  // hand-over between the steps); other memory: a copy
+  const float* mapped = kind ? nullptr : mapped_host(u_wall);
+  if (mapped)
+    LBM_CUDA(launch_copy_small(c->walls, mapped, 8, c->stream), "copy of wall velocities");
+  else
+    LBM_CUDA(cudaMemcpyAsync(c->walls, u_wall, 8 * sizeof(float), kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                             c->stream),
+             "copy of wall velocities");
   for (int i = 0; i < 8; ++i)
     if (kind == 0) c->cfg.u_wall[i / 2][i % 2] = u_wall[i];
   return LBM_OK;

@@ -435,6 +435,17 @@ cudaError_t launch_macros(const StepParams& P, int prec, bool het, bool thermal,
   return cudaGetLastError();
 }
 
+// a few floats, e.g. wall velocities from page-locked host memory that the device reads directly
+__global__ void k_copy_small(float* __restrict__ dst, const float* __restrict__ src, int n) {
+  const int i = threadIdx.x;
+  if (i < n) dst[i] = src[i];
+}
+
+cudaError_t launch_copy_small(float* dst, const float* src, int n, cudaStream_t s) {
+  k_copy_small<<<1, 32, 0, s>>>(dst, src, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_probe(const StepParams& P, int prec, bool het, bool thermal, int x, int y, float* out, cudaStream_t s) {
 #define CALL_PROBE(PR, H, TH) k_probe<PR, H, TH><<<1, 32, 0, s>>>(P, x, y, out)
   LBM_DISPATCH_PHT(prec, het, thermal, CALL_PROBE);

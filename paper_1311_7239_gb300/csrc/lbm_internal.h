@@ -52,6 +52,7 @@ cudaError_t launch_import(const StepParams& P, int prec, const float* f, const f
 cudaError_t launch_export(const StepParams& P, int prec, bool het, bool thermal, float* f, float* g, cudaStream_t s);
 cudaError_t launch_macros(const StepParams& P, int prec, bool het, bool thermal, float* p, float* ux, float* uy, float* T,
                           cudaStream_t s);
+cudaError_t launch_copy_small(float* dst, const float* src, int n, cudaStream_t s);
 cudaError_t launch_probe(const StepParams& P, int prec, bool het, bool thermal, int x, int y, float* out, cudaStream_t s);
 int residual_blocks(int nx, int ny);
 cudaError_t launch_residual(const StepParams& P, int prec, bool het, bool thermal, const void* prev, const void* gprev,
