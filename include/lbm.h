@@ -269,6 +269,9 @@ typedef struct lbm_batch lbm_batch;
 
 /* Create the batch and initialise every lattice to the equilibrium at p = 1, u = 0. */
 LBM_API int lbm_batch_create(const lbm_config* cfgs, int n, lbm_batch** out);
+/* lbm_batch_create under the name used in the method's interface description (same arguments,
+ * same behaviour). */
+LBM_API int lbm_create_batch(const lbm_config* cfgs, int n, lbm_batch** out);
 LBM_API void lbm_batch_destroy(lbm_batch* b);
 /* Medium of lattice d (as lbm_set_medium; waits for the stream). */
 LBM_API int lbm_batch_set_medium(lbm_batch* b, int d, const float* eps, const float* K);

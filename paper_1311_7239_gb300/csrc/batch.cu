@@ -390,6 +390,8 @@ int lbm_batch_create(const lbm_config* cfgs, int n, lbm_batch** out) {
   return LBM_OK;
 }
 
+int lbm_create_batch(const lbm_config* cfgs, int n, lbm_batch** out) { return lbm_batch_create(cfgs, n, out); }
+
 void lbm_batch_destroy(lbm_batch* b) { release(b); }
 
 int lbm_batch_set_medium(lbm_batch* b, int d, const float* eps, const float* K) {

@@ -101,6 +101,7 @@ SIGNATURES = {
     "lbm_step_count": (ctypes.c_int, [_c_ctx, ctypes.POINTER(ctypes.c_int64)]),
     "lbm_memory_bytes": (ctypes.c_int, [_c_ctx, ctypes.POINTER(ctypes.c_uint64)]),
     "lbm_batch_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "lbm_create_batch": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     "lbm_batch_destroy": (None, [ctypes.c_void_p]),
     "lbm_batch_set_medium": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _f32p, _f32p]),
     "lbm_batch_init_equilibrium": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double,

@@ -89,6 +89,7 @@ def test_batch_rejects_mixed_streaming_without_a_device(L):
     cfgs = (lbm.Config * 2)(lbm.default_config(), lbm.default_config(streaming=lbm.STREAM_INPLACE))
     h = ctypes.c_void_p()
     assert L.lbm_batch_create(cfgs, 2, ctypes.byref(h)) == lbm.EINVAL
+    assert L.lbm_create_batch(cfgs, 2, ctypes.byref(h)) == lbm.EINVAL  # the same call under its other name
     assert not h.value and b"streaming" in L.lbm_last_error()
 
 
