@@ -70,8 +70,9 @@ extern "C" {
                                * LBM_STREAM_AB with half the population memory.  All sides; with LBM_NEE or
                                * LBM_PRESSURE sides each step first computes the boundary nodes' states
                                * (one small extra launch; 4 (8 or 13) (nx + ny) bytes kept), since a
-                               * boundary node reads a neighbour that the step overwrites.  Not for
-                               * lbm_adjoint; batches: LBM_PERIODIC and LBM_WALL sides only.  The last step of each
+                               * boundary node reads a neighbour that the step overwrites.  lbm_adjoint
+                               * runs on two A-B buffers of its workspace; batches: LBM_PERIODIC and
+                               * LBM_WALL sides only.  The last step of each
                                * lbm_step call records the velocity of its collisions, u(t-1) for
                                * lbm_residual (8 B per cell kept and written once per call), unless
                                * LBM_OPT_NO_RESIDUAL_RECORD is set.  Limit:
@@ -222,8 +223,9 @@ LBM_API int lbm_residual_noalloc(const float* ux, const float* uy, const float* 
 
 /* Discrete adjoint of T flow steps (collision Eq. 14, streaming Eq. 15, pressure columns and
  * extrapolated wall nodes) from the current initial state (call right after lbm_init_equilibrium;
- * ESTATE otherwise, and for thermal or in-place contexts; EINVAL for an LBM_NEE side pair fewer than
- * 4 nodes apart): runs the T steps -- the context ends at step T, as after lbm_step(ctx, T) -- and
+ * ESTATE otherwise, and for thermal contexts; EINVAL for an LBM_NEE side pair fewer than 4 nodes
+ * apart; an in-place context runs the sweep on two A-B state buffers of the workspace and takes the
+ * final state back into its own layout): runs the T steps -- the context ends at step T, as after lbm_step(ctx, T) -- and
  * returns the loss and its gradient with respect to the per-cell log K and eps (phi) fields,
  * including their effect on the initial equilibrium (Eq. 22).  Memory: checkpoints of the
  * post-collision state every ceil(sqrt(T)) steps, two segments of ceil(sqrt(T)) states (the

@@ -935,7 +935,6 @@ int lbm_adjoint(lbm_ctx* c, int T, int loss_kind, const float* target_ux, const 
   if (loss_kind != LBM_LOSS_OUTLET_FLUX && loss_kind != LBM_LOSS_VELOCITY_MISFIT) return fail(LBM_EINVAL, "unknown loss kind");
   if (loss_kind == LBM_LOSS_VELOCITY_MISFIT && (!target_ux || !target_uy)) return fail(LBM_EINVAL, "misfit loss needs a target");
   if (thermal_of(c)) return fail(LBM_ESTATE, "the adjoint covers the isothermal flow step only");
-  if (c->inplace) return fail(LBM_ESTATE, "the adjoint needs A-B streaming (its checkpoints are A-B states)");
   if ((c->cfg.bc_x == LBM_NEE && c->cfg.nx < 4) || (c->cfg.bc_y == LBM_NEE && c->cfg.ny < 4))
     return fail(LBM_EINVAL, "the adjoint through extrapolated wall nodes needs at least 4 nodes across each such side pair");
   if (c->steps != 0 || c->history != 0)
@@ -968,7 +967,31 @@ int lbm_adjoint(lbm_ctx* c, int T, int loss_kind, const float* target_ux, const 
   for (int h = 0; h < 2; ++h)
     for (int j = 0; j < ck; ++j)
       if (!(seg[h][j] = ws_slot(c, 6 + nck + h * ck + j, fbytes, &rc, "cudaMalloc(segment states)"))) return rc;
-  ws_trim(c, 6 + nck + 2 * ck);
+  // In-place contexts: the sweep runs on two A-B state buffers of the workspace, from the same
+  // initial state and with the same kernels as an A-B context; the final state is then written back
+  // into the in-place layout (and the velocity of step T - 1 into the residual's record).
+  const bool ip = c->inplace;
+  void* ab[2] = {c->f[0], c->f[1]};
+  for (int b = 0; ip && b < 2; ++b)
+    if (!(ab[b] = ws_slot(c, 6 + nck + 2 * ck + b, fbytes, &rc, "cudaMalloc(A-B states)"))) return rc;
+  ws_trim(c, 6 + nck + 2 * ck + (ip ? 2 : 0));
+  if (ip && (rc = ensure_stage(c, 10 * n * sizeof(float)))) return rc;  // targets, then the final state
+  StepParams B = params_for(c);
+  B.inplace = 0;
+  B.parity = 0;
+  B.edge = nullptr;
+  B.urec = nullptr;
+  int cur = ip ? 0 : c->cur;
+  auto ab_params = [&](int k) {
+    StepParams Q = B;
+    Q.src = ab[k];
+    Q.dst = ab[k ^ 1];
+    return Q;
+  };
+  if (ip)
+    LBM_CUDA(launch_init(ab_params(1), c->prec, c->het, false, (float)c->init_p0, (float)c->init_ux, (float)c->init_uy, c->init_phip,
+                         0.0f, true, false, c->stream),
+             "init kernel");
   if (!c->adj_hi) {
     int least = 0, greatest = 0;
     LBM_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest), "cudaDeviceGetStreamPriorityRange");
@@ -994,20 +1017,36 @@ int lbm_adjoint(lbm_ctx* c, int T, int loss_kind, const float* target_ux, const 
   // forward sweep, keeping the buffer before every ck-th step
   for (int t = 0; t < T; ++t) {
     if (t % ck == 0)
-      LBM_CUDA(cudaMemcpyAsync(ckpt[t / ck], c->f[c->cur], fbytes, cudaMemcpyDeviceToDevice, c->stream), "checkpoint copy");
-    LBM_CUDA(launch_step(params_at(c, c->cur), c->prec, c->het, false, c->stream), "step kernel");
-    c->cur ^= 1;
+      LBM_CUDA(cudaMemcpyAsync(ckpt[t / ck], ab[cur], fbytes, cudaMemcpyDeviceToDevice, c->stream), "checkpoint copy");
+    LBM_CUDA(launch_step(ab_params(cur), c->prec, c->het, false, c->stream), "step kernel");
+    cur ^= 1;
     ++c->steps;
     ++c->history;
   }
-  StepParams P = params_at(c, c->cur);
+  if (!ip) c->cur = cur;
+  StepParams P = ab_params(cur);
   const int nb = residual_blocks((int)c->cfg.nx, (int)c->cfg.ny);
   double* loss_dev = c->red + 2 * kResidualMaxBlocks;
   LBM_CUDA(launch_adj_seed(P, c->prec, c->het, nu[0], hl, hp, loss_kind, tux, tuy, c->red, nb, loss_dev, c->stream), "adjoint seed");
   const bool walls = c->cfg.bc_x == LBM_NEE || c->cfg.bc_y == LBM_NEE;
   // J_N^T of the boundary nodes N = (wall nodes) o (pressure columns): wall nodes first
-  if (walls) LBM_CUDA(launch_adj_wall(P, c->prec, c->het, c->f[c->cur], nu[0], hl, hp, c->stream), "adjoint wall nodes");
-  if (pressure) LBM_CUDA(launch_adj_nee(P, c->prec, c->het, c->f[c->cur], nu[0], hl, hp, c->stream), "adjoint pressure columns");
+  if (walls) LBM_CUDA(launch_adj_wall(P, c->prec, c->het, ab[cur], nu[0], hl, hp, c->stream), "adjoint wall nodes");
+  if (pressure) LBM_CUDA(launch_adj_nee(P, c->prec, c->het, ab[cur], nu[0], hl, hp, c->stream), "adjoint pressure columns");
+  if (ip) {  // the state after step T into the in-place layout; u of step T - 1 into the record
+    // (moved as deviations, p_rest = 0 on both sides, so that no rest value is added and taken off
+    // again; the boundary nodes' own values, which that changes, are never read: the in-place step
+    // and the read-outs extrapolate them from their inner neighbours)
+    float* dense = c->stage + 2 * n;
+    StepParams E = ab_params(cur), I = params_at(c, c->cur);
+    E.p_rest = 0.0f;
+    I.p_rest = 0.0f;
+    LBM_CUDA(launch_export(E, c->prec, c->het, false, dense, nullptr, c->stream), "export kernel");
+    LBM_CUDA(launch_put_inplace(I, c->prec, c->het, dense, nullptr, true, false, 0.0f, 0.0f, 0.0f, 0, 0.0f, c->stream),
+             "in-place put kernel");
+    if (c->uprev)
+      LBM_CUDA(launch_macros(ab_params(cur ^ 1), c->prec, c->het, false, nullptr, c->uprev, c->uprev + n, nullptr, c->stream),
+               "record of u(t-1)");
+  }
   int cur_nu = 0, unfolded = 1;
   constexpr int kAdjFold = 64;  // at most this many per-step terms in an FP32 partial sum
   // Reverse sweep over the segments, last first.  The states of segment k - 1 are recomputed from
