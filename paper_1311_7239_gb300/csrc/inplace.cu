@@ -29,6 +29,21 @@ __device__ __forceinline__ void record_u(const StepParams& P, int x, int y, floa
   P.urec[(int64_t)P.nx * P.ny + o] = uy;
 }
 
+// the same for the two cells x, x + 1 (x even): one 8-byte store per component when the record's
+// rows start on 8 bytes (nx even)
+__device__ __forceinline__ void record_u2(const StepParams& P, int x, int y, float2 ux, float2 uy) {
+  const int64_t o = (int64_t)y * P.nx + x, n = (int64_t)P.nx * P.ny;
+  if ((P.nx & 1) == 0) {
+    *reinterpret_cast<float2*>(P.urec + o) = ux;
+    *reinterpret_cast<float2*>(P.urec + n + o) = uy;
+  } else {
+    P.urec[o] = ux.x;
+    P.urec[o + 1] = ux.y;
+    P.urec[n + o] = uy.x;
+    P.urec[n + o + 1] = uy.y;
+  }
+}
+
 // Extrapolated sides (wall nodes and pressure columns): a boundary node's pre-collision state is
 // a function of its inner neighbour's, which that neighbour's own update overwrites in the same
 // pass.  So k_edge_ip computes the states of all boundary nodes of the coming step first (the
@@ -285,10 +300,7 @@ __device__ __forceinline__ void ip_block(const StepParams& P, int frame_blocks, 
       float2 ux, uy;
       collide_pair(dp2, pair_coef_uniform(P.pc), f2(P.pc.u_hx), f2(P.pc.u_hy), P.pc, ux, uy);
       check += (fabsf(ux.x) + fabsf(uy.x)) + (fabsf(ux.y) + fabsf(uy.y));
-      if (REC) {
-        record_u(P, x0 + 2 * h, y, ux.x, uy.x);
-        record_u(P, x0 + 2 * h + 1, y, ux.y, uy.y);
-      }
+      if (REC) record_u2(P, x0 + 2 * h, y, ux, uy);
 #pragma unroll
       for (int i = 0; i < 8; ++i) w[i][h] = S::f2w(dp2[i]);
     }
@@ -328,7 +340,7 @@ __device__ __forceinline__ void ip_block(const StepParams& P, int frame_blocks, 
       load_right<PREC>(G + (PAR ? 3 : 1) * pl + y0x, 0, inv, g[3]);    // (-1, 0): cells x + 1
       S::load4(G + ((PAR ? 4 : 2) * pl + y0x + dp), g[4], inv);        // ( 0,-1): row y + 1
     }
-    float check = 0.0f;
+    float check = 0.0f, rux = 0.0f, ruy = 0.0f;
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       float dc[8];
@@ -340,7 +352,14 @@ __device__ __forceinline__ void ip_block(const StepParams& P, int frame_blocks, 
       float ux, uy, phip;
       collide_d2q8(dc, cf, P.ax, ay, P, ux, uy, phip);
       check += fabsf(ux) + fabsf(uy);
-      if (REC) record_u(P, x0 + c, y, ux, uy);
+      if (REC) {  // the record in pairs of cells
+        if (c & 1) {
+          record_u2(P, x0 + c - 1, y, make_float2(rux, ux), make_float2(ruy, uy));
+        } else {
+          rux = ux;
+          ruy = uy;
+        }
+      }
 #pragma unroll
       for (int i = 0; i < 8; ++i) d[i][c] = dc[i];
       if (THERMAL) {
