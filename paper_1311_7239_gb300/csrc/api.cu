@@ -1073,26 +1073,26 @@ int lbm_adjoint(lbm_ctx* c, int T, int loss_kind, const float* target_ux, const 
     return LBM_OK;
   };
   auto sweep = [&]() -> int {
-  int rc2 = recompute(nck - 1);
-  if (rc2) return rc2;
-  for (int k = nck - 1; k >= 0; --k) {
-    const int t0 = k * ck, t1 = (t0 + ck < T) ? t0 + ck : T;
-    if (k > 0 && (rc2 = recompute(k - 1))) return rc2;
-    LBM_CUDA(cudaStreamWaitEvent(hi, ready[k & 1], 0), "cudaStreamWaitEvent");
-    for (int t = t1 - 1; t >= t0; --t) {
-      const void* buf = seg[k & 1][t - t0];
-      LBM_CUDA(launch_adj_step(P, c->prec, c->het, buf, nu[cur_nu], nu[cur_nu ^ 1], hl, hp, hi), "adjoint step");
-      cur_nu ^= 1;
-      if (walls) LBM_CUDA(launch_adj_wall(P, c->prec, c->het, buf, nu[cur_nu], hl, hp, hi), "adjoint wall nodes");
-      if (pressure) LBM_CUDA(launch_adj_nee(P, c->prec, c->het, buf, nu[cur_nu], hl, hp, hi), "adjoint pressure columns");
-      if (++unfolded == kAdjFold) {
-        LBM_CUDA(launch_adj_fold(hl, hp, gl, gp, c->plane, hi), "gradient fold");
-        unfolded = 0;
+    int rc2 = recompute(nck - 1);
+    if (rc2) return rc2;
+    for (int k = nck - 1; k >= 0; --k) {
+      const int t0 = k * ck, t1 = (t0 + ck < T) ? t0 + ck : T;
+      if (k > 0 && (rc2 = recompute(k - 1))) return rc2;
+      LBM_CUDA(cudaStreamWaitEvent(hi, ready[k & 1], 0), "cudaStreamWaitEvent");
+      for (int t = t1 - 1; t >= t0; --t) {
+        const void* buf = seg[k & 1][t - t0];
+        LBM_CUDA(launch_adj_step(P, c->prec, c->het, buf, nu[cur_nu], nu[cur_nu ^ 1], hl, hp, hi), "adjoint step");
+        cur_nu ^= 1;
+        if (walls) LBM_CUDA(launch_adj_wall(P, c->prec, c->het, buf, nu[cur_nu], hl, hp, hi), "adjoint wall nodes");
+        if (pressure) LBM_CUDA(launch_adj_nee(P, c->prec, c->het, buf, nu[cur_nu], hl, hp, hi), "adjoint pressure columns");
+        if (++unfolded == kAdjFold) {
+          LBM_CUDA(launch_adj_fold(hl, hp, gl, gp, c->plane, hi), "gradient fold");
+          unfolded = 0;
+        }
       }
+      LBM_CUDA(cudaEventRecord(freed[k & 1], hi), "cudaEventRecord");
     }
-    LBM_CUDA(cudaEventRecord(freed[k & 1], hi), "cudaEventRecord");
-  }
-  return LBM_OK;
+    return LBM_OK;
   };
   if ((rc = sweep())) {  // nothing of the sweep may still run when the workspace changes hands
     cudaStreamSynchronize(hi);
